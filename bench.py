@@ -1,0 +1,368 @@
+"""Benchmark: G pair-interactions/s of velocity-Verlet steps at N = 1e5.
+
+Workload: the large-cloud configuration -- 1e5 singly charged ions of 40 u,
+uniform in a 200 x 200 x 1000 um ellipsoid held by the harmonic
+pseudopotential for which that spheroid is a cold-fluid equilibrium, 10 mK
+velocities, dt = 1 ns (seeded, synthetic).  A step is one full
+velocity-Verlet step through the C ABI (nb_step: drift, the O(N^2) pair
+kernel, the kick/trap/friction epilogue).  value = N^2 pair interactions per
+step x steps x ranks / the max over ranks of the device time of the K timed
+steps (CUDA events on the launching stream; L2 flushed by a 256 MB write
+between timed steps, outside the timed events).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+  python bench.py --impl reference   # the FP64 CPU oracle on the host cores
+
+--gpus N > 1 runs one independent replica per rank (the path is one
+all-pairs problem per GPU here; no collective on the data path).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G pair-interactions/s & % FMA peak, FP64 vs mixed (rel err ≤1e-6) at N=1e5"
+UNIT = "G pair-interactions/s"
+# Flop convention A: 20 flops per pair interaction (3 sub, 3 mul + 2 add for
+# r^2, 1 softening add, sqrt, divide, 2 mul for the cube, 3 mul + 3 add).
+FLOPS_PER_PAIR = 20
+# ALU peaks from unit counts and the maximum SM clock (152 SMs, 2070 MHz):
+# FP64: 2 FMA lanes/clk/SM (1.25 TFLOP/s nominal), FP32: 128 FMA lanes/clk/SM.
+SM_COUNT, SM_MHZ = 152, 2070.0
+PEAK_TFLOPS = {
+    "fp64": 2 * 2 * SM_COUNT * SM_MHZ * 1e6 / 1e12,
+    "f32": 2 * 128 * SM_COUNT * SM_MHZ * 1e6 / 1e12,
+}
+PATH_PEAK = {"fp64": "fp64", "mixed": "f32", "mixed_split": "f32"}
+DTYPE = {"fp64": "f64", "mixed": "f32+f64", "mixed_split": "f32+f64"}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed_split", choices=["fp64", "mixed", "mixed_split"])
+    ap.add_argument("--n", type=int, default=100000, help="ions (default: the 1e5 workload)")
+    ap.add_argument("--no-paths", action="store_true", help="skip the secondary precisions")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--profile-forces", action="store_true",
+                    help="profiling case: two nb_forces calls per precision at --n, no timing")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "nb_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    elif args.impl == "ours":
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world, device="cuda"):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(w, target_s=12.0):
+    """The FP64 oracle (as it stands) on the host cores: one force evaluation
+    restricted to a bounded sample of target ions [0, S) against all N."""
+    import oracle
+    p = oracle.make_params(**w["phys"])
+    n = w["n"]
+    s0 = 256
+    t = time.perf_counter()
+    oracle.coulomb(p, *w["pos"], i0=0, i1=s0)
+    dt0 = time.perf_counter() - t
+    s = int(min(n, max(s0, s0 * target_s / max(dt0, 1e-6))))
+    t = time.perf_counter()
+    oracle.coulomb(p, *w["pos"], i0=0, i1=s)
+    dt = time.perf_counter() - t
+    return {"value": s * n / dt / 1e9, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": "one FP64 force evaluation of ions [0, %d) against all %d ions (%.3g pairs, %.1f s)"
+                      % (s, n, s * n, dt)}
+
+
+# ---------------------------------------------------------------------------
+def run_path(nb, w, precision, steps, warmup, world, flush, clocks=None):
+    """Time `steps` single-step nb_step calls; returns device ms per step, the
+    mean pair-kernel duration, and the launch count of the timed region."""
+    import torch
+    lib = nb.lib()
+    par = nb.Params.from_phys(w["phys"], precision=precision)
+    sysm = nb.System(w["pos"], w["vel"])
+    nb.forces(par, sysm, total=True)
+    for _ in range(warmup):
+        nb.step(par, sysm, 1)
+    nb.sync_status()
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    _check(lib.nb_timing_enable(steps), lib)
+    launches0 = lib.nb_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(st)
+        nb.step(par, sysm, 1)
+        ev[k][1].record(st)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier(world)
+    clk = clocks.stop() if clocks else None
+    launches = lib.nb_launch_count() - launches0
+    nl, tot = _timing_read(lib)
+    _check(lib.nb_timing_enable(0), lib)
+    nb.sync_status()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    return {"ms": dev_ms, "ms_per_step": dev_ms / steps, "kernel_ms": tot / max(nl, 1),
+            "kernel_launches": nl, "launches": int(launches), "wall_s": t_wall, "clocks": clk,
+            "sys": sysm, "par": par}
+
+
+def _check(rc, lib):
+    if rc != 0:
+        raise RuntimeError("libnb: " + lib.nb_last_error().decode())
+
+
+def _timing_read(lib):
+    import ctypes as C
+    n = C.c_int64()
+    ms = C.c_double()
+    _check(lib.nb_timing_read(C.byref(n), C.byref(ms)), lib)
+    return n.value, ms.value
+
+
+def run_e2e(nb, w, precision, steps, world, flush):
+    """Same metric through the public API with host buffers: every step copies
+    the state (x, v, a) from pinned host memory to the device, runs nb_step,
+    and reads the state back into pinned host memory."""
+    import torch
+    n = w["n"]
+    par = nb.Params.from_phys(w["phys"], precision=precision)
+    sysm = nb.System(w["pos"], w["vel"])
+    nb.forces(par, sysm, total=True)
+    names = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")
+    host = {k: getattr(sysm, k).cpu().pin_memory() for k in names}
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(st)
+        for nm in names:
+            getattr(sysm, nm).copy_(host[nm], non_blocking=True)
+        nb.step(par, sysm, 1)
+        for nm in names:
+            host[nm].copy_(getattr(sysm, nm), non_blocking=True)
+        ev[k][1].record(st)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms = allreduce_max(ms, world)
+    nbytes = len(names) * n * 8
+    return {"value": world * n * n * steps / (ms / 1e3) / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+
+def roofline(path, n, kernel_ms):
+    achieved = FLOPS_PER_PAIR * n * n / (kernel_ms / 1e3) / 1e12
+    peak = PEAK_TFLOPS[PATH_PEAK[path]]
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "k_pair_force<%s>" % path,
+            "peak_source": "%s FMA lanes x 2 flops x 152 SMs x 2070 MHz (unit counts and max clock)"
+                           % ("2 FP64" if PATH_PEAK[path] == "fp64" else "128 FP32"),
+            "convention": "A: 20 flops per pair interaction"}
+
+
+def main_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    import paper_2106_11143_gb300 as nb
+    from paper_2106_11143_gb300 import workloads as W
+    w = W.cloud_large(n=args.n)
+    n = w["n"]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    head = run_path(nb, w, args.precision, args.steps, args.warmup, world, flush, clocks)
+    ms = allreduce_max(head["ms"], world)
+    value = world * n * n * args.steps / (ms / 1e3) / 1e9
+    e2e = run_e2e(nb, w, args.precision, min(args.steps, 20), world, flush)
+    paths = {}
+    if not args.no_paths:
+        for pth in ("fp64", "mixed", "mixed_split"):
+            r = head if pth == args.precision else run_path(nb, w, pth, max(2, min(args.steps, 5)), 1,
+                                                            world, flush)
+            paths[pth] = {"value": round(n * n / (r["ms_per_step"] / 1e3) / 1e9, 3), "unit": UNIT,
+                          "ms_per_step": round(r["ms_per_step"], 4),
+                          "kernel_ms": round(r["kernel_ms"], 4),
+                          "roofline": roofline(pth, n, r["kernel_ms"])}
+        paths["speedup_mixed_over_fp64"] = round(paths["fp64"]["ms_per_step"] / paths["mixed"]["ms_per_step"], 3)
+        paths["speedup_mixed_split_over_fp64"] = round(
+            paths["fp64"]["ms_per_step"] / paths["mixed_split"]["ms_per_step"], 3)
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu else cpu_baseline(w)
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": w["name"] + ": 1e5 ions (40 u, +e) uniform in a 200x200x1000 um ellipsoid, "
+                   "cold-fluid harmonic trap, 10 mK, dt=1 ns; one velocity-Verlet step per timed step",
+                   "n": n, "precision": args.precision, "pairs_per_step": n * n,
+                   "l2": "flushed between timed steps (256 MB write outside the timed events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline(args.precision, n, head["kernel_ms"]),
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": head["launches"],
+        "clocks": head["clocks"],
+        "paths": paths,
+    }
+    print(json.dumps(out))
+
+
+def main_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2106_11143_gb300 import workloads as W
+    w = W.cloud_large(n=args.n)
+    n = w["n"]
+    p = oracle.make_params(**w["phys"])
+    # one step = one oracle force evaluation for a bounded sample of target ions
+    s0 = 128
+    t = time.perf_counter()
+    oracle.coulomb(p, *w["pos"], i0=0, i1=s0)
+    dt0 = time.perf_counter() - t
+    s = int(min(n, max(s0, s0 * 4.0 / max(dt0, 1e-6))))
+    for k in range(args.warmup):
+        oracle.coulomb(p, *w["pos"], i0=0, i1=min(s, 2048))
+    t = time.perf_counter()
+    for k in range(args.steps):
+        i0 = (k * s) % n
+        oracle.coulomb(p, *w["pos"], i0=i0, i1=min(n, i0 + s))
+    dt = time.perf_counter() - t
+    value = args.steps * s * n / dt / 1e9
+    sample = "per step: FP64 oracle forces of %d target ions against all %d ions (%.3g pairs)" % (s, n, s * n)
+    print(json.dumps({
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": w["name"], "n": n, "precision": "fp64 oracle (Neumaier-compensated)"},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": oracle.get_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def profile_forces(args):
+    """Small case for ncu: a warm-up pass then a measured pass of nb_forces in
+    each precision (pair-kernel launches 1-3 warm up, 4-6 are the ones to capture)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2106_11143_gb300 as nb
+    from paper_2106_11143_gb300 import workloads as W
+    w = W.cloud_large(n=args.n)
+    sysm = nb.System(w["pos"], w["vel"])
+    for _ in range(2):
+        for prec in ("fp64", "mixed", "mixed_split"):
+            nb.forces(nb.Params.from_phys(w["phys"], precision=prec), sysm)
+    nb.sync_status()
+    print("profile case done: n=%d" % w["n"])
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.profile_forces:
+        profile_forces(a)
+    elif a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

@@ -1,0 +1,192 @@
+/*
+ * nb.h -- C ABI of libnb.so, a GB300 (sm_103a) library for the direct
+ * N-body problem of laser-cooled trapped ions, after Pedregosa-Gutierrez &
+ * Dempsey, "Direct N-Body problem optimisation using the AVX-512
+ * instruction set" (arXiv 2106.11143).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Units are SI.  Arrays are structure-of-arrays (SoA), float64, one value
+ *    per ion, contiguous, 8-byte aligned, and live in DEVICE memory of the
+ *    current CUDA device unless the argument says "host".  The caller owns
+ *    every array it passes; the library never frees or keeps caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous with respect to the host on that
+ *    stream unless stated otherwise.
+ *  - Scratch memory (pair partial sums, the second position buffer, block
+ *    partials, a device error word) belongs to the library.  It is
+ *    allocated with cudaMalloc on first use, per (device, stream), grown on
+ *    demand, reused by later calls on the same stream, and freed by
+ *    nb_release().  Calls on the same stream are ordered; calls on
+ *    different streams use different scratch.
+ *  - Every call validates its arguments on the host first and returns
+ *    NB_EINVAL without enqueuing any work if they are wrong.  Numerical
+ *    failures on the device (a non-finite acceleration or velocity) are
+ *    recorded in the stream's device error word and reported by the next
+ *    nb_sync_status() on that stream; the state is then undefined.
+ *  - n == 0 is valid and does nothing.
+ *  - Results are deterministic: identical inputs and launch configuration
+ *    give bitwise-identical outputs (fixed, atomic-free summation order).
+ */
+#ifndef NB_H
+#define NB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NB_OK = 0,
+  NB_EINVAL = 1,      /* invalid argument (null pointer, bad size, bad enum) */
+  NB_ECUDA = 2,       /* a CUDA runtime call failed; see nb_last_error() */
+  NB_ENONFINITE = 3,  /* a non-finite acceleration or velocity was produced */
+  NB_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+  NB_ENOMEM = 5,      /* scratch allocation failed */
+  NB_ENOTSUP = 6      /* valid request this build does not implement */
+} nb_status;
+
+/* Arithmetic of the pair interaction (the O(N^2) inner loop).
+ *  NB_FP64       -- FP64 throughout.  1/sqrt(r^2) is seeded by the FP32
+ *                   hardware reciprocal square root (MUFU) and refined in
+ *                   FP64 (Sec. IV: approximate 1/sqrt refined by
+ *                   Newton-Raphson), result within a few ulp of FP64.
+ *  NB_MIXED      -- pair displacements in FP64, cast to FP32; r^2, rsqrt,
+ *                   r^-3 and the products in FP32; per-tile FP32 partial
+ *                   sums added into FP64 accumulators with compensation.
+ *  NB_MIXED_SPLIT -- as NB_MIXED, but each position is carried as an FP32
+ *                   (hi, lo) pair built from the FP64 value once per call,
+ *                   and the displacement is (hi_i - hi_j) + (lo_i - lo_j)
+ *                   in FP32.  Same accuracy class as NB_MIXED.
+ * Positions, velocities, the integrator and energies are FP64 in all modes. */
+typedef enum { NB_FP64 = 0, NB_MIXED = 1, NB_MIXED_SPLIT = 2 } nb_precision;
+
+/* Confinement (Eq. 1 of the paper).
+ *  NB_TRAP_HARMONIC -- static pseudopotential: a_k = -omega_k(t)^2 x_k.
+ *  NB_TRAP_RF       -- linear Paul trap with Mathieu a = 0 and q = q_mathieu:
+ *                      a_x = -(q Omega^2/2) cos(Omega t + phase) x,
+ *                      a_y = +(q Omega^2/2) cos(Omega t + phase) y,
+ *                      a_z = -omega_z(t)^2 z  (omega_z = omega[2]).       */
+typedef enum { NB_TRAP_HARMONIC = 0, NB_TRAP_RF = 1 } nb_trap;
+
+typedef struct nb_params {
+  double k_coulomb;     /* 1/(4 pi eps0) */
+  double mass;          /* kg, one species (Sec. II) */
+  double charge;        /* C, charge of every ion when nb_system.q is NULL */
+  double soft2;         /* softening eps^2 added to r^2 (m^2); 0 = none */
+  int32_t trap;         /* nb_trap */
+  int32_t precision;    /* nb_precision */
+  double omega[3];      /* rad/s at t = 0 */
+  double omega_rate[3]; /* rad/s^2: omega_k(t) = omega[k] + omega_rate[k] t */
+  double q_mathieu;     /* RF Mathieu q */
+  double omega_rf;      /* RF angular frequency Omega (rad/s) */
+  double rf_phase;      /* rad */
+  double gamma;         /* friction coefficient Gamma (kg/s), Eq. 1 */
+  double dt;            /* time step (s) */
+  double t0;            /* time of step 0: t = t0 + step * dt */
+  double noise_T;       /* Langevin temperature (K); 0 = no noise */
+  uint64_t seed;        /* Philox4x32-10 key for the Langevin noise */
+  uint32_t instance;    /* ensemble member index (noise counter word) */
+  uint32_t reserved;    /* must be 0 */
+} nb_params;
+
+typedef struct nb_system {
+  int64_t n;            /* number of ions */
+  double *x, *y, *z;    /* positions (m), device */
+  double *vx, *vy, *vz; /* velocities (m/s), device */
+  double *ax, *ay, *az; /* acceleration (m/s^2), device: the Verlet state */
+  const double *q;      /* per-ion charge (C), device, or NULL = params.charge */
+  int64_t step;         /* step counter; time t = t0 + step * dt */
+} nb_system;
+
+/* nb_forces flags */
+#define NB_ACC_COULOMB 0 /* write the Coulomb acceleration only */
+#define NB_ACC_TOTAL 1   /* Coulomb + trap(t) - (gamma/m) v: the Verlet state */
+
+/* Acceleration of every ion (Eq. 1; the Sec. III pair loop):
+ *   a_i = k_C q_i / m * sum_{j != i} q_j (r_i - r_j) / (|r_i - r_j|^2 + soft2)^{3/2}
+ * plus, with NB_ACC_TOTAL, the trap term at t = t0 + step*dt and the friction
+ * -(gamma/m) v.  Writes sys->ax/ay/az.  The pair arithmetic follows
+ * params->precision.  If phi is non-NULL (device, n doubles) it receives the
+ * potential sum_{j != i} q_j / sqrt(r_ij^2 + soft2) (FP64; no k_C factor).
+ * Two distinct ions at the same position with soft2 == 0 contribute nothing
+ * to each other (the self-pair rule applied to r == 0).                   */
+nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi,
+                    int flags, void *stream);
+
+/* nsteps velocity-Verlet steps (Sec. II):
+ *   r+ = r + v dt + a dt^2/2;  a+ = a(r+, t+dt);  v+ = v + (a + a+) dt/2.
+ * The friction part of a+ depends on v+; the velocity update is solved for it
+ * exactly: v+ = (v + (a + a+_cons) dt/2) / (1 + gamma dt/(2m)), and the stored
+ * a+ = a+_cons - (gamma/m) v+.  With noise_T > 0 a Langevin kick
+ * sqrt(2 gamma kB T dt)/m * xi is added to v+, xi ~ N(0,1) per component from
+ * Philox4x32-10 with key `seed` and counter {ion, step, step >> 32, instance}
+ * (step of the new state), via Box-Muller.
+ * On entry sys->a must hold the total acceleration at the current state (call
+ * nb_forces with NB_ACC_TOTAL once after setting positions/velocities).
+ * Updates x, v, a in place and advances sys->step by nsteps.  One force
+ * launch and one epilogue launch per step; no host synchronisation.      */
+nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps,
+                  void *stream);
+
+/* Energies at the current state, written to HOST memory out[4] =
+ * {kinetic, trap, Coulomb, total} in joules:
+ *   kinetic = (m/2) sum |v|^2,
+ *   trap    = the potential of the trap term of Eq. 1 at t (harmonic:
+ *             (m/2) sum omega_k^2 x_k^2; RF: (m/2) sum (c (x^2 - y^2) +
+ *             omega_z^2 z^2), c = (q Omega^2/2) cos(Omega t + phase)),
+ *   Coulomb = (k_C/2) sum_i q_i sum_{j != i} q_j / sqrt(r_ij^2 + soft2).
+ * FP64 pair arithmetic regardless of params->precision.  Synchronises the
+ * stream before returning.                                               */
+nb_status nb_energy(const nb_params *params, const nb_system *sys,
+                    double out[4], void *stream);
+
+/* Vector-Jacobian product of the position dependence of the acceleration:
+ *   g_i = k_C q_i/m sum_{j != i} q_j [ dl/s^3 - 3 d (d . dl) / s^5 ],
+ *   d = r_i - r_j, dl = lam_i - lam_j, s^2 = |d|^2 + soft2,
+ * plus, with NB_ACC_TOTAL, the trap's diagonal term at the current time.
+ * The Jacobian is symmetric, so this is also the Jacobian-vector product.
+ * lam* and g* are device SoA arrays of n doubles.  FP64.                  */
+nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys,
+                        const double *lx, const double *ly, const double *lz,
+                        double *gx, double *gy, double *gz, int flags,
+                        void *stream);
+
+/* Synchronises `stream`, then returns and clears its device error word:
+ * NB_OK, NB_ENONFINITE or NB_ETIMEOUT (or NB_ECUDA if the stream failed). */
+nb_status nb_sync_status(void *stream);
+
+/* Frees all library scratch on every device (after synchronising them). */
+nb_status nb_release(void);
+
+/* Static description of a status code. */
+const char *nb_strerror(nb_status status);
+
+/* Detail of the most recent failure on the calling thread ("" if none). */
+const char *nb_last_error(void);
+
+/* Library version string. */
+const char *nb_version(void);
+
+/* ---- Instrumentation (benchmarks and tests) ---------------------------- */
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t nb_launch_count(void);
+
+/* Kernel timing: with capacity > 0, every O(N^2) pair-kernel launch of the
+ * calling process is bracketed by two CUDA events recorded on the stream it
+ * is launched on, for up to `capacity` launches (events are created here, on
+ * the current device).  capacity == 0 disables timing and frees the events. */
+nb_status nb_timing_enable(int64_t capacity);
+
+/* Waits for the recorded events, returns the number of timed pair-kernel
+ * launches and their summed device duration in milliseconds, and restarts
+ * the count.  Launches beyond the capacity are not timed.                  */
+nb_status nb_timing_read(int64_t *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NB_H */

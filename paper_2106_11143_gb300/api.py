@@ -1,0 +1,238 @@
+"""ctypes binding of libnb.so (include/nb.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI.  Device arrays are torch float64 CUDA tensors; the
+binding passes their data pointers and the current torch stream.  There is
+no CPU fallback -- if libnb.so is missing, every call raises.
+"""
+import ctypes as C
+import os
+from dataclasses import dataclass, field, fields
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnb.so")
+
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_split": 2}
+TRAPS = {"harmonic": 0, "rf": 1}
+NB_ACC_COULOMB, NB_ACC_TOTAL = 0, 1
+
+
+class NbParams(C.Structure):
+    _fields_ = [
+        ("k_coulomb", C.c_double), ("mass", C.c_double), ("charge", C.c_double),
+        ("soft2", C.c_double), ("trap", C.c_int32), ("precision", C.c_int32),
+        ("omega", C.c_double * 3), ("omega_rate", C.c_double * 3),
+        ("q_mathieu", C.c_double), ("omega_rf", C.c_double), ("rf_phase", C.c_double),
+        ("gamma", C.c_double), ("dt", C.c_double), ("t0", C.c_double),
+        ("noise_T", C.c_double), ("seed", C.c_uint64), ("instance", C.c_uint32),
+        ("reserved", C.c_uint32),
+    ]
+
+
+_dp = C.POINTER(C.c_double)
+
+
+class NbSystem(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64),
+        ("x", _dp), ("y", _dp), ("z", _dp),
+        ("vx", _dp), ("vy", _dp), ("vz", _dp),
+        ("ax", _dp), ("ay", _dp), ("az", _dp),
+        ("q", _dp), ("step", C.c_int64),
+    ]
+
+
+class NBError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__("%s: %s (status %d)%s" % (where, _lib_strerror(status), status,
+                                                   (": " + detail) if detail else ""))
+
+
+_LIB = None
+
+
+def lib():
+    """Load libnb.so (raises if it has not been built: no fallback exists)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnb.so is not built (run paper_2106_11143_gb300/build.py); "
+                               "this package has no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        P, S, V = C.POINTER(NbParams), C.POINTER(NbSystem), C.c_void_p
+        L.nb_forces.argtypes = [P, S, _dp, C.c_int, V]
+        L.nb_step.argtypes = [P, S, C.c_int64, V]
+        L.nb_energy.argtypes = [P, S, _dp, V]
+        L.nb_forces_vjp.argtypes = [P, S, _dp, _dp, _dp, _dp, _dp, _dp, C.c_int, V]
+        L.nb_sync_status.argtypes = [V]
+        L.nb_strerror.argtypes = [C.c_int]
+        L.nb_strerror.restype = C.c_char_p
+        L.nb_last_error.restype = C.c_char_p
+        L.nb_version.restype = C.c_char_p
+        L.nb_timing_enable.argtypes = [C.c_int64]
+        L.nb_timing_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+        L.nb_launch_count.restype = C.c_uint64
+        for f in ("nb_forces", "nb_step", "nb_energy", "nb_forces_vjp", "nb_sync_status",
+                  "nb_release", "nb_timing_enable", "nb_timing_read"):
+            getattr(L, f).restype = C.c_int
+        _LIB = L
+    return _LIB
+
+
+def _lib_strerror(status):
+    try:
+        return lib().nb_strerror(status).decode()
+    except Exception:
+        return "status"
+
+
+def _check(status, where):
+    if status != 0:
+        raise NBError(status, where, lib().nb_last_error().decode())
+
+
+@dataclass
+class Params:
+    """Physical parameters (SI) and the pair-arithmetic precision."""
+    k_coulomb: float
+    mass: float
+    charge: float
+    soft2: float = 0.0
+    trap: str = "harmonic"
+    precision: str = "fp64"
+    omega: tuple = (0.0, 0.0, 0.0)
+    omega_rate: tuple = (0.0, 0.0, 0.0)
+    q_mathieu: float = 0.0
+    omega_rf: float = 0.0
+    rf_phase: float = 0.0
+    gamma: float = 0.0
+    dt: float = 1e-9
+    t0: float = 0.0
+    noise_T: float = 0.0
+    seed: int = 0
+    instance: int = 0
+
+    @classmethod
+    def from_phys(cls, phys, precision="fp64", **kw):
+        names = {f.name for f in fields(cls)}
+        d = {k: v for k, v in phys.items() if k in names}
+        d["precision"] = precision
+        d.update(kw)
+        return cls(**d)
+
+    def to_c(self):
+        p = NbParams()
+        p.k_coulomb, p.mass, p.charge, p.soft2 = self.k_coulomb, self.mass, self.charge, self.soft2
+        p.trap = TRAPS[self.trap]
+        p.precision = PRECISIONS[self.precision]
+        p.omega = (C.c_double * 3)(*self.omega)
+        p.omega_rate = (C.c_double * 3)(*self.omega_rate)
+        p.q_mathieu, p.omega_rf, p.rf_phase = self.q_mathieu, self.omega_rf, self.rf_phase
+        p.gamma, p.dt, p.t0, p.noise_T = self.gamma, self.dt, self.t0, self.noise_T
+        p.seed, p.instance, p.reserved = int(self.seed), int(self.instance), 0
+        return p
+
+
+def _dev(a, device):
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device, dtype=torch.float64).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=device)
+
+
+def _ptr(t):
+    return None if t is None else C.cast(C.c_void_p(t.data_ptr()), _dp)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class System:
+    """Ion state in device memory: SoA float64 tensors x, y, z, vx, vy, vz,
+    ax, ay, az (length n), optional per-ion charges q, and the step counter."""
+
+    def __init__(self, pos, vel=None, q=None, device="cuda", step=0):
+        pos = _dev(pos, device).reshape(3, -1)
+        n = pos.shape[1]
+        vel = torch.zeros(3, n, dtype=torch.float64, device=device) if vel is None else \
+            _dev(vel, device).reshape(3, n)
+        self.n = n
+        self.x, self.y, self.z = (pos[k].contiguous() for k in range(3))
+        self.vx, self.vy, self.vz = (vel[k].contiguous() for k in range(3))
+        self.ax, self.ay, self.az = (torch.zeros(n, dtype=torch.float64, device=device)
+                                     for _ in range(3))
+        self.q = None if q is None else _dev(q, device).reshape(n)
+        self.step = int(step)
+
+    def to_c(self):
+        s = NbSystem()
+        s.n = self.n
+        for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
+            setattr(s, k, _ptr(getattr(self, k)))
+        s.q = _ptr(self.q)
+        s.step = self.step
+        return s
+
+    def pos(self):
+        return torch.stack([self.x, self.y, self.z])
+
+    def vel(self):
+        return torch.stack([self.vx, self.vy, self.vz])
+
+    def acc(self):
+        return torch.stack([self.ax, self.ay, self.az])
+
+
+def forces(params, system, total=False, want_phi=False, stream=None):
+    """nb_forces: write system.ax/ay/az (Coulomb, or the total Verlet-state
+    acceleration when total=True).  Returns phi (device tensor) if asked."""
+    phi = torch.empty(system.n, dtype=torch.float64, device=system.x.device) if want_phi else None
+    s = system.to_c()
+    _check(lib().nb_forces(C.byref(params.to_c()), C.byref(s), _ptr(phi),
+                           NB_ACC_TOTAL if total else NB_ACC_COULOMB, _stream(stream)), "nb_forces")
+    return phi
+
+
+def step(params, system, nsteps, stream=None):
+    """nb_step: nsteps velocity-Verlet steps in place."""
+    s = system.to_c()
+    _check(lib().nb_step(C.byref(params.to_c()), C.byref(s), int(nsteps), _stream(stream)),
+           "nb_step")
+    system.step = s.step
+
+
+def energy(params, system, stream=None):
+    """nb_energy: (kinetic, trap, Coulomb, total) in J as a numpy array."""
+    out = np.empty(4)
+    s = system.to_c()
+    _check(lib().nb_energy(C.byref(params.to_c()), C.byref(s),
+                           out.ctypes.data_as(_dp), _stream(stream)), "nb_energy")
+    return out
+
+
+def forces_vjp(params, system, lam, total=False, stream=None):
+    """nb_forces_vjp: J^T lam for lam of shape (3, n); returns (3, n)."""
+    lam = _dev(lam, system.x.device).reshape(3, system.n)
+    lx, ly, lz = (lam[k].contiguous() for k in range(3))
+    g = torch.empty(3, system.n, dtype=torch.float64, device=system.x.device)
+    s = system.to_c()
+    _check(lib().nb_forces_vjp(C.byref(params.to_c()), C.byref(s), _ptr(lx), _ptr(ly), _ptr(lz),
+                               _ptr(g[0]), _ptr(g[1]), _ptr(g[2]),
+                               NB_ACC_TOTAL if total else NB_ACC_COULOMB, _stream(stream)),
+           "nb_forces_vjp")
+    return g
+
+
+def sync_status(stream=None):
+    """nb_sync_status: synchronise and raise on a recorded device error."""
+    _check(lib().nb_sync_status(_stream(stream)), "nb_sync_status")
+
+
+def release():
+    _check(lib().nb_release(), "nb_release")

@@ -1,0 +1,473 @@
+// nb_api.cu -- host side of the C ABI declared in include/nb.h.
+//
+// Argument validation, per-(device, stream) scratch arenas, launch planning
+// and the orchestration of the pair and epilogue kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <map>
+#include <vector>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include "nb_common.cuh"
+
+namespace nb {
+
+cudaError_t launch_chunk_sum1(int64_t n, const double *part, int n_jc, double scale, double *out,
+                              cudaStream_t st);
+
+namespace {
+
+thread_local std::string g_last_error;
+
+nb_status fail(nb_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define NB_CUDA_TRY(call)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(NB_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                  __FILE__, __LINE__);                                                 \
+  } while (0)
+
+// Scratch owned by the library for one (device, stream).
+struct Arena {
+  char *buf = nullptr;
+  size_t cap = 0;
+  unsigned *err = nullptr;  // device error word
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, cudaStream_t>, Arena> g_arenas;
+
+// Returns the arena of the current device and `st` with at least `bytes`
+// of scratch.  Growing synchronises `st` before the old buffer is freed.
+nb_status get_arena(cudaStream_t st, size_t bytes, Arena **out) {
+  int dev = 0;
+  NB_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  Arena &a = g_arenas[std::make_pair(dev, st)];
+  if (!a.err) {
+    if (cudaMalloc(&a.err, 256) != cudaSuccess) return fail(NB_ENOMEM, "cudaMalloc(error word) failed");
+    NB_CUDA_TRY(cudaMemsetAsync(a.err, 0, 256, st));
+  }
+  if (a.cap < bytes) {
+    if (a.buf) {
+      NB_CUDA_TRY(cudaStreamSynchronize(st));
+      NB_CUDA_TRY(cudaFree(a.buf));
+      a.buf = nullptr;
+      a.cap = 0;
+    }
+    const size_t want = bytes + bytes / 8;  // headroom against repeated growth
+    if (cudaMalloc(&a.buf, want) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(NB_ENOMEM, "cudaMalloc(%zu bytes of scratch) failed", want);
+    }
+    a.cap = want;
+  }
+  *out = &a;
+  return NB_OK;
+}
+
+// Carves aligned sub-buffers out of an arena.
+struct Carver {
+  size_t off = 0;
+  char *base = nullptr;
+  template <class T>
+  T *take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+bool finite(double v) { return std::isfinite(v); }
+
+nb_status check_params(const nb_params *p) {
+  if (!p) return fail(NB_EINVAL, "params is NULL");
+  if (!(p->mass > 0.0) || !finite(p->mass)) return fail(NB_EINVAL, "mass must be positive and finite");
+  if (!finite(p->k_coulomb) || !finite(p->charge) || !finite(p->soft2) || p->soft2 < 0.0)
+    return fail(NB_EINVAL, "k_coulomb, charge and soft2 must be finite (soft2 >= 0)");
+  if (p->trap != NB_TRAP_HARMONIC && p->trap != NB_TRAP_RF) return fail(NB_EINVAL, "unknown trap %d", p->trap);
+  if (p->precision < NB_FP64 || p->precision > NB_MIXED_SPLIT)
+    return fail(NB_EINVAL, "unknown precision %d", p->precision);
+  for (int k = 0; k < 3; ++k)
+    if (!finite(p->omega[k]) || !finite(p->omega_rate[k])) return fail(NB_EINVAL, "omega must be finite");
+  if (!finite(p->q_mathieu) || !finite(p->omega_rf) || !finite(p->rf_phase) || !finite(p->gamma) ||
+      !finite(p->dt) || !finite(p->t0) || !finite(p->noise_T))
+    return fail(NB_EINVAL, "trap, friction and time parameters must be finite");
+  if (p->gamma < 0.0 || p->noise_T < 0.0) return fail(NB_EINVAL, "gamma and noise_T must be >= 0");
+  if (p->noise_T > 0.0 && p->gamma == 0.0) return fail(NB_EINVAL, "noise_T > 0 needs gamma > 0");
+  if (p->reserved != 0) return fail(NB_EINVAL, "params.reserved must be 0");
+  return NB_OK;
+}
+
+bool aligned8(const void *ptr) { return ((uintptr_t)ptr & 7u) == 0; }
+
+nb_status check_array(const void *ptr, const char *name) {
+  if (!ptr) return fail(NB_EINVAL, "%s is NULL", name);
+  if (!aligned8(ptr)) return fail(NB_EINVAL, "%s is not 8-byte aligned", name);
+  return NB_OK;
+}
+
+#define NB_TRY(expr)          \
+  do {                        \
+    nb_status s_ = (expr);    \
+    if (s_ != NB_OK) return s_; \
+  } while (0)
+
+nb_status check_system(const nb_system *s, bool need_v, bool need_a) {
+  if (!s) return fail(NB_EINVAL, "system is NULL");
+  if (s->n < 0) return fail(NB_EINVAL, "n must be >= 0");
+  if (s->n > ((int64_t)1 << 31)) return fail(NB_EINVAL, "n above 2^31 is not supported");
+  if (s->n == 0) return NB_OK;
+  NB_TRY(check_array(s->x, "x"));
+  NB_TRY(check_array(s->y, "y"));
+  NB_TRY(check_array(s->z, "z"));
+  if (need_v) {
+    NB_TRY(check_array(s->vx, "vx"));
+    NB_TRY(check_array(s->vy, "vy"));
+    NB_TRY(check_array(s->vz, "vz"));
+  }
+  if (need_a) {
+    NB_TRY(check_array(s->ax, "ax"));
+    NB_TRY(check_array(s->ay, "ay"));
+    NB_TRY(check_array(s->az, "az"));
+  }
+  if (s->q && !aligned8(s->q)) return fail(NB_EINVAL, "q is not 8-byte aligned");
+  return NB_OK;
+}
+
+Phys to_phys(const nb_params *p) {
+  Phys f;
+  f.k_coulomb = p->k_coulomb;
+  f.mass = p->mass;
+  f.charge = p->charge;
+  f.soft2 = p->soft2;
+  f.trap = p->trap;
+  f.precision = p->precision;
+  for (int k = 0; k < 3; ++k) {
+    f.omega[k] = p->omega[k];
+    f.omega_rate[k] = p->omega_rate[k];
+  }
+  f.q_mathieu = p->q_mathieu;
+  f.omega_rf = p->omega_rf;
+  f.rf_phase = p->rf_phase;
+  f.gamma = p->gamma;
+  f.dt = p->dt;
+  f.t0 = p->t0;
+  f.noise_T = p->noise_T;
+  f.seed = p->seed;
+  f.instance = p->instance;
+  return f;
+}
+
+StateView to_view(const nb_system *s) {
+  StateView v;
+  v.n = s->n;
+  v.x = s->x; v.y = s->y; v.z = s->z;
+  v.vx = s->vx; v.vy = s->vy; v.vz = s->vz;
+  v.ax = s->ax; v.ay = s->ay; v.az = s->az;
+  v.q = s->q;
+  return v;
+}
+
+// Scratch need of one force evaluation.
+size_t force_bytes(const Plan &pl, int mode, int64_t n, bool extra_pos, bool phi, const Plan &plp) {
+  Carver c;
+  c.take<double>((size_t)pl.n_jc * 3 * n);
+  if (mode == MODE_SPLIT) c.take<float>(6 * (size_t)n);
+  if (extra_pos) c.take<double>(3 * (size_t)n);
+  if (phi) c.take<double>((size_t)plp.n_jc * n);
+  return c.off + 256;
+}
+
+// Force evaluation at positions (x, y, z) into `part`.
+nb_status pair_forces(const Plan &pl, int mode, int64_t n, const double *x, const double *y,
+                      const double *z, const double *q, double soft2, double *part, float *split,
+                      cudaStream_t st) {
+  PosF32 pf{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (mode == MODE_SPLIT) {
+    NB_CUDA_TRY(launch_split_positions(n, x, y, z, split, st));
+    count_launches(1);
+    pf = PosF32{split, split + n, split + 2 * n, split + 3 * n, split + 4 * n, split + 5 * n};
+  }
+  timing_begin(st);
+  NB_CUDA_TRY(launch_pair_force(pl, mode, n, x, y, z, q, pf, soft2, part, st));
+  timing_end(st);
+  count_launches(1);
+  return NB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Instrumentation state.
+std::atomic<uint64_t> g_launches{0};
+std::mutex g_tmu;
+std::vector<cudaEvent_t> g_ev;  // pairs: start, stop
+int64_t g_ev_cap = 0, g_ev_used = 0;
+
+}  // namespace
+
+void count_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+
+void timing_begin(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  if (g_ev_used < g_ev_cap) cudaEventRecord(g_ev[2 * g_ev_used], st);
+}
+
+void timing_end(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  if (g_ev_used < g_ev_cap) {
+    cudaEventRecord(g_ev[2 * g_ev_used + 1], st);
+    ++g_ev_used;
+  }
+}
+
+}  // namespace nb
+
+using namespace nb;
+
+extern "C" {
+
+nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi, int flags,
+                    void *stream) {
+  NB_TRY(check_params(params));
+  NB_TRY(check_system(sys, (flags & NB_ACC_TOTAL) != 0, true));
+  if (flags & ~NB_ACC_TOTAL) return fail(NB_EINVAL, "unknown flags 0x%x", flags);
+  if (phi && !aligned8(phi)) return fail(NB_EINVAL, "phi is not 8-byte aligned");
+  const int64_t n = sys->n;
+  if (n == 0) return NB_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int mode = params->precision;
+  const Plan pl = make_plan(n, mode, 0);
+  const Plan plp = make_plan(n, MODE_FP64, 1);
+  Arena *a = nullptr;
+  NB_TRY(get_arena(st, force_bytes(pl, mode, n, false, phi != nullptr, plp), &a));
+  Carver cv;
+  cv.base = a->buf;
+  double *part = cv.take<double>((size_t)pl.n_jc * 3 * n);
+  float *split = mode == MODE_SPLIT ? cv.take<float>(6 * (size_t)n) : nullptr;
+  double *ppart = phi ? cv.take<double>((size_t)plp.n_jc * n) : nullptr;
+  const Phys p = to_phys(params);
+  const StateView v = to_view(sys);
+  const double t = params->t0 + (double)sys->step * params->dt;
+  NB_TRY(pair_forces(pl, mode, n, sys->x, sys->y, sys->z, sys->q, params->soft2, part, split, st));
+  NB_CUDA_TRY(launch_epi_forces(p, v, part, pl.n_jc, flags, t, a->err, st));
+  count_launches(1);
+  if (phi) {
+    NB_CUDA_TRY(launch_pair_phi(plp, n, sys->x, sys->y, sys->z, sys->q, params->charge, params->soft2, ppart, st));
+    // the pair sums carry w_j = q_j, or 1 for a single species
+    NB_CUDA_TRY(launch_chunk_sum1(n, ppart, plp.n_jc, sys->q ? 1.0 : params->charge, phi, st));
+    count_launches(2);
+  }
+  return NB_OK;
+}
+
+nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void *stream) {
+  NB_TRY(check_params(params));
+  NB_TRY(check_system(sys, true, true));
+  if (nsteps < 0) return fail(NB_EINVAL, "nsteps must be >= 0");
+  if (!(params->dt > 0.0)) return fail(NB_EINVAL, "dt must be > 0");
+  const int64_t n = sys->n;
+  if (n == 0 || nsteps == 0) {
+    sys->step += nsteps;
+    return NB_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int mode = params->precision;
+  const Plan pl = make_plan(n, mode, 0);
+  Arena *a = nullptr;
+  NB_TRY(get_arena(st, force_bytes(pl, mode, n, true, false, pl), &a));
+  Carver cv;
+  cv.base = a->buf;
+  double *part = cv.take<double>((size_t)pl.n_jc * 3 * n);
+  float *split = mode == MODE_SPLIT ? cv.take<float>(6 * (size_t)n) : nullptr;
+  double *other = cv.take<double>(3 * (size_t)n);
+  double *ubuf[3] = {sys->x, sys->y, sys->z};
+  double *obuf[3] = {other, other + n, other + 2 * n};
+  // Position buffer of step s: chosen so that the last step reads the
+  // library buffer and writes the final positions into the caller's arrays.
+  auto buf = [&](int64_t s) -> double ** { return ((nsteps - 1 - s) % 2 == 0) ? obuf : ubuf; };
+  const Phys p = to_phys(params);
+  const StateView v = to_view(sys);
+  double **b0 = buf(0);
+  NB_CUDA_TRY(launch_drift(p, v, b0[0], b0[1], b0[2], st));
+  count_launches(1);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    double **P = buf(s);
+    NB_TRY(pair_forces(pl, mode, n, P[0], P[1], P[2], sys->q, params->soft2, part, split, st));
+    const int64_t snew = sys->step + s + 1;
+    if (s + 1 < nsteps) {
+      double **Nx = buf(s + 1);
+      NB_CUDA_TRY(launch_epi_step(p, v, P[0], P[1], P[2], part, pl.n_jc, snew, Nx[0], Nx[1], Nx[2], a->err, st));
+    } else {
+      NB_CUDA_TRY(launch_epi_step(p, v, P[0], P[1], P[2], part, pl.n_jc, snew, nullptr, nullptr, nullptr, a->err, st));
+    }
+    count_launches(1);
+  }
+  sys->step += nsteps;
+  return NB_OK;
+}
+
+nb_status nb_energy(const nb_params *params, const nb_system *sys, double out[4], void *stream) {
+  NB_TRY(check_params(params));
+  NB_TRY(check_system(sys, true, false));
+  if (!out) return fail(NB_EINVAL, "out is NULL");
+  const int64_t n = sys->n;
+  if (n == 0) {
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    return NB_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const Plan pl = make_plan(n, MODE_FP64, 1);
+  Carver need;
+  need.take<double>((size_t)pl.n_jc * n);
+  need.take<double>(3 * ENERGY_BLOCKS);
+  need.take<double>(4);
+  Arena *a = nullptr;
+  NB_TRY(get_arena(st, need.off + 256, &a));
+  Carver cv;
+  cv.base = a->buf;
+  double *ppart = cv.take<double>((size_t)pl.n_jc * n);
+  double *bpart = cv.take<double>(3 * ENERGY_BLOCKS);
+  double *out4 = cv.take<double>(4);
+  const Phys p = to_phys(params);
+  const StateView v = to_view(sys);
+  const double t = params->t0 + (double)sys->step * params->dt;
+  NB_CUDA_TRY(launch_pair_phi(pl, n, sys->x, sys->y, sys->z, sys->q, params->charge, params->soft2, ppart, st));
+  NB_CUDA_TRY(launch_energy(p, v, ppart, pl.n_jc, t, bpart, out4, st));
+  count_launches(3);
+  NB_CUDA_TRY(cudaMemcpyAsync(out, out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  NB_CUDA_TRY(cudaStreamSynchronize(st));
+  return NB_OK;
+}
+
+nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys, const double *lx,
+                        const double *ly, const double *lz, double *gx, double *gy, double *gz,
+                        int flags, void *stream) {
+  NB_TRY(check_params(params));
+  NB_TRY(check_system(sys, false, false));
+  if (flags & ~NB_ACC_TOTAL) return fail(NB_EINVAL, "unknown flags 0x%x", flags);
+  const int64_t n = sys->n;
+  if (n == 0) return NB_OK;
+  NB_TRY(check_array(lx, "lx"));
+  NB_TRY(check_array(ly, "ly"));
+  NB_TRY(check_array(lz, "lz"));
+  NB_TRY(check_array(gx, "gx"));
+  NB_TRY(check_array(gy, "gy"));
+  NB_TRY(check_array(gz, "gz"));
+  cudaStream_t st = (cudaStream_t)stream;
+  const Plan pl = make_plan(n, MODE_FP64, 2);
+  Arena *a = nullptr;
+  NB_TRY(get_arena(st, (size_t)pl.n_jc * 3 * n * sizeof(double) + 512, &a));
+  double *part = reinterpret_cast<double *>(a->buf);
+  const Phys p = to_phys(params);
+  const StateView v = to_view(sys);
+  const double t = params->t0 + (double)sys->step * params->dt;
+  NB_CUDA_TRY(launch_pair_vjp(pl, n, sys->x, sys->y, sys->z, sys->q, lx, ly, lz, params->soft2, part, st));
+  NB_CUDA_TRY(launch_epi_vjp(p, v, part, pl.n_jc, lx, ly, lz, gx, gy, gz, flags, t, st));
+  count_launches(2);
+  return NB_OK;
+}
+
+nb_status nb_sync_status(void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  NB_CUDA_TRY(cudaStreamSynchronize(st));
+  int dev = 0;
+  NB_CUDA_TRY(cudaGetDevice(&dev));
+  unsigned *err = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_arenas.find(std::make_pair(dev, st));
+    if (it == g_arenas.end() || !it->second.err) return NB_OK;
+    err = it->second.err;
+  }
+  unsigned h = 0;
+  NB_CUDA_TRY(cudaMemcpy(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (h) NB_CUDA_TRY(cudaMemset(err, 0, sizeof(unsigned)));
+  if (h & ERR_TIMEOUT) return fail(NB_ETIMEOUT, "a bounded device wait gave up");
+  if (h & ERR_NONFINITE) return fail(NB_ENONFINITE, "a non-finite acceleration or velocity was produced");
+  return NB_OK;
+}
+
+nb_status nb_release(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  nb_status rc = NB_OK;
+  for (auto &kv : g_arenas) {
+    if (cudaSetDevice(kv.first.first) != cudaSuccess) { rc = NB_ECUDA; continue; }
+    cudaDeviceSynchronize();
+    if (kv.second.buf && cudaFree(kv.second.buf) != cudaSuccess) rc = NB_ECUDA;
+    if (kv.second.err && cudaFree(kv.second.err) != cudaSuccess) rc = NB_ECUDA;
+  }
+  g_arenas.clear();
+  cudaSetDevice(cur);
+  if (rc != NB_OK) fail(rc, "freeing scratch failed");
+  return rc;
+}
+
+const char *nb_strerror(nb_status status) {
+  switch (status) {
+    case NB_OK: return "success";
+    case NB_EINVAL: return "invalid argument";
+    case NB_ECUDA: return "CUDA runtime error";
+    case NB_ENONFINITE: return "non-finite acceleration or velocity";
+    case NB_ETIMEOUT: return "device-side wait timed out";
+    case NB_ENOMEM: return "out of device memory";
+    case NB_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+const char *nb_last_error(void) { return g_last_error.c_str(); }
+
+const char *nb_version(void) { return "nb-gb300 0.1 (sm_103a)"; }
+
+uint64_t nb_launch_count(void) { return g_launches.load(); }
+
+nb_status nb_timing_enable(int64_t capacity) {
+  if (capacity < 0) return fail(NB_EINVAL, "capacity must be >= 0");
+  std::lock_guard<std::mutex> lk(g_tmu);
+  for (cudaEvent_t e : g_ev) cudaEventDestroy(e);
+  g_ev.clear();
+  g_ev_cap = g_ev_used = 0;
+  for (int64_t k = 0; k < 2 * capacity; ++k) {
+    cudaEvent_t e;
+    NB_CUDA_TRY(cudaEventCreate(&e));
+    g_ev.push_back(e);
+  }
+  g_ev_cap = capacity;
+  return NB_OK;
+}
+
+nb_status nb_timing_read(int64_t *launches, double *total_ms) {
+  if (!launches || !total_ms) return fail(NB_EINVAL, "NULL output");
+  std::lock_guard<std::mutex> lk(g_tmu);
+  double tot = 0.0;
+  for (int64_t k = 0; k < g_ev_used; ++k) {
+    float ms = 0.0f;
+    NB_CUDA_TRY(cudaEventSynchronize(g_ev[2 * k + 1]));
+    NB_CUDA_TRY(cudaEventElapsedTime(&ms, g_ev[2 * k], g_ev[2 * k + 1]));
+    tot += ms;
+  }
+  *launches = g_ev_used;
+  *total_ms = tot;
+  g_ev_used = 0;
+  return NB_OK;
+}
+
+}  // extern "C"

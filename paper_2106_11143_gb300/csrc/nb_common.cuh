@@ -1,0 +1,190 @@
+// nb_common.cuh -- device helpers and internal launch interface of libnb.so.
+//
+// Internal to the library: the public ABI is include/nb.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/nb.h"
+
+namespace nb {
+
+// ---------------------------------------------------------------------------
+// Device error word bits (reported by nb_sync_status).
+enum : unsigned { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
+
+// CODATA 2018 exact Boltzmann constant (J/K), for the Langevin kick.
+constexpr double KB = 1.380649e-23;
+
+// Pair-arithmetic modes (nb_precision).
+enum Mode : int { MODE_FP64 = 0, MODE_MIXED = 1, MODE_SPLIT = 2 };
+
+// ---------------------------------------------------------------------------
+// Integer-only conversions between FP64 and FP32 bit patterns.  On this GPU
+// the FP64<->FP32 convert instructions issue on the narrow FP64 pipe (about
+// 1.7 lanes/clk/SM), so the pair loop builds the FP32 operand and the FP64
+// seed with integer shifts and adds instead (64 lanes/clk/SM).
+
+// 1/sqrt(r2) for an FP64 r2 >= 0, from the FP32 hardware approximation
+// (MUFU.RSQ, relative error about 2^-22), returned as an FP64 value.
+// r2 = 1.m * 2^E is scaled by 2^-2k (k = floor(E/2)) into [1, 4) while
+// building the FP32 bit pattern, so every normal FP64 r2 is accepted; the
+// FP32 result is rescaled by 2^-k while building the FP64 bit pattern.
+// The mantissa is truncated to 23 bits (relative error < 2^-23 on r2).
+// r2 == 0 or subnormal returns 0, which makes the pair contribute nothing.
+__device__ __forceinline__ double rsqrt_seed_f64(double r2) {
+  const int hi = __double2hiint(r2);
+  const unsigned lo = (unsigned)__double2loint(r2);
+  const int e = hi >> 20;                     // biased exponent (r2 >= 0)
+  const int k = (e - 1023) >> 1;              // floor((e - 1023) / 2)
+  const unsigned fs = __funnelshift_l(lo, (unsigned)hi, 3);
+  // exponent 127 ([1,2)) when e - 1023 is even, 128 ([2,4)) when odd
+  const unsigned fexp = (e & 1) ? 0x3f800000u : 0x40000000u;
+  const float r2s = __uint_as_float((fs & 0x007fffffu) | fexp);
+  float ys;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ys) : "f"(r2s));
+  const unsigned yb = __float_as_uint(ys);
+  const int yhi = (int)(yb >> 3) + ((896 - k) << 20);
+  const int ylo = (int)(yb << 29);
+  return (e == 0) ? 0.0 : __hiloint2double(yhi, ylo);
+}
+
+// FP64 -> FP32 rounded to nearest (ties away from zero) with 32-bit integer
+// ops only: 64-bit integer adds and masks would issue on the FP64 pipe.  The
+// rounding increment at mantissa bit 29 is a carry-chained 32-bit add.
+// |d| < 2^-126 yields an FP32 zero or subnormal of the same sign (such
+// displacements only occur as exact zeros); |d| must be below 2^128.
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+  const unsigned lo = (unsigned)__double2loint(d);
+  const unsigned hi = (unsigned)__double2hiint(d);
+  unsigned lo2, ahi2;
+  asm("add.cc.u32 %0, %2, 0x10000000;\n\taddc.u32 %1, %3, 0;"
+      : "=r"(lo2), "=r"(ahi2)
+      : "r"(lo), "r"(hi & 0x7fffffffu));
+  const int t = max((int)ahi2 - (896 << 20), 0);  // FP32 exponent field in bits 20..27
+  const unsigned mag = __funnelshift_l(lo2, (unsigned)t, 3);
+  return __uint_as_float(mag | (hi & 0x80000000u));
+}
+
+// Exact FP32 -> FP64 widening by integer ops, for normal or zero inputs
+// (subnormal FP32 inputs flush to zero).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned a = b & 0x7fffffffu;
+  const int hi = (int)((b & 0x80000000u) | ((a >> 3) + (896u << 20)));
+  const int lo = (int)(b << 29);
+  return (a < 0x00800000u) ? __hiloint2double((int)(b & 0x80000000u), 0)
+                           : __hiloint2double(hi, lo);
+}
+
+// Non-finite test on the FP64 bit pattern (exponent all ones).
+__device__ __forceinline__ bool not_finite(double v) {
+  return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+}
+
+// Error-free sum: s + e == a + b exactly (Knuth TwoSum).
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+  s = a + b;
+  const double bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// ---------------------------------------------------------------------------
+// Physics parameters as the kernels see them (copied by value).
+struct Phys {
+  double k_coulomb, mass, charge, soft2;
+  int trap, precision;
+  double omega[3], omega_rate[3];
+  double q_mathieu, omega_rf, rf_phase, gamma, dt, t0, noise_T;
+  unsigned long long seed;
+  unsigned instance;
+};
+
+// Trap acceleration at time t (Eq. 1).
+__device__ __forceinline__ void trap_accel(const Phys &p, double t, double x, double y,
+                                           double z, double &tx, double &ty, double &tz) {
+  if (p.trap == NB_TRAP_RF) {
+    const double c = 0.5 * p.q_mathieu * p.omega_rf * p.omega_rf * cos(p.omega_rf * t + p.rf_phase);
+    const double wz = p.omega[2] + p.omega_rate[2] * t;
+    tx = -c * x;
+    ty = c * y;
+    tz = -wz * wz * z;
+  } else {
+    const double wx = p.omega[0] + p.omega_rate[0] * t;
+    const double wy = p.omega[1] + p.omega_rate[1] * t;
+    const double wz = p.omega[2] + p.omega_rate[2] * t;
+    tx = -wx * wx * x;
+    ty = -wy * wy * y;
+    tz = -wz * wz * z;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pair-sum launch plan: blocks of `block` threads, each thread owns R
+// i-particles (i-tile = block * R), j split into chunks of `jchunk`
+// (a multiple of block) so that n_it * n_jc blocks fill the GPU.  Each
+// (i-tile, j-chunk) block writes its partial sums to its own slot; a later
+// kernel adds the slots in chunk order, so the result is deterministic.
+struct Plan {
+  int block = 128;
+  int R = 1;
+  int64_t jchunk = 0;
+  int n_it = 0;
+  int n_jc = 0;
+};
+
+Plan make_plan(int64_t n, int mode, int kind);  // kind: 0 force, 1 phi, 2 vjp
+int device_sm_count();
+
+// Launch accounting and optional event timing of pair kernels (nb_api.cu).
+void count_launches(int k);
+void timing_begin(cudaStream_t st);
+void timing_end(cudaStream_t st);
+
+// Pair kernels (nb_pair.cu).  Partial outputs are [n_jc][3][n] (force, vjp)
+// or [n_jc][n] (phi), un-scaled sums over j of the pair terms.
+struct PosF32 {  // split FP32 positions for MODE_SPLIT: hi and lo parts
+  const float *xh, *yh, *zh, *xl, *yl, *zl;
+};
+cudaError_t launch_pair_force(const Plan &pl, int mode, int64_t n, const double *x,
+                              const double *y, const double *z, const double *q,
+                              const PosF32 &pf, double soft2, double *part,
+                              cudaStream_t st);
+cudaError_t launch_pair_phi(const Plan &pl, int64_t n, const double *x, const double *y,
+                            const double *z, const double *q, double charge, double soft2,
+                            double *part, cudaStream_t st);
+cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const double *y,
+                            const double *z, const double *q, const double *lx,
+                            const double *ly, const double *lz, double soft2, double *part,
+                            cudaStream_t st);
+cudaError_t launch_split_positions(int64_t n, const double *x, const double *y,
+                                   const double *z, float *out6, cudaStream_t st);
+
+// Epilogue kernels (nb_integrate.cu).
+struct StateView {
+  int64_t n;
+  double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az;
+  const double *q;
+};
+cudaError_t launch_epi_forces(const Phys &p, const StateView &s, const double *part, int n_jc,
+                              int flags, double t, unsigned *err, cudaStream_t st);
+cudaError_t launch_epi_vjp(const Phys &p, const StateView &s, const double *part, int n_jc,
+                           const double *lx, const double *ly, const double *lz, double *gx,
+                           double *gy, double *gz, int flags, double t, cudaStream_t st);
+cudaError_t launch_drift(const Phys &p, const StateView &s, double *px, double *py, double *pz,
+                         cudaStream_t st);
+// One Verlet epilogue: forces at positions (cx,cy,cz) = r+ (time index snew)
+// -> kick v and a in s; then drift into (nx,ny,nz) if nx != nullptr, else
+// copy r+ into s.x/y/z.
+cudaError_t launch_epi_step(const Phys &p, const StateView &s, const double *cx,
+                            const double *cy, const double *cz, const double *part, int n_jc,
+                            int64_t snew, double *nx, double *ny, double *nz, unsigned *err,
+                            cudaStream_t st);
+// Energies: block partials then one final block; out4 is device memory.
+constexpr int ENERGY_BLOCKS = 128;
+constexpr int ENERGY_THREADS = 256;
+cudaError_t launch_energy(const Phys &p, const StateView &s, const double *phi_part, int n_jc,
+                          double t, double *block_part, double *out4, cudaStream_t st);
+
+}  // namespace nb

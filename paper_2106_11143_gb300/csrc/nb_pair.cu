@@ -1,0 +1,426 @@
+// nb_pair.cu -- the O(N^2) pair kernels of libnb.so (sm_103a).
+//
+// Each kernel evaluates the sum over j of a pair term for the i-particles
+// of one i-tile and the j-particles of one j-chunk (Eq. 1 of the paper;
+// the Sec. III double loop).  Grid: x = i-tile, y = j-chunk.  The j-chunk
+// is streamed through shared memory one block-sized tile at a time; every
+// thread reads the same j entry (a broadcast load) and applies it to the R
+// i-particles it keeps in registers, the GPU analogue of the paper's packed
+// i x j register tile (Sec. VI.A).  The partial sums of each (i-tile,
+// j-chunk) block go to their own slot of `part`; the epilogue kernels add
+// the slots in chunk order, so no atomics are used and the result does not
+// depend on scheduling.
+//
+// 1/sqrt: the paper replaces SQRT+DIV by an approximate reciprocal square
+// root refined by Newton-Raphson (Sec. IV).  Here the seed is the FP32
+// MUFU.RSQ of an FP32 copy of r^2 built with integer ops, and a single
+// third-order refinement is applied directly to r^-3:
+//   Y ~ r2^(-1/2),  e = 1 - r2 Y^2,  r^-3 = Y^3 (1 - e)^(-3/2)
+//                                        ~ Y^3 (1 + 3/2 e + 15/8 e^2),
+// whose truncation error (35/16)|e|^3 < 2^-61 is below FP64 rounding for
+// the |e| < 2^-20.7 the seed guarantees.
+#include <algorithm>
+
+#include "nb_common.cuh"
+
+namespace nb {
+
+// One staged j-particle: position and weight (or lambda), 16-byte aligned so
+// a tile entry is read with two 128-bit shared-memory loads.
+struct __align__(16) D4 {
+  double x, y, z, w;
+};
+__device__ __forceinline__ D4 make_d4(double x, double y, double z, double w) {
+  D4 r;
+  r.x = x; r.y = y; r.z = z; r.w = w;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Pair terms.
+
+// FP64: acc += w_j (r_i - r_j) / (|r_i - r_j|^2 + soft2)^(3/2)
+template <bool QARR>
+__device__ __forceinline__ void pair_f64(double xi, double yi, double zi, const D4 &pj,
+                                         double soft2, double &ax, double &ay, double &az) {
+  const double dx = xi - pj.x;
+  const double dy = yi - pj.y;
+  const double dz = zi - pj.z;
+  const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
+  const double Y = rsqrt_seed_f64(r2);
+  const double Y2 = Y * Y;
+  const double e = fma(-r2, Y2, 1.0);
+  const double Y3 = Y2 * Y;
+  const double p = fma(e, 1.875, 1.5);
+  const double t = Y3 * e;
+  double s = fma(t, p, Y3);
+  if (QARR) s *= pj.w;
+  ax = fma(dx, s, ax);
+  ay = fma(dy, s, ay);
+  az = fma(dz, s, az);
+}
+
+// FP32 bulk shared by the two mixed modes: given the FP32 displacement,
+// acc += w_j d / s^3 with s^-3 = y^3 (1 + 3/2 e), y = MUFU.RSQ(s^2),
+// e = 1 - s^2 y^2 (one first-order correction in FP32).
+template <bool QARR>
+__device__ __forceinline__ void pair_f32_bulk(float fx, float fy, float fz, float qj,
+                                              float soft2f, float &ax, float &ay, float &az) {
+  const float r2 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, soft2f)));
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+  y = (r2 > 0.0f) ? y : 0.0f;
+  const float y2 = y * y;
+  const float e15 = fmaf(-1.5f * r2, y2, 1.5f);
+  const float y3 = y2 * y;
+  float s = fmaf(y3, e15, y3);
+  if (QARR) s *= qj;
+  ax = fmaf(fx, s, ax);
+  ay = fmaf(fy, s, ay);
+  az = fmaf(fz, s, az);
+}
+
+// Adds a tile's FP32 partial to an FP64 accumulator with TwoSum
+// compensation (the error term is kept in c and added at the end).
+__device__ __forceinline__ void flush_tile(float &af, double &ad, double &c) {
+  double s, e;
+  two_sum(ad, f32_to_f64(af), s, e);
+  ad = s;
+  c += e;
+  af = 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Force kernel: part[(jc*3 + c)*n + i] = sum_{j in chunk jc} w_j d_ij^c / s_ij^3.
+template <int MODE, int R, bool QARR>
+__global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
+                                                    const double *__restrict__ x,
+                                                    const double *__restrict__ y,
+                                                    const double *__restrict__ z,
+                                                    const double *__restrict__ q, PosF32 pf,
+                                                    double soft2, double *__restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int B = blockDim.x;
+  const int tid = threadIdx.x;
+  const int64_t ibase = (int64_t)blockIdx.x * B * R + tid;
+  const int64_t jb = (int64_t)blockIdx.y * jchunk;
+  const int64_t je = min(jb + jchunk, n);
+
+  double xi[R], yi[R], zi[R];
+  float xh[R], yh[R], zh[R], xl[R], yl[R], zl[R];
+  double ad[R][3], cd[R][3];
+  float af[R][3];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = min(ibase + (int64_t)r * B, n - 1);
+    if (MODE == MODE_SPLIT) {
+      xh[r] = pf.xh[i]; yh[r] = pf.yh[i]; zh[r] = pf.zh[i];
+      xl[r] = pf.xl[i]; yl[r] = pf.yl[i]; zl[r] = pf.zl[i];
+    } else {
+      xi[r] = x[i]; yi[r] = y[i]; zi[r] = z[i];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { ad[r][c] = 0.0; cd[r][c] = 0.0; af[r][c] = 0.0f; }
+  }
+  const float soft2f = (float)soft2;
+
+  for (int64_t j0 = jb; j0 < je; j0 += B) {
+    __syncthreads();
+    const int64_t j = j0 + tid;
+    if (j < je) {
+      if (MODE == MODE_SPLIT) {
+        float4 *s4 = reinterpret_cast<float4 *>(smem_raw);
+        const float qf = QARR ? (float)q[j] : 0.0f;
+        s4[2 * tid] = make_float4(pf.xh[j], pf.yh[j], pf.zh[j], qf);
+        s4[2 * tid + 1] = make_float4(pf.xl[j], pf.yl[j], pf.zl[j], 0.0f);
+      } else {
+        D4 *s4 = reinterpret_cast<D4 *>(smem_raw);
+        s4[tid] = make_d4(x[j], y[j], z[j], QARR ? q[j] : 0.0);
+      }
+    }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)B, je - j0);
+    if (MODE == MODE_FP64) {
+      const D4 *s4 = reinterpret_cast<const D4 *>(smem_raw);
+#pragma unroll 2
+      for (int k = 0; k < cnt; ++k) {
+        const D4 pj = s4[k];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          pair_f64<QARR>(xi[r], yi[r], zi[r], pj, soft2, ad[r][0], ad[r][1], ad[r][2]);
+      }
+    } else if (MODE == MODE_MIXED) {
+      const D4 *s4 = reinterpret_cast<const D4 *>(smem_raw);
+#pragma unroll 2
+      for (int k = 0; k < cnt; ++k) {
+        const D4 pj = s4[k];
+        const float qf = QARR ? (float)pj.w : 0.0f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float fx = f64_to_f32_rn(xi[r] - pj.x);
+          const float fy = f64_to_f32_rn(yi[r] - pj.y);
+          const float fz = f64_to_f32_rn(zi[r] - pj.z);
+          pair_f32_bulk<QARR>(fx, fy, fz, qf, soft2f, af[r][0], af[r][1], af[r][2]);
+        }
+      }
+    } else {
+      const float4 *s4 = reinterpret_cast<const float4 *>(smem_raw);
+#pragma unroll 4
+      for (int k = 0; k < cnt; ++k) {
+        const float4 ph = s4[2 * k];
+        const float4 pl = s4[2 * k + 1];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float fx = (xh[r] - ph.x) + (xl[r] - pl.x);
+          const float fy = (yh[r] - ph.y) + (yl[r] - pl.y);
+          const float fz = (zh[r] - ph.z) + (zl[r] - pl.z);
+          pair_f32_bulk<QARR>(fx, fy, fz, ph.w, soft2f, af[r][0], af[r][1], af[r][2]);
+        }
+      }
+    }
+    if (MODE != MODE_FP64) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) flush_tile(af[r][c], ad[r][c], cd[r][c]);
+    }
+  }
+
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = ibase + (int64_t)r * B;
+    if (i < n) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        part[((int64_t)blockIdx.y * 3 + c) * n + i] = (MODE == MODE_FP64) ? ad[r][c] : ad[r][c] + cd[r][c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Potential kernel (FP64): part[jc*n + i] = sum_{j in chunk, j != i} w_j / s_ij,
+// 1/s = Y (1 - e)^(-1/2) ~ Y (1 + e/2 + 3/8 e^2).
+template <bool QARR>
+__global__ void __launch_bounds__(256) k_pair_phi(int64_t n, int64_t jchunk,
+                                                  const double *__restrict__ x,
+                                                  const double *__restrict__ y,
+                                                  const double *__restrict__ z,
+                                                  const double *__restrict__ q, double soft2,
+                                                  double *__restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  D4 *s4 = reinterpret_cast<D4 *>(smem_raw);
+  const int B = blockDim.x;
+  const int tid = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * B + tid;
+  const int64_t ic = min(i, n - 1);
+  const int64_t jb = (int64_t)blockIdx.y * jchunk;
+  const int64_t je = min(jb + jchunk, n);
+  const double xi = x[ic], yi = y[ic], zi = z[ic];
+  double acc = 0.0;
+  for (int64_t j0 = jb; j0 < je; j0 += B) {
+    __syncthreads();
+    const int64_t j = j0 + tid;
+    if (j < je) s4[tid] = make_d4(x[j], y[j], z[j], QARR ? q[j] : 1.0);
+    __syncthreads();
+    const int cnt = (int)min((int64_t)B, je - j0);
+    for (int k = 0; k < cnt; ++k) {
+      const D4 pj = s4[k];
+      const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+      const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
+      const double Y = rsqrt_seed_f64(r2);
+      const double e = fma(-r2, Y * Y, 1.0);
+      const double p = fma(e, 0.375, 0.5);
+      double inv = fma(Y * e, p, Y);
+      inv = (j0 + k == ic) ? 0.0 : inv;  // self pair (matters when soft2 > 0)
+      acc = QARR ? fma(pj.w, inv, acc) : acc + inv;
+    }
+  }
+  if (i < n) part[(int64_t)blockIdx.y * n + i] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// VJP kernel (FP64): part[(jc*3+c)*n + i] =
+//   sum_{j in chunk} w_j [ dl^c / s^3 - 3 d^c (d . dl) / s^5 ],  dl = lam_i - lam_j.
+template <bool QARR>
+__global__ void __launch_bounds__(256) k_pair_vjp(int64_t n, int64_t jchunk,
+                                                  const double *__restrict__ x,
+                                                  const double *__restrict__ y,
+                                                  const double *__restrict__ z,
+                                                  const double *__restrict__ q,
+                                                  const double *__restrict__ lx,
+                                                  const double *__restrict__ ly,
+                                                  const double *__restrict__ lz, double soft2,
+                                                  double *__restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  D4 *s4 = reinterpret_cast<D4 *>(smem_raw);
+  const int B = blockDim.x;
+  const int tid = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * B + tid;
+  const int64_t ic = min(i, n - 1);
+  const int64_t jb = (int64_t)blockIdx.y * jchunk;
+  const int64_t je = min(jb + jchunk, n);
+  const double xi = x[ic], yi = y[ic], zi = z[ic];
+  const double mi = lx[ic], ni = ly[ic], oi = lz[ic];
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int64_t j0 = jb; j0 < je; j0 += B) {
+    __syncthreads();
+    const int64_t j = j0 + tid;
+    if (j < je) {
+      s4[2 * tid] = make_d4(x[j], y[j], z[j], QARR ? q[j] : 1.0);
+      s4[2 * tid + 1] = make_d4(lx[j], ly[j], lz[j], 0.0);
+    }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)B, je - j0);
+    for (int k = 0; k < cnt; ++k) {
+      const D4 pj = s4[2 * k];
+      const D4 lj = s4[2 * k + 1];
+      const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+      const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
+      const double Y = rsqrt_seed_f64(r2);
+      const double e = fma(-r2, Y * Y, 1.0);
+      const double p = fma(e, 0.375, 0.5);
+      const double inv = fma(Y * e, p, Y);
+      const double inv2 = inv * inv;
+      double s3 = inv2 * inv;
+      if (QARR) s3 *= pj.w;
+      const double s5 = s3 * inv2;
+      const double ex = mi - lj.x, ey = ni - lj.y, ez = oi - lj.z;
+      const double dot = fma(dx, ex, fma(dy, ey, dz * ez));
+      const double w3 = 3.0 * (dot * s5);
+      gx = fma(ex, s3, gx);
+      gy = fma(ey, s3, gy);
+      gz = fma(ez, s3, gz);
+      gx = fma(-dx, w3, gx);
+      gy = fma(-dy, w3, gy);
+      gz = fma(-dz, w3, gz);
+    }
+  }
+  if (i < n) {
+    part[((int64_t)blockIdx.y * 3 + 0) * n + i] = gx;
+    part[((int64_t)blockIdx.y * 3 + 1) * n + i] = gy;
+    part[((int64_t)blockIdx.y * 3 + 2) * n + i] = gz;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split FP64 positions into FP32 (hi, lo): hi = fl32(x), lo = fl32(x - hi).
+// out6 = [xh | yh | zh | xl | yl | zl], n floats each.
+__global__ void k_split_positions(int64_t n, const double *__restrict__ x,
+                                  const double *__restrict__ y, const double *__restrict__ z,
+                                  float *__restrict__ out6) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v[3] = {x[i], y[i], z[i]};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float h = __double2float_rn(v[c]);
+    out6[c * n + i] = h;
+    out6[(3 + c) * n + i] = __double2float_rn(v[c] - (double)h);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+
+static int round_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+template <int MODE, int R>
+static cudaError_t launch_force_mr(const Plan &pl, int64_t n, const double *x, const double *y,
+                                   const double *z, const double *q, const PosF32 &pf,
+                                   double soft2, double *part, cudaStream_t st) {
+  const dim3 grid(pl.n_it, pl.n_jc);
+  const size_t smem = (MODE == MODE_SPLIT ? 2 * sizeof(float4) : sizeof(D4)) * pl.block;
+  if (q)
+    k_pair_force<MODE, R, true><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, pf, soft2, part);
+  else
+    k_pair_force<MODE, R, false><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, pf, soft2, part);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_force_m(const Plan &pl, int64_t n, const double *x, const double *y,
+                                  const double *z, const double *q, const PosF32 &pf,
+                                  double soft2, double *part, cudaStream_t st) {
+  switch (pl.R) {
+    case 1: return launch_force_mr<MODE, 1>(pl, n, x, y, z, q, pf, soft2, part, st);
+    case 2: return launch_force_mr<MODE, 2>(pl, n, x, y, z, q, pf, soft2, part, st);
+    case 4: return launch_force_mr<MODE, 4>(pl, n, x, y, z, q, pf, soft2, part, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_pair_force(const Plan &pl, int mode, int64_t n, const double *x,
+                              const double *y, const double *z, const double *q,
+                              const PosF32 &pf, double soft2, double *part, cudaStream_t st) {
+  switch (mode) {
+    case MODE_FP64: return launch_force_m<MODE_FP64>(pl, n, x, y, z, q, pf, soft2, part, st);
+    case MODE_MIXED: return launch_force_m<MODE_MIXED>(pl, n, x, y, z, q, pf, soft2, part, st);
+    case MODE_SPLIT: return launch_force_m<MODE_SPLIT>(pl, n, x, y, z, q, pf, soft2, part, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_pair_phi(const Plan &pl, int64_t n, const double *x, const double *y,
+                            const double *z, const double *q, double charge, double soft2,
+                            double *part, cudaStream_t st) {
+  (void)charge;
+  const dim3 grid(pl.n_it, pl.n_jc);
+  const size_t smem = sizeof(D4) * pl.block;
+  if (q)
+    k_pair_phi<true><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, soft2, part);
+  else
+    k_pair_phi<false><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, soft2, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const double *y,
+                            const double *z, const double *q, const double *lx,
+                            const double *ly, const double *lz, double soft2, double *part,
+                            cudaStream_t st) {
+  const dim3 grid(pl.n_it, pl.n_jc);
+  const size_t smem = 2 * sizeof(D4) * pl.block;
+  if (q)
+    k_pair_vjp<true><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, lx, ly, lz, soft2, part);
+  else
+    k_pair_vjp<false><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, lx, ly, lz, soft2, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_positions(int64_t n, const double *x, const double *y, const double *z,
+                                   float *out6, cudaStream_t st) {
+  const int T = 256;
+  k_split_positions<<<round_up(n, T), T, 0, st>>>(n, x, y, z, out6);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Plan: i-tile and j-chunk sizes.  Blocks of one to four warps; enough
+// (i-tile, j-chunk) blocks for about 16 per SM so the last wave is short;
+// j-chunks of at least 4 tiles so the partial-sum traffic stays small.
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+  return sms;
+}
+
+Plan make_plan(int64_t n, int mode, int kind) {
+  Plan pl;
+  pl.block = n >= 8192 ? 128 : (n >= 2048 ? 64 : 32);
+  pl.R = (kind == 0 && mode == MODE_SPLIT && n >= 16384) ? 2 : 1;
+  const int64_t it = (int64_t)pl.block * pl.R;
+  pl.n_it = round_up(n, it);
+  // about 16 blocks per SM for large n; small n keeps at least 8 warps per SM
+  const int64_t target = (int64_t)device_sm_count() * (pl.block == 32 ? 32 : 16);
+  int64_t njc = (target + pl.n_it - 1) / pl.n_it;
+  const int64_t min_tiles = n >= 8192 ? 4 : 1;
+  const int64_t max_jc = std::max<int64_t>(1, n / (min_tiles * (int64_t)pl.block));
+  njc = std::min<int64_t>(std::max<int64_t>(njc, 1), max_jc);
+  int64_t chunk = (n + njc - 1) / njc;
+  chunk = ((chunk + pl.block - 1) / pl.block) * pl.block;
+  pl.jchunk = std::max<int64_t>(chunk, pl.block);
+  pl.n_jc = round_up(n, pl.jchunk);
+  return pl;
+}
+
+}  // namespace nb

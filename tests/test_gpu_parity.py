@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Error measure for forces: the conditioned error per ion
+    e_i = |a_i^gpu - a_i^oracle| / sum_{j != i} |a_ij|,
+(the oracle also returns the sum of the pair-term magnitudes), gated at
+1e-12 for the FP64 path and 1e-6 for the mixed paths.  The plain relative
+error |da|/|a| is ill-conditioned for ions whose pair forces cancel.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2106_11143_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def nb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_11143_gb300 as nbm
+    nbm.lib()
+    return nbm
+
+
+def oparams(orc, phys):
+    return orc.make_params(**phys)
+
+
+def cond_err(gpu, ref, absf):
+    d = np.sqrt(np.sum((np.asarray(gpu) - np.asarray(ref)) ** 2, axis=0))
+    return float(np.max(d / absf))
+
+
+def gpu_forces(nb, phys, pos, q=None, precision="fp64", total=False, vel=None, step=0):
+    sysm = nb.System(pos, vel, q=q, step=step)
+    par = nb.Params.from_phys(phys, precision=precision)
+    nb.forces(par, sysm, total=total)
+    nb.sync_status()
+    return sysm.acc().cpu().numpy()
+
+
+SIZES = [1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 129, 255, 257, 1000, 1024, 2049, 4097, 8191, 9000]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_split"])
+def test_forces_ragged_sizes(nb, orc, precision):
+    phys = W.phys()
+    worst = 0.0
+    for k, n in enumerate(SIZES):
+        pos, _ = W.random_cloud(n, seed=100 + k)
+        g = gpu_forces(nb, phys, pos, precision=precision)
+        if n == 1:
+            assert np.all(g == 0)
+            continue
+        ax, ay, az, _, absf = orc.coulomb(oparams(orc, phys), *pos, want_absf=True)
+        e = cond_err(g, np.stack([ax, ay, az]), absf)
+        worst = max(worst, e)
+        assert e <= TOL[precision], (n, e)
+    print("max conditioned error %s: %.3g" % (precision, worst))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_split"])
+def test_forces_charges_and_softening(nb, orc, precision):
+    rng = np.random.default_rng(7)
+    n = 3001
+    pos, _ = W.random_cloud(n, seed=7)
+    q = W.E_CHARGE * rng.choice([-1.0, 1.0, 2.0], size=n)
+    for soft2 in (0.0, (0.2e-6) ** 2):
+        phys = W.phys(soft2=soft2)
+        g = gpu_forces(nb, phys, pos, q=q, precision=precision)
+        ax, ay, az, _, absf = orc.coulomb(oparams(orc, phys), *pos, q=q, want_absf=True)
+        e = cond_err(g, np.stack([ax, ay, az]), absf)
+        assert e <= TOL[precision], (soft2, e)
+
+
+def test_forces_total_rf_trap_friction(nb, orc):
+    w = W.cloud_rf_16384(n=2000)
+    phys = dict(w["phys"])
+    step = 37
+    g = gpu_forces(nb, phys, w["pos"], vel=w["vel"], total=True, step=step)
+    t = phys["t0"] + step * phys["dt"]
+    ref = np.stack(orc.accel(oparams(orc, phys), t, *w["pos"], *w["vel"]))
+    _, _, _, _, absf = orc.coulomb(oparams(orc, phys), *w["pos"], want_absf=True)
+    scale = absf + np.sqrt(np.sum(ref ** 2, axis=0))
+    assert cond_err(g, ref, scale) <= 1e-12
+
+
+def test_potential_and_energy(nb, orc):
+    for trap in ("harmonic", "rf"):
+        w = W.cloud_harmonic_1024(n=1500) if trap == "harmonic" else W.cloud_rf_16384(n=1500)
+        phys = w["phys"]
+        sysm = nb.System(w["pos"], w["vel"], step=11)
+        par = nb.Params.from_phys(phys)
+        phi = nb.forces(par, sysm, want_phi=True).cpu().numpy()
+        _, _, _, phi_ref, _ = orc.coulomb(oparams(orc, phys), *w["pos"], want_phi=True)
+        assert np.max(np.abs(phi - phi_ref) / phi_ref) <= 1e-12
+        e = nb.energy(par, sysm)
+        e_ref = orc.energy(oparams(orc, phys), 11, *w["pos"], *w["vel"])
+        for k in range(3):
+            assert abs(e[k] - e_ref[k]) <= 1e-12 * abs(e_ref[k]), (trap, k, e[k], e_ref[k])
+
+
+def test_energy_with_softening_and_charges(nb, orc):
+    rng = np.random.default_rng(3)
+    n = 700
+    pos, vel = W.random_cloud(n, seed=31)
+    q = W.E_CHARGE * rng.choice([1.0, 2.0], size=n)
+    phys = W.phys(soft2=(0.3e-6) ** 2, omega=(1e6, 2e6, 3e5))
+    sysm = nb.System(pos, vel, q=q)
+    e = nb.energy(nb.Params.from_phys(phys), sysm)
+    e_ref = orc.energy(oparams(orc, phys), 0, *pos, *vel, q=q)
+    assert np.all(np.abs(e - e_ref) <= 1e-12 * np.abs(e_ref))
+
+
+def test_vjp(nb, orc):
+    rng = np.random.default_rng(5)
+    n = 1500
+    pos, _ = W.random_cloud(n, seed=5)
+    q = W.E_CHARGE * rng.choice([1.0, 2.0], size=n)
+    lam = rng.standard_normal((3, n))
+    phys = W.phys(omega=(6e6, 5e6, 1.2e6))
+    for total in (False, True):
+        sysm = nb.System(pos, q=q)
+        g = nb.forces_vjp(nb.Params.from_phys(phys), sysm, lam, total=total).cpu().numpy()
+        ref = np.stack(orc.forces_vjp(oparams(orc, phys), 0.0, *pos, *lam, q=q, include_trap=total))
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(g - ref)) <= 1e-11 * scale
+
+
+def _oracle_traj(orc, phys, pos, vel, nsteps, reverse=False, q=None, eps=0.0):
+    p = oparams(orc, phys)
+    pos = np.asarray(pos) * (1.0 + eps)
+    ax, ay, az = orc.accel(p, phys["t0"], *pos, *vel, q=q, reverse=reverse)
+    st = dict(x=pos[0], y=pos[1], z=pos[2], vx=vel[0], vy=vel[1], vz=vel[2],
+              ax=ax, ay=ay, az=az, step=0)
+    return orc.run(p, st, nsteps, q=q, reverse=reverse)
+
+
+def _self_divergence(orc, phys, pos, vel, nsteps, ref):
+    """How far two correct FP64 computations of the same trajectory drift
+    apart: the oracle against itself with the j order reversed and with the
+    initial positions moved by one ulp (2^-52 relative).  The compensated
+    oracle sums are order-independent, so the second term dominates."""
+    rev = _oracle_traj(orc, phys, pos, vel, nsteps, reverse=True)
+    ulp = _oracle_traj(orc, phys, pos, vel, nsteps, eps=2.0 ** -52)
+    a = _traj_errs_np(ref, rev)
+    b = _traj_errs_np(ref, ulp)
+    return max(a[0], b[0]), max(a[1], b[1])
+
+
+def _gpu_traj(nb, phys, pos, vel, nsteps, precision="fp64", chunks=1, q=None):
+    sysm = nb.System(pos, vel, q=q)
+    par = nb.Params.from_phys(phys, precision=precision)
+    nb.forces(par, sysm, total=True)
+    for c in range(chunks):
+        nb.step(par, sysm, nsteps // chunks)
+    nb.sync_status()
+    return sysm
+
+
+def _traj_errs(sysm, ref):
+    gp = sysm.pos().cpu().numpy()
+    gv = sysm.vel().cpu().numpy()
+    rp = np.stack([ref["x"], ref["y"], ref["z"]])
+    rv = np.stack([ref["vx"], ref["vy"], ref["vz"]])
+    return np.max(np.abs(gp - rp)), np.max(np.abs(gv - rv))
+
+
+@pytest.mark.parametrize("which", ["harmonic", "rf"])
+def test_trajectory_parity(nb, orc, which):
+    """Trajectories: GPU vs oracle within 10x the oracle's own divergence (see
+    _self_divergence), with a floor of 1e-14 of the cloud size / thermal speed."""
+    if which == "harmonic":
+        w = W.cloud_harmonic_1024()
+        nsteps = 100
+    else:
+        w = W.cloud_rf_16384(n=2048)
+        nsteps = 200
+    phys = w["phys"]
+    ref = _oracle_traj(orc, phys, w["pos"], w["vel"], nsteps)
+    sysm = _gpu_traj(nb, phys, w["pos"], w["vel"], nsteps, chunks=2)
+    assert sysm.step == nsteps
+    dp_self, dv_self = _self_divergence(orc, phys, w["pos"], w["vel"], nsteps, ref)
+    dp, dv = _traj_errs(sysm, ref)
+    L = np.max(np.abs(w["pos"]))
+    V = math.sqrt(W.K_B * 10e-3 / W.MASS_40U)
+    print("%s: gpu dp=%.3g dv=%.3g | oracle self dp=%.3g dv=%.3g" % (which, dp, dv, dp_self, dv_self))
+    assert dp <= max(10 * dp_self, 1e-14 * L)
+    assert dv <= max(10 * dv_self, 1e-14 * V)
+
+
+def _traj_errs_np(a, b):
+    ap = np.stack([a["x"], a["y"], a["z"]]); bp = np.stack([b["x"], b["y"], b["z"]])
+    av = np.stack([a["vx"], a["vy"], a["vz"]]); bv = np.stack([b["vx"], b["vy"], b["vz"]])
+    return np.max(np.abs(ap - bp)), np.max(np.abs(av - bv))
+
+
+def test_trajectory_langevin_noise(nb, orc):
+    """Langevin kicks drawn from the same Philox stream on both sides."""
+    w = W.kz_ensemble(n_inst=1, n_min=300, n_max=300, steps=20000)
+    phys = dict(w["phys"])
+    pos, vel = w["pos"], w["vel"]
+    nsteps = 300
+    ref = _oracle_traj(orc, phys, pos, vel, nsteps)
+    sysm = _gpu_traj(nb, phys, pos, vel, nsteps, chunks=3)
+    dp_self, dv_self = _self_divergence(orc, phys, pos, vel, nsteps, ref)
+    dp, dv = _traj_errs(sysm, ref)
+    V = math.sqrt(W.K_B * 0.5e-3 / W.MASS_40U)
+    print("langevin: gpu dp=%.3g dv=%.3g | self dp=%.3g dv=%.3g" % (dp, dv, dp_self, dv_self))
+    # the kick is ~0.04 V per step: a wrong noise stream would differ by ~V
+    assert dv <= 10 * dv_self + 1e-14 * V
+    assert dp <= 10 * dp_self + 1e-14 * V * phys["dt"] * nsteps
+
+
+def test_step_determinism_and_resume(nb):
+    """Bitwise: two identical runs agree; 2 x 25 steps == 50 steps."""
+    w = W.cloud_harmonic_1024(n=3000)
+    a = _gpu_traj(nb, w["phys"], w["pos"], w["vel"], 50, chunks=1)
+    b = _gpu_traj(nb, w["phys"], w["pos"], w["vel"], 50, chunks=1)
+    c = _gpu_traj(nb, w["phys"], w["pos"], w["vel"], 50, chunks=2)
+    for t in ("x", "vx", "az"):
+        assert torch.equal(getattr(a, t), getattr(b, t))
+        assert torch.equal(getattr(a, t), getattr(c, t))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_split"])
+def test_full_size_sampled(nb, orc, precision):
+    """N = 1e5 (the large-cloud workload, launch configuration of the bench):
+    all forces on the GPU, a sample of 192 ions (spread over tiles and the
+    ragged tail) by the oracle one by one."""
+    w = W.cloud_large()
+    phys = w["phys"]
+    g = gpu_forces(nb, phys, w["pos"], precision=precision)
+    n = w["n"]
+    idx = np.unique(np.concatenate([np.arange(0, 64), np.arange(n - 64, n),
+                                    np.random.default_rng(1).integers(0, n, 64)]))
+    p = oparams(orc, phys)
+    errs = []
+    for i in idx:
+        ax, ay, az, _, absf = orc.coulomb(p, *w["pos"], i0=int(i), i1=int(i) + 1, want_absf=True)
+        d = math.sqrt((g[0, i] - ax[0]) ** 2 + (g[1, i] - ay[0]) ** 2 + (g[2, i] - az[0]) ** 2)
+        errs.append(d / absf[0])
+    print("N=1e5 %s: max conditioned error %.3g" % (precision, max(errs)))
+    assert max(errs) <= TOL[precision]
+    # Newton's third law over all ions (uniform mass: sum a_i = 0)
+    tot = np.abs(g).sum(axis=1)
+    assert np.all(np.abs(g.sum(axis=1)) <= (1e-12 if precision == "fp64" else 1e-6) * tot)
+
+
+def test_argument_errors(nb):
+    par = nb.Params.from_phys(W.phys())
+    sysm = nb.System(np.zeros((3, 4)) + np.arange(4.0) * 1e-6)
+    bad = nb.Params.from_phys(W.phys(), mass=-1.0)
+    with pytest.raises(nb.NBError) as ei:
+        nb.forces(bad, sysm)
+    assert ei.value.status == 1
+    with pytest.raises(nb.NBError):
+        nb.step(par, sysm, -1)
+    empty = nb.System(np.zeros((3, 0)))
+    nb.forces(par, empty)
+    nb.step(par, empty, 5)
+    assert empty.step == 5
+    assert np.all(nb.energy(par, empty) == 0)
+
+
+def test_nonfinite_detected(nb):
+    pos = np.zeros((3, 8)) + np.arange(8.0) * 1e-6
+    pos[0, 3] = np.nan
+    sysm = nb.System(pos)
+    nb.forces(nb.Params.from_phys(W.phys()), sysm)
+    with pytest.raises(nb.NBError) as ei:
+        nb.sync_status()
+    assert ei.value.status == 3
+    nb.sync_status()  # cleared
