@@ -153,6 +153,22 @@ nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys,
                         double *gx, double *gy, double *gz, int flags,
                         void *stream);
 
+/* nb_energy without any device allocation.  The paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc -- cudaMalloc may
+ * synchronise the device, which a latency-bound loop cannot afford, and under
+ * a host framework that owns device memory through its own pool it can fail
+ * or take memory budgeted elsewhere.  Same inputs, outputs and arithmetic as
+ * nb_energy (out[4] in HOST memory; synchronises the stream).  Its scratch is
+ * one fixed 8 MiB device array inside the library, held on every GPU that
+ * loads the library until the process exits; n above what it can hold (about
+ * 1,000,000) is rejected with NB_EINVAL and a message in nb_last_error().
+ * All calls share that array: calls that may overlap on the GPU (other
+ * streams, unordered host threads) race and must be serialised.  The first
+ * call on each device looks up the array's device address with that device
+ * current; make that first call before any stream capture.                 */
+nb_status nb_energy_noalloc(const nb_params *params, const nb_system *sys,
+                            double out[4], void *stream);
+
 /* Synchronises `stream`, then returns and clears its device error word:
  * NB_OK, NB_ENONFINITE or NB_ETIMEOUT (or NB_ECUDA if the stream failed). */
 nb_status nb_sync_status(void *stream);

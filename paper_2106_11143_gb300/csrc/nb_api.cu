@@ -223,6 +223,8 @@ int64_t g_ev_cap = 0, g_ev_used = 0;
 
 void count_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
 
+void record_error(const char *msg) { g_last_error = msg; }
+
 void timing_begin(cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_tmu);
   if (g_ev_used < g_ev_cap) cudaEventRecord(g_ev[2 * g_ev_used], st);

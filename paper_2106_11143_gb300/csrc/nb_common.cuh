@@ -139,6 +139,7 @@ int device_sm_count();
 
 // Launch accounting and optional event timing of pair kernels (nb_api.cu).
 void count_launches(int k);
+void record_error(const char *msg);  // message returned by nb_last_error()
 void timing_begin(cudaStream_t st);
 void timing_end(cudaStream_t st);
 
