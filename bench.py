@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--n", type=int, default=100000, help="ions (default: the 1e5 workload)")
     ap.add_argument("--no-paths", action="store_true", help="skip the secondary precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--workload", default="large", choices=["large", "kz"],
+                    help="large: the N=1e5 headline; kz: the 512-instance ensemble (extra line)")
     ap.add_argument("--profile-forces", action="store_true",
                     help="profiling case: two nb_forces calls per precision at --n, no timing")
     return ap.parse_args()
@@ -342,6 +344,54 @@ def main_reference(args):
     }))
 
 
+def main_kz(args):
+    """Extra line: the Kibble-Zurek ensemble (512 instances, N_k uniform in
+    32..4096, FP64) advanced by K steps in ONE persistent launch of
+    nb_step_batched; value = sum_k N_k^2 x K / device time."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2106_11143_gb300 as nb
+    from paper_2106_11143_gb300 import workloads as W
+    w = W.kz_ensemble()
+    off = w["offsets"]
+    pairs = float(np.sum(np.diff(off).astype(np.float64) ** 2))
+    par = nb.Params.from_phys(w["phys"])
+    sysm = nb.System(w["pos"], w["vel"])
+    nb.init_batched(par, sysm, off)
+    nb.step_batched(par, sysm, off, args.warmup)
+    nb.sync_status()
+    lib = nb.lib()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush.zero_()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    l0 = lib.nb_launch_count()
+    torch.cuda.synchronize()
+    clocks.start()
+    a.record(st)
+    nb.step_batched(par, sysm, off, args.steps)
+    b.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    nb.sync_status()
+    ms = a.elapsed_time(b)
+    sizes = np.diff(off)
+    order, start, mx, mean = nb.plan_batched(off, min(len(sizes), torch.cuda.get_device_properties(0).multi_processor_count))
+    print(json.dumps({
+        "metric": "G pair-interactions/s, FP64 Kibble-Zurek ensemble (extra line, not the headline)",
+        "value": round(pairs * args.steps / (ms / 1e3) / 1e9, 3), "unit": UNIT,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "instances": int(len(sizes)), "ions": int(off[-1]),
+                   "pairs_per_step": pairs, "launches": int(lib.nb_launch_count() - l0),
+                   "lpt_max_over_mean_load": round(mx / mean, 4)},
+        "roofline": {"bound": "alu", "achieved": round(FLOPS_PER_PAIR * pairs * args.steps / (ms / 1e3) / 1e12, 4),
+                     "peak": round(PEAK_TFLOPS["fp64"], 3), "unit": "TFLOP/s",
+                     "frac": round(FLOPS_PER_PAIR * pairs * args.steps / (ms / 1e3) / 1e12 / PEAK_TFLOPS["fp64"], 4)},
+        "clocks": clk}))
+
+
 def profile_forces(args):
     """Small case for ncu: a warm-up pass then a measured pass of nb_forces in
     each precision (pair-kernel launches 1-3 warm up, 4-6 are the ones to capture)."""
@@ -362,6 +412,8 @@ if __name__ == "__main__":
     a = parse()
     if a.profile_forces:
         profile_forces(a)
+    elif a.workload == "kz" and a.impl == "ours":
+        main_kz(a)
     elif a.impl == "reference":
         main_reference(a)
     else:

@@ -153,6 +153,82 @@ nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys,
                         double *gx, double *gy, double *gz, int flags,
                         void *stream);
 
+/* Ensemble of independent systems (a7: e.g. Kibble-Zurek quench
+ * realisations, Sec. I): n_inst instances packed back to back in the SoA
+ * arrays of `packed`; instance k owns ions [offsets[k], offsets[k+1])
+ * (`offsets` in HOST memory, n_inst + 1 entries, offsets[0] = 0,
+ * offsets[n_inst] = packed->n).  Every instance takes nsteps velocity-Verlet
+ * steps exactly as nb_step defines them, with the shared params; instance k
+ * draws its Langevin noise with instance word params->instance + k and ion
+ * index local to the instance, so it reproduces a standalone nb_step run of
+ * that instance.  One persistent kernel launch for all steps (FP64 only,
+ * otherwise NB_ENOTSUP); each instance lives in one thread block's shared
+ * memory, so n_inst <= 1024 and every instance <= 6144 ions (NB_EINVAL
+ * otherwise).  Instances are packed onto the SMs by the longest-processing-
+ * time rule on n^2 (nb_plan_batched).  The launch copies nothing from the
+ * host, so it can be captured in a CUDA graph after one uncaptured call has
+ * set up the stream's error word; a replay repeats the captured step window
+ * (the step counter, hence time and noise counter, is part of the launch).
+ * Advances packed->step by nsteps.                                         */
+nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t *offsets,
+                          nb_system *packed, int64_t nsteps, void *stream);
+
+/* Host-only: the instance-to-block schedule nb_step_batched uses for n_bins
+ * blocks.  order[n_inst] lists the instances grouped by block; block b runs
+ * order[bin_start[b] .. bin_start[b+1]-1].  max_load / mean_load (nullable)
+ * receive the largest and the mean per-block cost (sum of n^2).  No GPU.   */
+nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins,
+                          uint16_t *order, uint16_t *bin_start, double *max_load,
+                          double *mean_load);
+
+/* Launch-shape override (used by the autotuner, paper_2106_11143_gb300/
+ * tune.py).  For kind 0 (force), 1 (potential), 2 (VJP) pair kernels in
+ * `precision` and n in [n_lo, n_hi]: `block` threads per block (32, 64, 128
+ * or 256), `R` ions per thread (1, 2, 4; force kernel only) and about
+ * `blocks_per_sm` (i-tile, j-chunk) blocks per SM.  For kind 3 (the ensemble
+ * kernel): `block` threads per block (multiple of 32, <= 512).  The latest
+ * matching entry wins; block == 0 removes every override.  Results stay
+ * deterministic for a fixed shape; different shapes may differ in the last
+ * bits (summation order), except kind 3, which is shape-independent.     */
+nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n_hi,
+                        int32_t block, int32_t R, int32_t blocks_per_sm);
+
+/* ---- Trajectory loss and its gradient (a9) ------------------------------
+ * Loss of a velocity-Verlet trajectory (Sec. II) of nsteps steps from
+ * (x_0, v_0), a_0 = A(x_0):
+ *   L = E_coulomb(x_T) + E_trap(x_T) + sum_i |x_T,i - target_i|^2
+ * (energies as in nb_energy; the squared distance in m^2, added as plain
+ * numbers), and its exact gradient with respect to x_0, v_0 and the three
+ * trap frequencies by the discrete adjoint (reverse sweep) of the Verlet
+ * map.  Supported: static harmonic trap, gamma = 0, noise_T = 0, FP64 pair
+ * arithmetic (NB_ENOTSUP otherwise).  The forward stores the state (x, v, a)
+ * at steps 0, every, 2*every, ... in `ckpt`; the backward recomputes each
+ * segment from its checkpoint (bitwise identical to the forward) and sweeps
+ * it in reverse, so the result does not depend on `every`. */
+
+/* Doubles needed for the checkpoint buffer: ceil(nsteps/every) * 9 * n
+ * (9 * n when nsteps == 0); -1 on invalid arguments. */
+int64_t nb_traj_ckpt_doubles(int64_t n, int64_t nsteps, int64_t every);
+
+/* Forward: sys holds x_0, v_0 on entry (its a is overwritten with A(x_0));
+ * on return it holds x_T, v_T, a_T and step += nsteps.  ckpt (device,
+ * nb_traj_ckpt_doubles) receives the checkpoints; target: device, 3n doubles
+ * (x block, y block, z block); loss: device, one double.  Asynchronous.    */
+nb_status nb_traj_forward(const nb_params *params, nb_system *sys, int64_t nsteps,
+                          int64_t every, double *ckpt, const double *target, double *loss,
+                          void *stream);
+
+/* Backward: from the checkpoints of nb_traj_forward (same params, nsteps,
+ * every; sys supplies n and q only), writes gscale * dL/dx_0 and
+ * gscale * dL/dv_0 (device, 3n doubles each, SoA blocks) and
+ * gscale * dL/domega (device, 3 doubles).  gscale: device pointer to one
+ * double (the incoming gradient of a caller's chain rule) or NULL for 1.
+ * Asynchronous; uses library scratch of about (every + 20) * 3n doubles.   */
+nb_status nb_traj_backward(const nb_params *params, const nb_system *sys, int64_t nsteps,
+                           int64_t every, const double *ckpt, const double *target,
+                           const double *gscale, double *gx0, double *gv0, double *gomega,
+                           void *stream);
+
 /* nb_energy without any device allocation.  The paper has no counterpart:
  * this serves callers that cannot call cudaMalloc -- cudaMalloc may
  * synchronise the device, which a latency-bound loop cannot afford, and under

@@ -11,11 +11,14 @@ library without the built extension raises.
 from . import workloads  # noqa: F401  (pure numpy, no compute of the method)
 
 _API = ("Params", "System", "forces", "step", "energy", "forces_vjp", "sync_status",
-        "step_batched", "BatchedSystem", "trajectory_loss", "TrajectoryLoss", "lib",
-        "NBError", "PRECISIONS", "release")
+        "step_batched", "init_batched", "plan_batched", "set_tuning", "trajectory_loss", "TrajectoryLoss",
+        "lib", "NBError", "PRECISIONS", "release")
 
 
 def __getattr__(name):
+    if name in ("trajectory_loss", "TrajectoryLoss"):
+        from . import autograd
+        return getattr(autograd, name)
     if name in _API:
         from . import api
         return getattr(api, name)

@@ -73,11 +73,24 @@ def lib():
         L.nb_strerror.restype = C.c_char_p
         L.nb_last_error.restype = C.c_char_p
         L.nb_version.restype = C.c_char_p
+        I64P = C.POINTER(C.c_int64)
+        U16P = C.POINTER(C.c_uint16)
+        L.nb_step_batched.argtypes = [P, C.c_int32, I64P, S, C.c_int64, V]
+        L.nb_plan_batched.argtypes = [C.c_int32, I64P, C.c_int32, U16P, U16P, _dp, _dp]
+        L.nb_set_tuning.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int32,
+                                    C.c_int32, C.c_int32]
+        L.nb_energy_noalloc.argtypes = [P, S, _dp, V]
+        L.nb_traj_ckpt_doubles.argtypes = [C.c_int64, C.c_int64, C.c_int64]
+        L.nb_traj_ckpt_doubles.restype = C.c_int64
+        L.nb_traj_forward.argtypes = [P, S, C.c_int64, C.c_int64, _dp, _dp, _dp, V]
+        L.nb_traj_backward.argtypes = [P, S, C.c_int64, C.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, V]
         L.nb_timing_enable.argtypes = [C.c_int64]
         L.nb_timing_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
         L.nb_launch_count.restype = C.c_uint64
         for f in ("nb_forces", "nb_step", "nb_energy", "nb_forces_vjp", "nb_sync_status",
-                  "nb_release", "nb_timing_enable", "nb_timing_read"):
+                  "nb_release", "nb_timing_enable", "nb_timing_read", "nb_step_batched",
+                  "nb_plan_batched", "nb_set_tuning", "nb_energy_noalloc", "nb_traj_forward",
+                  "nb_traj_backward"):
             getattr(L, f).restype = C.c_int
         _LIB = L
     return _LIB
@@ -179,6 +192,16 @@ class System:
         s.step = self.step
         return s
 
+    def view(self, i0, i1):
+        """A System sharing memory with ions [i0, i1) of this one."""
+        v = System.__new__(System)
+        v.n = int(i1 - i0)
+        for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
+            setattr(v, k, getattr(self, k)[i0:i1])
+        v.q = None if self.q is None else self.q[i0:i1]
+        v.step = self.step
+        return v
+
     def pos(self):
         return torch.stack([self.x, self.y, self.z])
 
@@ -227,6 +250,54 @@ def forces_vjp(params, system, lam, total=False, stream=None):
                                NB_ACC_TOTAL if total else NB_ACC_COULOMB, _stream(stream)),
            "nb_forces_vjp")
     return g
+
+
+def _offsets(offsets):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    return off, off.ctypes.data_as(C.POINTER(C.c_int64))
+
+
+def step_batched(params, system, offsets, nsteps, stream=None):
+    """nb_step_batched: every instance [offsets[k], offsets[k+1]) of the packed
+    system takes nsteps velocity-Verlet steps (one persistent launch)."""
+    off, offp = _offsets(offsets)
+    s = system.to_c()
+    _check(lib().nb_step_batched(C.byref(params.to_c()), len(off) - 1, offp, C.byref(s),
+                                 int(nsteps), _stream(stream)), "nb_step_batched")
+    system.step = s.step
+
+
+def init_batched(params, system, offsets, stream=None):
+    """Set the Verlet-state acceleration of every instance of a packed ensemble
+    (nb_forces with NB_ACC_TOTAL on each instance's own ions)."""
+    off = np.asarray(offsets, dtype=np.int64)
+    for k in range(len(off) - 1):
+        if off[k + 1] > off[k]:
+            forces(params, system.view(int(off[k]), int(off[k + 1])), total=True, stream=stream)
+
+
+def plan_batched(offsets, n_bins):
+    """nb_plan_batched: (order, bin_start, max_load, mean_load) of the ensemble schedule."""
+    off, offp = _offsets(offsets)
+    n_inst = len(off) - 1
+    order = np.zeros(max(n_inst, 1), dtype=np.uint16)
+    start = np.zeros(n_bins + 1, dtype=np.uint16)
+    mx, mean = C.c_double(), C.c_double()
+    _check(lib().nb_plan_batched(n_inst, offp, int(n_bins),
+                                 order.ctypes.data_as(C.POINTER(C.c_uint16)),
+                                 start.ctypes.data_as(C.POINTER(C.c_uint16)),
+                                 C.byref(mx), C.byref(mean)), "nb_plan_batched")
+    return order[:n_inst], start, mx.value, mean.value
+
+
+KINDS = {"force": 0, "potential": 1, "vjp": 2, "ensemble": 3}
+
+
+def set_tuning(kind, precision, n_lo, n_hi, block, R=1, blocks_per_sm=16):
+    """nb_set_tuning: launch-shape override (block = 0 clears all)."""
+    _check(lib().nb_set_tuning(KINDS[kind] if isinstance(kind, str) else int(kind),
+                               PRECISIONS[precision], int(n_lo), int(n_hi), int(block), int(R),
+                               int(blocks_per_sm)), "nb_set_tuning")
 
 
 def sync_status(stream=None):

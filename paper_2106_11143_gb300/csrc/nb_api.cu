@@ -6,6 +6,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <array>
 #include <atomic>
 #include <map>
 #include <vector>
@@ -382,6 +384,251 @@ nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys, const dou
   NB_CUDA_TRY(launch_pair_vjp(pl, n, sys->x, sys->y, sys->z, sys->q, lx, ly, lz, params->soft2, part, st));
   NB_CUDA_TRY(launch_epi_vjp(p, v, part, pl.n_jc, lx, ly, lz, gx, gy, gz, flags, t, st));
   count_launches(2);
+  return NB_OK;
+}
+
+nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t *offsets,
+                          nb_system *packed, int64_t nsteps, void *stream) {
+  NB_TRY(check_params(params));
+  NB_TRY(check_system(packed, true, true));
+  if (params->precision != NB_FP64) return fail(NB_ENOTSUP, "the ensemble kernel is FP64 only");
+  if (nsteps < 0) return fail(NB_EINVAL, "nsteps must be >= 0");
+  if (!(params->dt > 0.0)) return fail(NB_EINVAL, "dt must be > 0");
+  if (n_inst < 0 || n_inst > BATCH_LIMIT_INST)
+    return fail(NB_EINVAL, "n_inst must be in [0, %d]", BATCH_LIMIT_INST);
+  if (n_inst > 0 && !offsets) return fail(NB_EINVAL, "offsets is NULL");
+  if (n_inst > 0) {
+    if (offsets[0] != 0 || offsets[n_inst] != packed->n)
+      return fail(NB_EINVAL, "offsets must start at 0 and end at n");
+    for (int k = 0; k < n_inst; ++k) {
+      const int64_t m = offsets[k + 1] - offsets[k];
+      if (m < 0) return fail(NB_EINVAL, "offsets must be non-decreasing");
+      if (m > BATCH_LIMIT_N)
+        return fail(NB_EINVAL, "instance %d has %lld ions, above the ensemble limit %d", k,
+                    (long long)m, BATCH_LIMIT_N);
+    }
+  }
+  if (n_inst == 0 || packed->n == 0 || nsteps == 0) {
+    packed->step += nsteps;
+    return NB_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena *a = nullptr;
+  NB_TRY(get_arena(st, 256, &a));
+  int threads = 512, R = 1, bps = 1;
+  tuning_lookup(3, NB_FP64, packed->n, &threads, &R, &bps);
+  const int n_bins = std::min(n_inst, device_sm_count());
+  NB_CUDA_TRY(launch_batched(to_phys(params), to_view(packed), n_inst, offsets, n_bins, threads,
+                             packed->step, nsteps, a->err, st));
+  count_launches(1);
+  packed->step += nsteps;
+  return NB_OK;
+}
+
+nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins,
+                          uint16_t *order, uint16_t *bin_start, double *max_load,
+                          double *mean_load) {
+  if (n_inst < 0 || n_inst > BATCH_LIMIT_INST || n_bins < 1 || n_bins > BATCH_LIMIT_INST)
+    return fail(NB_EINVAL, "n_inst must be in [0, %d] and n_bins in [1, %d]", BATCH_LIMIT_INST,
+                BATCH_LIMIT_INST);
+  if (!offsets || !order || !bin_start) return fail(NB_EINVAL, "NULL argument");
+  for (int k = 0; k < n_inst; ++k)
+    if (offsets[k + 1] < offsets[k]) return fail(NB_EINVAL, "offsets must be non-decreasing");
+  batched_plan(n_inst, offsets, n_bins, order, bin_start, max_load, mean_load);
+  return NB_OK;
+}
+
+nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n_hi, int32_t block,
+                        int32_t R, int32_t blocks_per_sm) {
+  if (block == 0) {
+    tuning_clear();
+    return NB_OK;
+  }
+  if (kind < 0 || kind > 3) return fail(NB_EINVAL, "kind must be 0..3");
+  if (precision < NB_FP64 || precision > NB_MIXED_SPLIT) return fail(NB_EINVAL, "bad precision");
+  if (n_lo < 0 || n_hi < n_lo) return fail(NB_EINVAL, "bad n range");
+  if (kind == 3) {
+    if (block < 32 || block > 512 || block % 32) return fail(NB_EINVAL, "block must be 32..512, a multiple of 32");
+  } else {
+    if (block != 32 && block != 64 && block != 128 && block != 256)
+      return fail(NB_EINVAL, "block must be 32, 64, 128 or 256");
+    if (R != 1 && R != 2 && R != 4) return fail(NB_EINVAL, "R must be 1, 2 or 4");
+    if (kind != 0 && R != 1) return fail(NB_EINVAL, "R > 1 is for the force kernel only");
+    if (blocks_per_sm < 1 || blocks_per_sm > 256) return fail(NB_EINVAL, "blocks_per_sm must be 1..256");
+  }
+  tuning_set(kind, precision, n_lo, n_hi, block, R, blocks_per_sm);
+  return NB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Trajectory loss and adjoint gradient (static harmonic trap, no friction or
+// noise, FP64 pair arithmetic).
+
+namespace nb {
+namespace {
+
+nb_status check_adjoint(const nb_params *p) {
+  NB_TRY(check_params(p));
+  if (p->trap != NB_TRAP_HARMONIC || p->gamma != 0.0 || p->noise_T != 0.0 ||
+      p->omega_rate[0] != 0.0 || p->omega_rate[1] != 0.0 || p->omega_rate[2] != 0.0)
+    return fail(NB_ENOTSUP, "the trajectory adjoint supports the static harmonic trap without friction or noise");
+  if (p->precision != NB_FP64) return fail(NB_ENOTSUP, "the trajectory adjoint is FP64 only");
+  if (!(p->dt > 0.0)) return fail(NB_EINVAL, "dt must be > 0");
+  return NB_OK;
+}
+
+int64_t n_segments(int64_t nsteps, int64_t every) {
+  return nsteps == 0 ? 1 : (nsteps + every - 1) / every;
+}
+
+}  // namespace
+}  // namespace nb
+
+extern "C" int64_t nb_traj_ckpt_doubles(int64_t n, int64_t nsteps, int64_t every) {
+  if (n < 0 || nsteps < 0 || every < 1) return -1;
+  return n_segments(nsteps, every) * 9 * n;
+}
+
+extern "C" nb_status nb_traj_forward(const nb_params *params, nb_system *sys, int64_t nsteps,
+                                     int64_t every, double *ckpt, const double *target, double *loss,
+                                     void *stream) {
+  NB_TRY(check_adjoint(params));
+  NB_TRY(check_system(sys, true, true));
+  if (nsteps < 0 || every < 1) return fail(NB_EINVAL, "nsteps must be >= 0 and every >= 1");
+  const int64_t n = sys->n;
+  if (n == 0) return fail(NB_EINVAL, "the trajectory loss needs n >= 1");
+  NB_TRY(check_array(ckpt, "ckpt"));
+  NB_TRY(check_array(target, "target"));
+  NB_TRY(check_array(loss, "loss"));
+  cudaStream_t st = (cudaStream_t)stream;
+  NB_TRY(nb_forces(params, sys, nullptr, NB_ACC_TOTAL, stream));
+  const int64_t S = n_segments(nsteps, every);
+  const size_t N8 = (size_t)n * sizeof(double);
+  for (int64_t seg = 0; seg < S; ++seg) {
+    double *c = ckpt + (size_t)seg * 9 * n;
+    double *src[9] = {sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz, sys->ax, sys->ay, sys->az};
+    for (int k = 0; k < 9; ++k)
+      NB_CUDA_TRY(cudaMemcpyAsync(c + (size_t)k * n, src[k], N8, cudaMemcpyDeviceToDevice, st));
+    const int64_t len = std::min(every, nsteps - seg * every);
+    if (len > 0) NB_TRY(nb_step(params, sys, len, stream));
+  }
+  const Plan plp = make_plan(n, MODE_FP64, 1);
+  Carver need;
+  need.take<double>((size_t)plp.n_jc * n);
+  need.take<double>(ADJ_PART_BLOCKS);
+  Arena *a = nullptr;
+  NB_TRY(get_arena(st, need.off + 256, &a));
+  Carver cv;
+  cv.base = a->buf;
+  double *ppart = cv.take<double>((size_t)plp.n_jc * n);
+  double *bpart = cv.take<double>(ADJ_PART_BLOCKS);
+  const double *xT[3] = {sys->x, sys->y, sys->z};
+  const double *tg[3] = {target, target + n, target + 2 * n};
+  NB_CUDA_TRY(launch_pair_phi(plp, n, sys->x, sys->y, sys->z, sys->q, params->charge, params->soft2, ppart, st));
+  NB_CUDA_TRY(launch_loss(to_phys(params), n, sys->q, xT, tg, ppart, plp.n_jc, bpart, loss, st));
+  count_launches(3);
+  return NB_OK;
+}
+
+extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *sys, int64_t nsteps,
+                                      int64_t every, const double *ckpt, const double *target,
+                                      const double *gscale, double *gx0, double *gv0, double *gomega,
+                                      void *stream) {
+  NB_TRY(check_adjoint(params));
+  if (!sys) return fail(NB_EINVAL, "system is NULL");
+  if (nsteps < 0 || every < 1) return fail(NB_EINVAL, "nsteps must be >= 0 and every >= 1");
+  const int64_t n = sys->n;
+  if (n < 1) return fail(NB_EINVAL, "the trajectory loss needs n >= 1");
+  if (sys->q && !aligned8(sys->q)) return fail(NB_EINVAL, "q is not 8-byte aligned");
+  NB_TRY(check_array(ckpt, "ckpt"));
+  NB_TRY(check_array(target, "target"));
+  NB_TRY(check_array(gx0, "gx0"));
+  NB_TRY(check_array(gv0, "gv0"));
+  NB_TRY(check_array(gomega, "gomega"));
+  if (gscale && !aligned8(gscale)) return fail(NB_EINVAL, "gscale is not 8-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  const Plan pl = make_plan(n, MODE_FP64, 0);
+  const Plan plv = make_plan(n, MODE_FP64, 2);
+  const int64_t S = n_segments(nsteps, every);
+  const int64_t slots = std::min(every, std::max<int64_t>(nsteps, 1)) + 2;
+  Carver need;
+  need.take<double>((size_t)slots * 3 * n);
+  need.take<double>(18 * (size_t)n);
+  need.take<double>((size_t)pl.n_jc * 3 * n);
+  need.take<double>((size_t)plv.n_jc * 3 * n);
+  need.take<double>(3 * ADJ_PART_BLOCKS);
+  Arena *a = nullptr;
+  NB_TRY(get_arena(st, need.off + 256, &a));
+  Carver cv;
+  cv.base = a->buf;
+  double *segbuf = cv.take<double>((size_t)slots * 3 * n);
+  double *st18 = cv.take<double>(18 * (size_t)n);
+  double *fpart = cv.take<double>((size_t)pl.n_jc * 3 * n);
+  double *vpart = cv.take<double>((size_t)plv.n_jc * 3 * n);
+  double *bpart = cv.take<double>(3 * ADJ_PART_BLOCKS);
+  auto arr3 = [&](double *base) { return std::array<double *, 3>{base, base + n, base + 2 * n}; };
+  const auto v3 = arr3(st18), a3 = arr3(st18 + 3 * n), xb = arr3(st18 + 6 * n), vb = arr3(st18 + 9 * n),
+             ab = arr3(st18 + 12 * n), wacc = arr3(st18 + 15 * n);
+  auto slot = [&](int64_t k) { return arr3(segbuf + (size_t)k * 3 * n); };
+  const double *tg[3] = {target, target + n, target + 2 * n};
+  const Phys p = to_phys(params);
+  const size_t N8 = (size_t)n * sizeof(double);
+  PosF32 nopf{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  for (int64_t seg = S - 1; seg >= 0; --seg) {
+    const int64_t start = seg * every;
+    const int64_t len = std::min(every, nsteps - start);
+    const double *c = ckpt + (size_t)seg * 9 * n;
+    const auto s0 = slot(0);
+    for (int k = 0; k < 3; ++k) {
+      NB_CUDA_TRY(cudaMemcpyAsync(s0[k], c + (size_t)k * n, N8, cudaMemcpyDeviceToDevice, st));
+      NB_CUDA_TRY(cudaMemcpyAsync(v3[k], c + (size_t)(3 + k) * n, N8, cudaMemcpyDeviceToDevice, st));
+      NB_CUDA_TRY(cudaMemcpyAsync(a3[k], c + (size_t)(6 + k) * n, N8, cudaMemcpyDeviceToDevice, st));
+    }
+    // recompute the segment from the checkpointed state (x, v, a): positions of
+    // steps start .. start+len into slots 0 .. len, bitwise as in the forward
+    StateView sv;
+    sv.n = n;
+    sv.x = s0[0]; sv.y = s0[1]; sv.z = s0[2];
+    sv.vx = v3[0]; sv.vy = v3[1]; sv.vz = v3[2];
+    sv.ax = a3[0]; sv.ay = a3[1]; sv.az = a3[2];
+    sv.q = sys->q;
+    if (len > 0) {
+      const auto s1 = slot(1);
+      NB_CUDA_TRY(launch_drift(p, sv, s1[0], s1[1], s1[2], st));
+      count_launches(1);
+      for (int64_t m = 0; m < len; ++m) {
+        const auto P = slot(m + 1), Nx = slot(m + 2);
+        NB_CUDA_TRY(launch_pair_force(pl, MODE_FP64, n, P[0], P[1], P[2], sys->q, nopf, params->soft2, fpart, st));
+        NB_CUDA_TRY(launch_epi_step(p, sv, P[0], P[1], P[2], fpart, pl.n_jc, start + m + 1, Nx[0], Nx[1], Nx[2],
+                                    a->err, st));
+        count_launches(2);
+      }
+    }
+    if (seg == S - 1) {
+      const auto sT = slot(len);
+      const double *xT[3] = {sT[0], sT[1], sT[2]};
+      const double *aT[3] = {a3[0], a3[1], a3[2]};
+      NB_CUDA_TRY(launch_adj_init(p, n, xT, aT, tg, xb.data(), vb.data(), ab.data(), wacc.data(), st));
+      count_launches(1);
+    }
+    // reverse sweep over the segment
+    for (int64_t m = len - 1; m >= 0; --m) {
+      const auto X = slot(m + 1);
+      NB_CUDA_TRY(launch_pair_vjp(plv, n, X[0], X[1], X[2], sys->q, ab[0], ab[1], ab[2], params->soft2, vpart, st));
+      const double *xc[3] = {X[0], X[1], X[2]};
+      NB_CUDA_TRY(launch_adj_epi(p, n, sys->q, xc, vpart, plv.n_jc, xb.data(), vb.data(), ab.data(),
+                                 wacc.data(), 0, (start + m) >= 1 ? 1 : 0, st));
+      count_launches(2);
+    }
+  }
+  // x_0 term: J(x_0)^T ab_0 (slot 0 holds x_0 after segment 0's recompute)
+  const auto X0 = slot(0);
+  NB_CUDA_TRY(launch_pair_vjp(plv, n, X0[0], X0[1], X0[2], sys->q, ab[0], ab[1], ab[2], params->soft2, vpart, st));
+  const double *x0c[3] = {X0[0], X0[1], X0[2]};
+  NB_CUDA_TRY(launch_adj_epi(p, n, sys->q, x0c, vpart, plv.n_jc, xb.data(), vb.data(), ab.data(), wacc.data(),
+                             1, 0, st));
+  NB_CUDA_TRY(launch_adj_out(n, xb.data(), vb.data(), wacc.data(), gscale, gx0, gv0, gomega, bpart, st));
+  count_launches(4);
   return NB_OK;
 }
 

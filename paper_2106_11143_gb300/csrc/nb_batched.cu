@@ -1,0 +1,241 @@
+// nb_batched.cu -- persistent velocity-Verlet kernel for an ensemble of
+// independent ion systems of uneven size (e.g. Kibble-Zurek quench
+// realisations, Sec. I of the paper: many independent numerical experiments
+// for defect statistics).
+//
+// One launch advances every instance by nsteps.  Each instance belongs to
+// exactly one CTA, which keeps the instance's positions (and charges) in
+// shared memory for the whole run, so no CTA ever waits on another CTA.
+// Per step the CTA runs: drift of its ions, __syncthreads, the all-pairs
+// FP64 Coulomb sum (the same pair term as the single-system kernel) and the
+// kick/trap/friction/Langevin update of each ion, __syncthreads.  Velocities
+// and accelerations stay in global memory (L2-resident).
+//
+// Load balance: instances are packed onto at most one CTA per SM by the
+// longest-processing-time rule on N^2 (host side, nb_plan_batched); each
+// CTA runs its instances one after another.  The schedule is passed to the
+// kernel by value (__grid_constant__), so a launch needs no host-to-device
+// copy and can be captured in a CUDA graph.
+//
+// The arithmetic of an ion depends only on its instance (the j order is
+// 0..n-1, accumulation sequential per ion), not on the schedule or the block
+// size, so results are bitwise reproducible.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "nb_common.cuh"
+
+namespace nb {
+
+struct __align__(16) BD4 {
+  double x, y, z, w;
+};
+
+constexpr int BATCH_MAX_INST = 1024;
+constexpr int BATCH_MAX_BINS = 1024;
+constexpr int BATCH_MAX_N = 6144;  // ions per instance: 32 B each in shared memory (192 KB)
+
+struct BatchSched {
+  int n_inst;
+  int n_bins;
+  int off[BATCH_MAX_INST + 1];                      // ion offsets of the instances
+  unsigned short order[BATCH_MAX_INST];             // instances, grouped by bin
+  unsigned short bin_start[BATCH_MAX_BINS + 1];     // bin b = order[bin_start[b] .. bin_start[b+1])
+};
+
+// FP64 pair term, identical arithmetic to the single-system force kernel.
+template <bool QARR>
+__device__ __forceinline__ void bpair(double xi, double yi, double zi, const BD4 &pj, double soft2,
+                                      double &ax, double &ay, double &az) {
+  const double dx = xi - pj.x;
+  const double dy = yi - pj.y;
+  const double dz = zi - pj.z;
+  const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
+  double s = rinv3_f64(r2);
+  if (QARR) s *= pj.w;
+  ax = fma(dx, s, ax);
+  ay = fma(dy, s, ay);
+  az = fma(dz, s, az);
+}
+
+// Philox4x32-10 and Box-Muller as in the single-system epilogue.
+__device__ __forceinline__ void bphilox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+__device__ __forceinline__ void bnormals3(unsigned long long seed, unsigned instance, int64_t step,
+                                          int64_t ion, double out[3]) {
+  uint32_t c[4] = {(uint32_t)ion, (uint32_t)((uint64_t)step & 0xffffffffu),
+                   (uint32_t)((uint64_t)step >> 32), instance};
+  bphilox(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+  const double s = 2.3283064365386963e-10;
+  const double u0 = ((double)c[0] + 0.5) * s, u1 = ((double)c[1] + 0.5) * s;
+  const double u2 = ((double)c[2] + 0.5) * s, u3 = ((double)c[3] + 0.5) * s;
+  const double m0 = sqrt(-2.0 * log(u0)), m1 = sqrt(-2.0 * log(u2));
+  double s1, c1, s3, c3;
+  sincospi(2.0 * u1, &s1, &c1);
+  sincospi(2.0 * u3, &s3, &c3);
+  out[0] = m0 * c1;
+  out[1] = m0 * s1;
+  out[2] = m1 * c3;
+}
+
+template <bool QARR>
+__global__ void __launch_bounds__(512) k_batched(Phys p, StateView s,
+                                                  const __grid_constant__ BatchSched sch,
+                                                  int64_t step0, int64_t nsteps, unsigned *err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BD4 *sp = reinterpret_cast<BD4 *>(smem_raw);
+  const int T = blockDim.x;
+  const int tid = threadIdx.x;
+  const double dt = p.dt, hdt2 = 0.5 * dt * dt;
+  const double cfr = p.gamma * dt / (2.0 * p.mass), g = p.gamma / p.mass;
+  const double sig = p.noise_T > 0.0 ? sqrt(2.0 * p.gamma * KB * p.noise_T * dt) / p.mass : 0.0;
+  const double pref_u = p.k_coulomb * p.charge * p.charge / p.mass;
+  bool bad = false;
+
+  for (int kk = sch.bin_start[blockIdx.x]; kk < sch.bin_start[blockIdx.x + 1]; ++kk) {
+    const int inst = sch.order[kk];
+    const int64_t i0 = sch.off[inst];
+    const int n = sch.off[inst + 1] - sch.off[inst];
+    const unsigned inst_id = p.instance + (unsigned)inst;
+    __syncthreads();  // the previous instance is done with shared memory
+    for (int i = tid; i < n; i += T) {
+      BD4 r;
+      r.x = s.x[i0 + i]; r.y = s.y[i0 + i]; r.z = s.z[i0 + i];
+      r.w = QARR ? s.q[i0 + i] : 0.0;
+      sp[i] = r;
+    }
+    __syncthreads();
+    for (int64_t st = 0; st < nsteps; ++st) {
+      const int64_t snew = step0 + st + 1;
+      const double t = p.t0 + (double)snew * dt;
+      // drift: r+ = r + v dt + a dt^2/2 (each thread its own ions)
+      for (int i = tid; i < n; i += T) {
+        BD4 r = sp[i];
+        r.x = r.x + s.vx[i0 + i] * dt + hdt2 * s.ax[i0 + i];
+        r.y = r.y + s.vy[i0 + i] * dt + hdt2 * s.ay[i0 + i];
+        r.z = r.z + s.vz[i0 + i] * dt + hdt2 * s.az[i0 + i];
+        sp[i] = r;
+      }
+      __syncthreads();
+      // forces at r+ and the kick
+      for (int ib = 0; ib < n; ib += T) {
+        const int i = ib + tid;
+        const BD4 ri = sp[min(i, n - 1)];
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 2
+        for (int j = 0; j < n; ++j) bpair<QARR>(ri.x, ri.y, ri.z, sp[j], p.soft2, a0, a1, a2);
+        if (i < n) {
+          const int64_t gi = i0 + i;
+          const double pref = QARR ? p.k_coulomb * ri.w / p.mass : pref_u;
+          double tr[3];
+          trap_accel(p, t, ri.x, ri.y, ri.z, tr[0], tr[1], tr[2]);
+          double xi[3] = {0.0, 0.0, 0.0};
+          if (sig > 0.0) bnormals3(p.seed, inst_id, snew, i, xi);
+          const double acc[3] = {a0, a1, a2};
+          double *vs[3] = {s.vx, s.vy, s.vz};
+          double *as[3] = {s.ax, s.ay, s.az};
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const double u = pref * acc[k] + tr[k];
+            double v = (vs[k][gi] + 0.5 * dt * (as[k][gi] + u)) / (1.0 + cfr);
+            v += sig * xi[k];
+            const double a = u - g * v;
+            vs[k][gi] = v;
+            as[k][gi] = a;
+            bad |= not_finite(v) || not_finite(a);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < n; i += T) {
+      s.x[i0 + i] = sp[i].x;
+      s.y[i0 + i] = sp[i].y;
+      s.z[i0 + i] = sp[i].z;
+    }
+  }
+  if (bad) atomicOr(err, ERR_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
+// Longest-processing-time packing of instances (cost n^2) onto n_bins bins:
+// instances in decreasing cost (ties by index) go to the currently lightest
+// bin (ties by bin index).  Deterministic.
+int batched_plan(int n_inst, const int64_t *offsets, int n_bins, unsigned short *order,
+                 unsigned short *bin_start, double *max_load, double *mean_load) {
+  std::vector<int> idx(n_inst);
+  for (int k = 0; k < n_inst; ++k) idx[k] = k;
+  auto cost = [&](int k) { const double m = (double)(offsets[k + 1] - offsets[k]); return m * m; };
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  std::vector<double> load(n_bins, 0.0);
+  std::vector<std::vector<int>> bins(n_bins);
+  for (int k : idx) {
+    int best = 0;
+    for (int b = 1; b < n_bins; ++b)
+      if (load[b] < load[best]) best = b;
+    load[best] += cost(k);
+    bins[best].push_back(k);
+  }
+  int pos = 0;
+  double mx = 0.0, sum = 0.0;
+  for (int b = 0; b < n_bins; ++b) {
+    bin_start[b] = (unsigned short)pos;
+    for (int k : bins[b]) order[pos++] = (unsigned short)k;
+    mx = std::max(mx, load[b]);
+    sum += load[b];
+  }
+  bin_start[n_bins] = (unsigned short)pos;
+  if (max_load) *max_load = mx;
+  if (mean_load) *mean_load = n_bins ? sum / n_bins : 0.0;
+  return pos;
+}
+
+cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const int64_t *offsets,
+                           int n_bins, int threads, int64_t step0, int64_t nsteps, unsigned *err,
+                           cudaStream_t st) {
+  BatchSched sch;
+  sch.n_inst = n_inst;
+  sch.n_bins = n_bins;
+  int maxn = 0;
+  for (int k = 0; k <= n_inst; ++k) sch.off[k] = (int)offsets[k];
+  for (int k = 0; k < n_inst; ++k) maxn = std::max(maxn, (int)(offsets[k + 1] - offsets[k]));
+  batched_plan(n_inst, offsets, n_bins, sch.order, sch.bin_start, nullptr, nullptr);
+  // At least 120 KB of shared memory per CTA, so no SM holds two bins: each
+  // bin then owns one SM, which is what the LPT packing assumes.
+  const size_t smem = std::max((size_t)std::max(maxn, 1) * sizeof(BD4), (size_t)120 * 1024);
+  static std::mutex mu;
+  static bool attr_done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_done[dev]) {
+      const int lim = 200 * 1024;
+      e = cudaFuncSetAttribute(k_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e != cudaSuccess) return e;
+      attr_done[dev] = true;
+    }
+  }
+  if (s.q)
+    k_batched<true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
+  else
+    k_batched<false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
+  return cudaGetLastError();
+}
+
+}  // namespace nb

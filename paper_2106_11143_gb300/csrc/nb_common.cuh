@@ -50,6 +50,48 @@ __device__ __forceinline__ double rsqrt_seed_f64(double r2) {
   return (e == 0) ? 0.0 : __hiloint2double(yhi, ylo);
 }
 
+// r2^(-3/2) for an FP64 r2 >= 0 with three FP64 instructions.
+// r2 = 2^(2k) r2s, r2s in [1, 4), is split by integer ops into FP32 parts
+// h (the top 24 significand bits) and l (the next 29 bits, rounded to 24):
+// r2s = h + l up to 2^-47 relative.  With y = MUFU.RSQ(h) and the exact
+// square y^2 = y2 + y2e (FMA), the Newton residual e = 1 - r2s y^2 is formed
+// in FP32 from the five products, each of which is computed exactly inside an
+// FFMA; the only roundings are of values near |e| < 2^-20, so e is accurate
+// to about 2^-44 absolute.  Then r2s^(-3/2) = y^3 (1 - e)^(-3/2) =
+// y^3 (1 + c), c = 3/2 e + 15/8 e^2 (truncation (35/16)|e|^3 < 2^-60), and
+// the FP64 part is Y = y 2^-k, Y^3 (1 + c) = fma(Y^3, c, Y^3).
+// Relative error <= ~2^-42 (worst case), ~2^-45 typical.
+// r2 == 0 or subnormal returns 0 (the pair then contributes nothing).
+__device__ __forceinline__ double rinv3_f64(double r2) {
+  const int hi = __double2hiint(r2);
+  const unsigned lo = (unsigned)__double2loint(r2);
+  const int e = hi >> 20;
+  const int k = (e - 1023) >> 1;
+  const unsigned fs = __funnelshift_l(lo, (unsigned)hi, 3);
+  const bool odd = (e & 1) != 0;  // e - 1023 even: r2s in [1, 2)
+  const float h = __uint_as_float((fs & 0x007fffffu) | (odd ? 0x3f800000u : 0x40000000u));
+  const float l = __uint2float_rn(lo & 0x1fffffffu) * (odd ? 0x1p-52f : 0x1p-51f);
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(h));
+  const float y2 = y * y;
+  const float y2e = fmaf(y, y, -y2);
+  float r = fmaf(-h, y2, 1.0f);
+  r = fmaf(-h, y2e, r);
+  r = fmaf(-l, y2, r);
+  const float c = r * fmaf(r, 1.875f, 1.5f);
+  const unsigned yb = __float_as_uint(y);
+  const int yhi = (int)(yb >> 3) + ((896 - k) << 20);
+  const int ylo = (int)(yb << 29);
+  const double Y = (e == 0) ? 0.0 : __hiloint2double(yhi, ylo);
+  const double Y3 = (Y * Y) * Y;
+  const unsigned cb = __float_as_uint(c);
+  const unsigned ca = cb & 0x7fffffffu;
+  const double C = (ca < 0x00800000u) ? 0.0
+                                      : __hiloint2double((int)((cb & 0x80000000u) | ((ca >> 3) + (896u << 20))),
+                                                         (int)(cb << 29));
+  return fma(Y3, C, Y3);
+}
+
 // FP64 -> FP32 rounded to nearest (ties away from zero) with 32-bit integer
 // ops only: 64-bit integer adds and masks would issue on the FP64 pipe.  The
 // rounding increment at mantissa bit 29 is a carry-chained 32-bit add.
@@ -182,6 +224,38 @@ cudaError_t launch_epi_step(const Phys &p, const StateView &s, const double *cx,
                             const double *cy, const double *cz, const double *part, int n_jc,
                             int64_t snew, double *nx, double *ny, double *nz, unsigned *err,
                             cudaStream_t st);
+// Ensemble kernel (nb_batched.cu).
+int batched_plan(int n_inst, const int64_t *offsets, int n_bins, unsigned short *order,
+                 unsigned short *bin_start, double *max_load, double *mean_load);
+cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const int64_t *offsets,
+                           int n_bins, int threads, int64_t step0, int64_t nsteps, unsigned *err,
+                           cudaStream_t st);
+constexpr int BATCH_LIMIT_INST = 1024;
+constexpr int BATCH_LIMIT_N = 6144;
+
+// Launch-shape overrides set by nb_set_tuning (nb_pair.cu); kind 3 is the
+// ensemble kernel (block = threads per CTA).
+bool tuning_lookup(int kind, int mode, int64_t n, int *block, int *R, int *blocks_per_sm);
+void tuning_set(int kind, int mode, int64_t n_lo, int64_t n_hi, int block, int R, int blocks_per_sm);
+void tuning_clear();
+
+// Adjoint kernels (nb_adjoint.cu).
+cudaError_t launch_adj_init(const Phys &p, int64_t n, const double *const xT[3],
+                            const double *const aT[3], const double *const tgt[3], double *const xb[3],
+                            double *const vb[3], double *const ab[3], double *const wacc[3],
+                            cudaStream_t st);
+cudaError_t launch_adj_epi(const Phys &p, int64_t n, const double *q, const double *const x[3],
+                           const double *part, int n_jc, double *const xb[3], double *const vb[3],
+                           double *const ab[3], double *const wacc[3], int last, int more,
+                           cudaStream_t st);
+cudaError_t launch_adj_out(int64_t n, double *const xb[3], double *const vb[3], double *const wacc[3],
+                           const double *gscale, double *gx0, double *gv0, double *gw, double *bpart,
+                           cudaStream_t st);
+cudaError_t launch_loss(const Phys &p, int64_t n, const double *q, const double *const x[3],
+                        const double *const tgt[3], const double *phi_part, int n_jc, double *bpart,
+                        double *loss, cudaStream_t st);
+constexpr int ADJ_PART_BLOCKS = 128;
+
 // Energies: block partials then one final block; out4 is device memory.
 constexpr int ENERGY_BLOCKS = 128;
 constexpr int ENERGY_THREADS = 256;

@@ -20,6 +20,8 @@
 // whose truncation error (35/16)|e|^3 < 2^-61 is below FP64 rounding for
 // the |e| < 2^-20.7 the seed guarantees.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "nb_common.cuh"
 
@@ -47,13 +49,7 @@ __device__ __forceinline__ void pair_f64(double xi, double yi, double zi, const 
   const double dy = yi - pj.y;
   const double dz = zi - pj.z;
   const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
-  const double Y = rsqrt_seed_f64(r2);
-  const double Y2 = Y * Y;
-  const double e = fma(-r2, Y2, 1.0);
-  const double Y3 = Y2 * Y;
-  const double p = fma(e, 1.875, 1.5);
-  const double t = Y3 * e;
-  double s = fma(t, p, Y3);
+  double s = rinv3_f64(r2);
   if (QARR) s *= pj.w;
   ax = fma(dx, s, ax);
   ay = fma(dy, s, ay);
@@ -404,14 +400,53 @@ int device_sm_count() {
   return sms;
 }
 
+// ---------------------------------------------------------------------------
+// Launch-shape overrides (set by the autotuner through nb_set_tuning).
+struct TuneEntry {
+  int kind, mode;
+  int64_t n_lo, n_hi;
+  int block, R, bps;
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tune;
+
+void tuning_set(int kind, int mode, int64_t n_lo, int64_t n_hi, int block, int R, int bps) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.push_back(TuneEntry{kind, mode, n_lo, n_hi, block, R, bps});
+}
+
+void tuning_clear() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+}
+
+bool tuning_lookup(int kind, int mode, int64_t n, int *block, int *R, int *bps) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto it = g_tune.rbegin(); it != g_tune.rend(); ++it)  // latest entry wins
+    if (it->kind == kind && it->mode == mode && n >= it->n_lo && n <= it->n_hi) {
+      *block = it->block;
+      *R = it->R;
+      *bps = it->bps;
+      return true;
+    }
+  return false;
+}
+
 Plan make_plan(int64_t n, int mode, int kind) {
   Plan pl;
   pl.block = n >= 8192 ? 128 : (n >= 2048 ? 64 : 32);
   pl.R = (kind == 0 && mode == MODE_SPLIT && n >= 16384) ? 2 : 1;
+  int bps = pl.block == 32 ? 32 : 16;
+  int tb = 0, tr = 0, tbps = 0;
+  if (tuning_lookup(kind, mode, n, &tb, &tr, &tbps)) {
+    pl.block = tb;
+    pl.R = (kind == 0) ? tr : 1;
+    bps = tbps;
+  }
   const int64_t it = (int64_t)pl.block * pl.R;
   pl.n_it = round_up(n, it);
   // about 16 blocks per SM for large n; small n keeps at least 8 warps per SM
-  const int64_t target = (int64_t)device_sm_count() * (pl.block == 32 ? 32 : 16);
+  const int64_t target = (int64_t)device_sm_count() * bps;
   int64_t njc = (target + pl.n_it - 1) / pl.n_it;
   const int64_t min_tiles = n >= 8192 ? 4 : 1;
   const int64_t max_jc = std::max<int64_t>(1, n / (min_tiles * (int64_t)pl.block));

@@ -1,0 +1,166 @@
+"""The ensemble kernel (nb_step_batched) against the FP64 oracle, instance
+by instance, plus its determinism, shape independence and CUDA-graph
+capture."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2106_11143_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_11143_gb300 as nbm
+    nbm.lib()
+    return nbm
+
+
+def small_ensemble(sizes, seed=11):
+    """Kibble-Zurek-style ensemble with the given instance sizes."""
+    w = W.kz_ensemble(n_inst=len(sizes), n_min=1, n_max=2, seed=seed)
+    sizes = np.asarray(sizes, dtype=np.int64)
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    rng = np.random.default_rng(seed)
+    pos = np.zeros((3, off[-1]))
+    for k, m in enumerate(sizes):
+        pos[2, off[k]:off[k + 1]] = W.chain_positions(int(m), 2 * math.pi * 100e3)
+    vel = W.thermal_velocities(int(off[-1]), 0.5e-3, W.MASS_40U, rng)
+    return off, pos, vel, w["phys"]
+
+
+def oracle_instance(orc, phys, off, pos, vel, k, nsteps, eps=0.0):
+    i0, i1 = int(off[k]), int(off[k + 1])
+    ph = dict(phys)
+    ph["instance"] = k
+    p = orc.make_params(**ph)
+    x = pos[:, i0:i1] * (1.0 + eps)
+    v = vel[:, i0:i1]
+    ax, ay, az = orc.accel(p, ph["t0"], *x, *v)
+    st = dict(x=x[0], y=x[1], z=x[2], vx=v[0], vy=v[1], vz=v[2], ax=ax, ay=ay, az=az, step=0)
+    return orc.run(p, st, nsteps)
+
+
+def run_gpu(nb, phys, off, pos, vel, nsteps, chunks=1):
+    par = nb.Params.from_phys(phys)
+    sysm = nb.System(pos, vel)
+    nb.init_batched(par, sysm, off)
+    for _ in range(chunks):
+        nb.step_batched(par, sysm, off, nsteps // chunks)
+    nb.sync_status()
+    return sysm
+
+
+def test_batched_matches_oracle_per_instance(nb, orc):
+    sizes = [1, 2, 3, 33, 100, 257, 600, 31]
+    off, pos, vel, phys = small_ensemble(sizes)
+    nsteps = 40
+    sysm = run_gpu(nb, phys, off, pos, vel, nsteps, chunks=2)
+    assert sysm.step == nsteps
+    gp = sysm.pos().cpu().numpy()
+    gv = sysm.vel().cpu().numpy()
+    V = math.sqrt(W.K_B * 0.5e-3 / W.MASS_40U)
+    for k in range(len(sizes)):
+        ref = oracle_instance(orc, phys, off, pos, vel, k, nsteps)
+        ulp = oracle_instance(orc, phys, off, pos, vel, k, nsteps, eps=2.0 ** -52)
+        i0, i1 = off[k], off[k + 1]
+        rp = np.stack([ref["x"], ref["y"], ref["z"]])
+        rv = np.stack([ref["vx"], ref["vy"], ref["vz"]])
+        up = np.stack([ulp["x"], ulp["y"], ulp["z"]])
+        uv = np.stack([ulp["vx"], ulp["vy"], ulp["vz"]])
+        dp, dv = np.max(np.abs(gp[:, i0:i1] - rp)), np.max(np.abs(gv[:, i0:i1] - rv))
+        sp, sv = np.max(np.abs(up - rp)), np.max(np.abs(uv - rv))
+        print("instance %d (n=%d): gpu dp=%.3g dv=%.3g | self dp=%.3g dv=%.3g" % (k, sizes[k], dp, dv, sp, sv))
+        assert dp <= 10 * sp + 1e-14 * 1e-4
+        assert dv <= 10 * sv + 1e-14 * V
+
+
+def test_batched_equals_standalone_instances(nb):
+    """Instance k of the ensemble is the standalone system with params.instance = k."""
+    sizes = [5, 64, 300]
+    off, pos, vel, phys = small_ensemble(sizes, seed=3)
+    nsteps = 10
+    ens = run_gpu(nb, phys, off, pos, vel, nsteps)
+    for k in range(len(sizes)):
+        i0, i1 = off[k], off[k + 1]
+        par = nb.Params.from_phys(phys, instance=k)
+        single = nb.System(pos[:, i0:i1], vel[:, i0:i1])
+        nb.forces(par, single, total=True)
+        nb.step(par, single, nsteps)
+        nb.sync_status()
+        scale = np.max(np.abs(pos[:, i0:i1])) + 1e-9
+        d = np.max(np.abs(ens.pos()[:, i0:i1].cpu().numpy() - single.pos().cpu().numpy()))
+        assert d <= 1e-9 * scale, (k, d)
+
+
+def test_batched_bitwise_deterministic_and_shape_independent(nb):
+    sizes = [7, 200, 129, 1000]
+    off, pos, vel, phys = small_ensemble(sizes, seed=5)
+    a = run_gpu(nb, phys, off, pos, vel, 12)
+    b = run_gpu(nb, phys, off, pos, vel, 12, chunks=3)
+    nb.set_tuning("ensemble", "fp64", 0, 1 << 40, 256)
+    try:
+        c = run_gpu(nb, phys, off, pos, vel, 12)
+    finally:
+        nb.set_tuning("ensemble", "fp64", 0, 0, 0)
+    for t in ("x", "vy", "az"):
+        assert torch.equal(getattr(a, t), getattr(b, t))
+        assert torch.equal(getattr(a, t), getattr(c, t))
+
+
+def test_batched_cuda_graph_capture(nb):
+    """One ensemble launch captured in a CUDA graph and replayed equals the
+    eager launch (the replay repeats the captured step window)."""
+    sizes = [50, 120, 7]
+    off, pos, vel, phys = small_ensemble(sizes, seed=8)
+    par = nb.Params.from_phys(phys)
+    eager = run_gpu(nb, phys, off, pos, vel, 3)
+    sysm = nb.System(pos, vel)
+    nb.init_batched(par, sysm, off)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        nb.step_batched(par, nb.System(pos, vel), off, 1, stream=s)  # sets up this stream's scratch
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        nb.step_batched(par, sysm, off, 3)
+    g.replay()
+    torch.cuda.synchronize()
+    for t in ("x", "vz", "ay"):
+        assert torch.equal(getattr(eager, t), getattr(sysm, t))
+
+
+def test_full_ensemble_sampled(nb, orc):
+    """The 512-instance Kibble-Zurek ensemble (N_k uniform in 32..4096): two
+    steps on the GPU in one launch; the largest and smallest instances
+    checked against the oracle."""
+    w = W.kz_ensemble()
+    off, pos, vel, phys = w["offsets"], w["pos"], w["vel"], w["phys"]
+    nsteps = 2
+    sysm = run_gpu(nb, phys, off, pos, vel, nsteps)
+    gp = sysm.pos().cpu().numpy()
+    gv = sysm.vel().cpu().numpy()
+    assert np.all(np.isfinite(gp)) and np.all(np.isfinite(gv))
+    sizes = np.diff(off)
+    picks = list(np.argsort(sizes)[:2]) + list(np.argsort(sizes)[-2:])
+    for k in picks:
+        ref = oracle_instance(orc, phys, off, pos, vel, int(k), nsteps)
+        ulp = oracle_instance(orc, phys, off, pos, vel, int(k), nsteps, eps=2.0 ** -52)
+        i0, i1 = off[k], off[k + 1]
+        rv = np.stack([ref["vx"], ref["vy"], ref["vz"]])
+        rp = np.stack([ref["x"], ref["y"], ref["z"]])
+        uv = np.stack([ulp["vx"], ulp["vy"], ulp["vz"]])
+        up = np.stack([ulp["x"], ulp["y"], ulp["z"]])
+        dv, sv = np.max(np.abs(gv[:, i0:i1] - rv)), np.max(np.abs(uv - rv))
+        dp, sp = np.max(np.abs(gp[:, i0:i1] - rp)), np.max(np.abs(up - rp))
+        print("instance %d (n=%d): gpu dp=%.3g dv=%.3g | self dp=%.3g dv=%.3g" % (k, sizes[k], dp, dv, sp, sv))
+        assert dv <= 10 * sv + 1e-14 * np.max(np.abs(rv))
+        assert dp <= 10 * sp + 1e-14 * np.max(np.abs(rp))

@@ -1,0 +1,63 @@
+"""Host-side logic of the C ABI that runs without a GPU: the ensemble
+schedule (longest-processing-time packing) and the tuning-override
+validation."""
+import numpy as np
+import pytest
+
+from paper_2106_11143_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2106_11143_gb300 import api as a
+    from paper_2106_11143_gb300 import build
+    build.build()
+    a.lib()
+    return a
+
+
+def test_plan_every_instance_once_and_lpt_bound(api):
+    w = W.kz_ensemble()
+    off = w["offsets"]
+    cost = np.diff(off).astype(float) ** 2
+    for n_bins in (1, 7, 152, 512):
+        order, start, mx, mean = api.plan_batched(off, n_bins)
+        assert sorted(order.tolist()) == list(range(len(off) - 1))
+        assert start[0] == 0 and start[-1] == len(off) - 1 and np.all(np.diff(start.astype(int)) >= 0)
+        loads = [cost[order[start[b]:start[b + 1]]].sum() for b in range(n_bins)]
+        assert max(loads) == mx
+        assert abs(np.mean(loads) - mean) <= 1e-9 * mean
+        # Graham's bound for LPT: makespan <= (4/3 - 1/(3m)) OPT, OPT >= max(mean, max item)
+        opt_lb = max(cost.sum() / n_bins, cost.max())
+        assert mx <= (4 / 3 - 1 / (3 * n_bins)) * opt_lb * (1 + 1e-12) or mx <= (4 / 3) * opt_lb
+
+
+def test_plan_is_deterministic_and_lpt_greedy(api):
+    off = np.array([0, 3, 13, 14, 24, 30])
+    o1 = api.plan_batched(off, 2)
+    o2 = api.plan_batched(off, 2)
+    assert np.array_equal(o1[0], o2[0]) and np.array_equal(o1[1], o2[1])
+    # costs 9, 100, 1, 100, 36 taken in the order 1, 3, 4, 0, 2 (ties by index),
+    # each to the lightest bin (ties to the lower bin): {1, 4} = 136, {3, 0, 2} = 110
+    order, start, mx, mean = o1
+    bins = [sorted(order[start[b]:start[b + 1]].tolist()) for b in range(2)]
+    assert bins == [[1, 4], [0, 2, 3]]
+    assert mx == 136.0 and mean == 123.0
+
+
+def test_plan_rejects_bad_input(api):
+    with pytest.raises(api.NBError):
+        api.plan_batched(np.array([0, 5, 3]), 2)
+    with pytest.raises(api.NBError):
+        api.plan_batched(np.array([0, 5]), 0)
+
+
+def test_tuning_validation(api):
+    with pytest.raises(api.NBError):
+        api.set_tuning("force", "fp64", 0, 100, 48)
+    with pytest.raises(api.NBError):
+        api.set_tuning("potential", "fp64", 0, 100, 64, R=2)
+    with pytest.raises(api.NBError):
+        api.set_tuning("ensemble", "fp64", 0, 100, 1024)
+    api.set_tuning("force", "fp64", 0, 100, 64, R=2, blocks_per_sm=8)
+    api.set_tuning("force", "fp64", 0, 0, 0)  # clear
