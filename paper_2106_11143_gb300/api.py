@@ -168,7 +168,9 @@ def _stream(stream):
 
 class System:
     """Ion state in device memory: SoA float64 tensors x, y, z, vx, vy, vz,
-    ax, ay, az (length n), optional per-ion charges q, and the step counter."""
+    ax, ay, az (length n), optional per-ion charges q, and the step counter.
+    The constructor copies pos/vel/q: the library updates its own arrays in
+    place, never the caller's."""
 
     def __init__(self, pos, vel=None, q=None, device="cuda", step=0):
         pos = _dev(pos, device).reshape(3, -1)
@@ -176,11 +178,11 @@ class System:
         vel = torch.zeros(3, n, dtype=torch.float64, device=device) if vel is None else \
             _dev(vel, device).reshape(3, n)
         self.n = n
-        self.x, self.y, self.z = (pos[k].contiguous() for k in range(3))
-        self.vx, self.vy, self.vz = (vel[k].contiguous() for k in range(3))
+        self.x, self.y, self.z = (pos[k].clone() for k in range(3))
+        self.vx, self.vy, self.vz = (vel[k].clone() for k in range(3))
         self.ax, self.ay, self.az = (torch.zeros(n, dtype=torch.float64, device=device)
                                      for _ in range(3))
-        self.q = None if q is None else _dev(q, device).reshape(n)
+        self.q = None if q is None else _dev(q, device).reshape(n).clone()
         self.step = int(step)
 
     def to_c(self):

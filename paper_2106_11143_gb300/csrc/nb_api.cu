@@ -415,7 +415,7 @@ nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t
   cudaStream_t st = (cudaStream_t)stream;
   Arena *a = nullptr;
   NB_TRY(get_arena(st, 256, &a));
-  int threads = 512, R = 1, bps = 1;
+  int threads = 256, R = 1, bps = 1;  // 256 threads: fastest in the autotuner on GB300
   tuning_lookup(3, NB_FP64, packed->n, &threads, &R, &bps);
   const int n_bins = std::min(n_inst, device_sm_count());
   NB_CUDA_TRY(launch_batched(to_phys(params), to_view(packed), n_inst, offsets, n_bins, threads,

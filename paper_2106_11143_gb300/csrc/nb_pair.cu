@@ -434,9 +434,17 @@ bool tuning_lookup(int kind, int mode, int64_t n, int *block, int *R, int *bps) 
 
 Plan make_plan(int64_t n, int mode, int kind) {
   Plan pl;
-  pl.block = n >= 8192 ? 128 : (n >= 2048 ? 64 : 32);
-  pl.R = (kind == 0 && mode == MODE_SPLIT && n >= 16384) ? 2 : 1;
-  int bps = pl.block == 32 ? 32 : 16;
+  int bps;
+  if (kind == 0) {
+    // force kernel: shapes found by the autotuner on GB300 (tune.py)
+    pl.block = n >= 24000 ? 256 : (n >= 3000 ? 128 : 32);
+    pl.R = (mode == MODE_SPLIT && n >= 24000) ? 4 : 1;
+    bps = 32;
+  } else {
+    pl.block = n >= 8192 ? 128 : (n >= 2048 ? 64 : 32);
+    pl.R = 1;
+    bps = pl.block == 32 ? 32 : 16;
+  }
   int tb = 0, tr = 0, tbps = 0;
   if (tuning_lookup(kind, mode, n, &tb, &tr, &tbps)) {
     pl.block = tb;
