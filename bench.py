@@ -42,8 +42,8 @@ PEAK_TFLOPS = {
     "fp64": 2 * 2 * SM_COUNT * SM_MHZ * 1e6 / 1e12,
     "f32": 2 * 128 * SM_COUNT * SM_MHZ * 1e6 / 1e12,
 }
-PATH_PEAK = {"fp64": "fp64", "mixed": "f32", "mixed_split": "f32"}
-DTYPE = {"fp64": "f64", "mixed": "f32+f64", "mixed_split": "f32+f64"}
+PATH_PEAK = {"fp64": "fp64", "df64": "f32", "mixed": "f32", "mixed_split": "f32"}
+DTYPE = {"fp64": "f64", "df64": "f32x2+f64", "mixed": "f32+f64", "mixed_split": "f32+f64"}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed_split", choices=["fp64", "mixed", "mixed_split"])
+    ap.add_argument("--precision", default="mixed_split", choices=["fp64", "df64", "mixed", "mixed_split"])
     ap.add_argument("--n", type=int, default=100000, help="ions (default: the 1e5 workload)")
     ap.add_argument("--no-paths", action="store_true", help="skip the secondary precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -276,7 +276,7 @@ def main_ours(args):
     e2e = run_e2e(nb, w, args.precision, min(args.steps, 20), world, flush)
     paths = {}
     if not args.no_paths:
-        for pth in ("fp64", "mixed", "mixed_split"):
+        for pth in ("fp64", "df64", "mixed", "mixed_split"):
             r = head if pth == args.precision else run_path(nb, w, pth, max(2, min(args.steps, 5)), 1,
                                                             world, flush)
             paths[pth] = {"value": round(n * n / (r["ms_per_step"] / 1e3) / 1e9, 3), "unit": UNIT,
@@ -286,6 +286,7 @@ def main_ours(args):
         paths["speedup_mixed_over_fp64"] = round(paths["fp64"]["ms_per_step"] / paths["mixed"]["ms_per_step"], 3)
         paths["speedup_mixed_split_over_fp64"] = round(
             paths["fp64"]["ms_per_step"] / paths["mixed_split"]["ms_per_step"], 3)
+        paths["speedup_df64_over_fp64"] = round(paths["fp64"]["ms_per_step"] / paths["df64"]["ms_per_step"], 3)
     if rank != 0:
         return
     cpu = None if args.no_cpu else cpu_baseline(w)
@@ -394,7 +395,8 @@ def main_kz(args):
 
 def profile_forces(args):
     """Small case for ncu: a warm-up pass then a measured pass of nb_forces in
-    each precision (pair-kernel launches 1-3 warm up, 4-6 are the ones to capture)."""
+    each precision (pair-kernel launches 1-4 warm up, 5-8 are the ones to capture:
+    fp64, df64, mixed, mixed_split)."""
     import torch
     torch.cuda.set_device(0)
     import paper_2106_11143_gb300 as nb
@@ -402,7 +404,7 @@ def profile_forces(args):
     w = W.cloud_large(n=args.n)
     sysm = nb.System(w["pos"], w["vel"])
     for _ in range(2):
-        for prec in ("fp64", "mixed", "mixed_split"):
+        for prec in ("fp64", "df64", "mixed", "mixed_split"):
             nb.forces(nb.Params.from_phys(w["phys"], precision=prec), sysm)
     nb.sync_status()
     print("profile case done: n=%d" % w["n"])

@@ -59,8 +59,15 @@ typedef enum {
  *                   (hi, lo) pair built from the FP64 value once per call,
  *                   and the displacement is (hi_i - hi_j) + (lo_i - lo_j)
  *                   in FP32.  Same accuracy class as NB_MIXED.
+ *  NB_DF64       -- FP64-class accuracy from FP32 arithmetic: FP64
+ *                   displacement split into an FP32 (hi, lo) pair; r^2,
+ *                   r^-3 and the force products as double-floats (FP32
+ *                   pairs with exact products and TwoSum); per-tile
+ *                   double-float sums added in FP64.  Per-pair relative
+ *                   error about 2^-44.  Needs |r_i - r_j| >= 2.3e-13 and
+ *                   r^2 within the FP32 normal range (SI ion-trap scales).
  * Positions, velocities, the integrator and energies are FP64 in all modes. */
-typedef enum { NB_FP64 = 0, NB_MIXED = 1, NB_MIXED_SPLIT = 2 } nb_precision;
+typedef enum { NB_FP64 = 0, NB_MIXED = 1, NB_MIXED_SPLIT = 2, NB_DF64 = 3 } nb_precision;
 
 /* Confinement (Eq. 1 of the paper).
  *  NB_TRAP_HARMONIC -- static pseudopotential: a_k = -omega_k(t)^2 x_k.

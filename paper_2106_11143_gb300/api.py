@@ -15,7 +15,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnb.so")
 
-PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_split": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_split": 2, "df64": 3}
 TRAPS = {"harmonic": 0, "rf": 1}
 NB_ACC_COULOMB, NB_ACC_TOTAL = 0, 1
 

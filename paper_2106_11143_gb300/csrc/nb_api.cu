@@ -104,7 +104,7 @@ nb_status check_params(const nb_params *p) {
   if (!finite(p->k_coulomb) || !finite(p->charge) || !finite(p->soft2) || p->soft2 < 0.0)
     return fail(NB_EINVAL, "k_coulomb, charge and soft2 must be finite (soft2 >= 0)");
   if (p->trap != NB_TRAP_HARMONIC && p->trap != NB_TRAP_RF) return fail(NB_EINVAL, "unknown trap %d", p->trap);
-  if (p->precision < NB_FP64 || p->precision > NB_MIXED_SPLIT)
+  if (p->precision < NB_FP64 || p->precision > NB_DF64)
     return fail(NB_EINVAL, "unknown precision %d", p->precision);
   for (int k = 0; k < 3; ++k)
     if (!finite(p->omega[k]) || !finite(p->omega_rate[k])) return fail(NB_EINVAL, "omega must be finite");
@@ -445,7 +445,7 @@ nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n
     return NB_OK;
   }
   if (kind < 0 || kind > 3) return fail(NB_EINVAL, "kind must be 0..3");
-  if (precision < NB_FP64 || precision > NB_MIXED_SPLIT) return fail(NB_EINVAL, "bad precision");
+  if (precision < NB_FP64 || precision > NB_DF64) return fail(NB_EINVAL, "bad precision");
   if (n_lo < 0 || n_hi < n_lo) return fail(NB_EINVAL, "bad n range");
   if (kind == 3) {
     if (block < 32 || block > 512 || block % 32) return fail(NB_EINVAL, "block must be 32..512, a multiple of 32");

@@ -18,7 +18,7 @@ enum : unsigned { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
 constexpr double KB = 1.380649e-23;
 
 // Pair-arithmetic modes (nb_precision).
-enum Mode : int { MODE_FP64 = 0, MODE_MIXED = 1, MODE_SPLIT = 2 };
+enum Mode : int { MODE_FP64 = 0, MODE_MIXED = 1, MODE_SPLIT = 2, MODE_DF64 = 3 };
 
 // ---------------------------------------------------------------------------
 // Integer-only conversions between FP64 and FP32 bit patterns.  On this GPU
@@ -107,6 +107,28 @@ __device__ __forceinline__ float f64_to_f32_rn(double d) {
   const int t = max((int)ahi2 - (896 << 20), 0);  // FP32 exponent field in bits 20..27
   const unsigned mag = __funnelshift_l(lo2, (unsigned)t, 3);
   return __uint_as_float(mag | (hi & 0x80000000u));
+}
+
+// Splits an FP64 value into FP32 parts d ~ h + l: h = RN32(d) (integer
+// ops), l = RN32(d - h) rebuilt from the 29 mantissa bits below h's rounding
+// point (a signed 29-bit integer, converted by I2F and scaled by 2^(E-52)).
+// |h + l - d| <= 2^-48 |d| for |d| >= 2^-74; below that l is 0.
+__device__ __forceinline__ void split_f64(double d, float &h, float &l) {
+  const unsigned lo = (unsigned)__double2loint(d);
+  const unsigned hi = (unsigned)__double2hiint(d);
+  unsigned lo2, ahi2;
+  asm("add.cc.u32 %0, %2, 0x10000000;\n\taddc.u32 %1, %3, 0;"
+      : "=r"(lo2), "=r"(ahi2)
+      : "r"(lo), "r"(hi & 0x7fffffffu));
+  const int t = max((int)ahi2 - (896 << 20), 0);
+  const unsigned sign = hi & 0x80000000u;
+  h = __uint_as_float(__funnelshift_l(lo2, (unsigned)t, 3) | sign);
+  // remainder below the rounding point: the low 29 bits as a signed value
+  const int r = ((int)(lo << 3)) >> 3;
+  const int e64 = (int)((hi >> 20) & 0x7ffu);
+  const int se = max(e64 - 948, 0);  // FP32 exponent field of 2^(E - 52)
+  const float scale = __uint_as_float(((unsigned)se << 23) | sign);
+  l = __int2float_rn(r) * scale;
 }
 
 // Exact FP32 -> FP64 widening by integer ops, for normal or zero inputs

@@ -76,6 +76,82 @@ __device__ __forceinline__ void pair_f32_bulk(float fx, float fy, float fz, floa
   az = fmaf(fz, s, az);
 }
 
+// ---------------------------------------------------------------------------
+// FP64-class pair term on the FP32 pipe ("double-float", MODE_DF64).
+// The displacement is an FP64 subtraction (exact for close pairs), split into
+// FP32 (hi, lo) parts.  r^2 is summed as a double-float from exact products
+// (FMA) and TwoSums; r^-3 takes the FP32 seed of its high part and the
+// compensated residual of rinv3_f64, with y^3 kept as a double-float; the
+// three force products are exact-product double-floats accumulated with
+// TwoSum into a per-tile double-float, flushed into FP64 once per tile.
+// Relative error per pair about 2^-44 (the residual's FP32 roundings).
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// y larger than 2^42 would overflow y^3 (1 + c) in FP32; real pairs need
+// |r_i - r_j| >= 2.3e-13 (in the caller's length unit) for this mode.
+constexpr float DF_YMAX = 4.398046511104e12f;  // 2^42
+
+template <bool QARR>
+__device__ __forceinline__ void pair_df64(double xi, double yi, double zi, const D4 &pj,
+                                          float s2h, float s2l, float ah[3], float al[3]) {
+  float dh[3], dl[3];
+  split_f64(xi - pj.x, dh[0], dl[0]);
+  split_f64(yi - pj.y, dh[1], dl[1]);
+  split_f64(zi - pj.z, dh[2], dl[2]);
+  // r^2 = sum_k (dh + dl)^2 (+ soft2) as a double-float (h, l)
+  const float p0 = dh[0] * dh[0], p1 = dh[1] * dh[1], p2 = dh[2] * dh[2];
+  const float e0 = fmaf(dh[0], dh[0], -p0), e1 = fmaf(dh[1], dh[1], -p1), e2 = fmaf(dh[2], dh[2], -p2);
+  float h, t1, t2;
+  two_sum_f(p0, p1, h, t1);
+  two_sum_f(h, p2, h, t2);
+  float l = (t1 + t2) + (e0 + e1 + e2);
+  l = fmaf(dh[0] + dh[0], dl[0], l);
+  l = fmaf(dh[1] + dh[1], dl[1], l);
+  l = fmaf(dh[2] + dh[2], dl[2], l);
+  if (s2h != 0.0f) {
+    float t3;
+    two_sum_f(h, s2h, h, t3);
+    l += t3 + s2l;
+  }
+  // r^-3 = y^3 (1 + c), y = MUFU.RSQ(h), c from the residual 1 - (h + l) y^2
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(h));
+  y = fminf(y, DF_YMAX);
+  const float y2 = y * y;
+  const float y2e = fmaf(y, y, -y2);
+  float r = fmaf(-h, y2, 1.0f);
+  r = fmaf(-h, y2e, r);
+  r = fmaf(-l, y2, r);
+  const float c = r * fmaf(r, 1.875f, 1.5f);
+  const float y3h = y2 * y;
+  float y3e = fmaf(y2, y, -y3h);
+  y3e = fmaf(y2e, y, y3e);
+  float sh = y3h;
+  float sl = fmaf(y3h, c, y3e);
+  if (QARR) {  // times q_j, carried as an FP32 pair in the staged entry's w
+    const float2 q = *reinterpret_cast<const float2 *>(&pj.w);
+    const float ph = sh * q.x;
+    const float pe = fmaf(sh, q.x, -ph);
+    sl = fmaf(sh, q.y, fmaf(sl, q.x, pe));
+    sh = ph;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float ph = dh[k] * sh;
+    const float pe = fmaf(dh[k], sh, -ph);
+    const float pl = fmaf(dh[k], sl, fmaf(dl[k], sh, pe));
+    float s, t;
+    two_sum_f(ah[k], ph, s, t);
+    ah[k] = s;
+    al[k] += t + pl;
+  }
+}
+
 // Adds a tile's FP32 partial to an FP64 accumulator with TwoSum
 // compensation (the error term is kept in c and added at the end).
 __device__ __forceinline__ void flush_tile(float &af, double &ad, double &c) {
@@ -119,6 +195,8 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
     for (int c = 0; c < 3; ++c) { ad[r][c] = 0.0; cd[r][c] = 0.0; af[r][c] = 0.0f; }
   }
   const float soft2f = (float)soft2;
+  float s2h = 0.0f, s2l = 0.0f;
+  if (MODE == MODE_DF64) split_f64(soft2, s2h, s2l);
 
   for (int64_t j0 = jb; j0 < je; j0 += B) {
     __syncthreads();
@@ -129,6 +207,15 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
         const float qf = QARR ? (float)q[j] : 0.0f;
         s4[2 * tid] = make_float4(pf.xh[j], pf.yh[j], pf.zh[j], qf);
         s4[2 * tid + 1] = make_float4(pf.xl[j], pf.yl[j], pf.zl[j], 0.0f);
+      } else if (MODE == MODE_DF64) {
+        D4 *s4 = reinterpret_cast<D4 *>(smem_raw);
+        D4 e = make_d4(x[j], y[j], z[j], 0.0);
+        if (QARR) {
+          float qh, ql;
+          split_f64(q[j], qh, ql);
+          *reinterpret_cast<float2 *>(&e.w) = make_float2(qh, ql);
+        }
+        s4[tid] = e;
       } else {
         D4 *s4 = reinterpret_cast<D4 *>(smem_raw);
         s4[tid] = make_d4(x[j], y[j], z[j], QARR ? q[j] : 0.0);
@@ -145,6 +232,26 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
         for (int r = 0; r < R; ++r)
           pair_f64<QARR>(xi[r], yi[r], zi[r], pj, soft2, ad[r][0], ad[r][1], ad[r][2]);
       }
+    } else if (MODE == MODE_DF64) {
+      const D4 *s4 = reinterpret_cast<const D4 *>(smem_raw);
+      float al[R][3];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) al[r][c] = 0.0f;
+#pragma unroll 2
+      for (int k = 0; k < cnt; ++k) {
+        const D4 pj = s4[k];
+#pragma unroll
+        for (int r = 0; r < R; ++r) pair_df64<QARR>(xi[r], yi[r], zi[r], pj, s2h, s2l, af[r], al[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          ad[r][c] += f32_to_f64(af[r][c]) + f32_to_f64(al[r][c]);
+          af[r][c] = 0.0f;
+        }
     } else if (MODE == MODE_MIXED) {
       const D4 *s4 = reinterpret_cast<const D4 *>(smem_raw);
 #pragma unroll 2
@@ -174,7 +281,7 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
         }
       }
     }
-    if (MODE != MODE_FP64) {
+    if (MODE == MODE_MIXED || MODE == MODE_SPLIT) {
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -188,7 +295,8 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
     if (i < n) {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        part[((int64_t)blockIdx.y * 3 + c) * n + i] = (MODE == MODE_FP64) ? ad[r][c] : ad[r][c] + cd[r][c];
+        part[((int64_t)blockIdx.y * 3 + c) * n + i] =
+            (MODE == MODE_FP64 || MODE == MODE_DF64) ? ad[r][c] : ad[r][c] + cd[r][c];
     }
   }
 }
@@ -352,6 +460,7 @@ cudaError_t launch_pair_force(const Plan &pl, int mode, int64_t n, const double 
     case MODE_FP64: return launch_force_m<MODE_FP64>(pl, n, x, y, z, q, pf, soft2, part, st);
     case MODE_MIXED: return launch_force_m<MODE_MIXED>(pl, n, x, y, z, q, pf, soft2, part, st);
     case MODE_SPLIT: return launch_force_m<MODE_SPLIT>(pl, n, x, y, z, q, pf, soft2, part, st);
+    case MODE_DF64: return launch_force_m<MODE_DF64>(pl, n, x, y, z, q, pf, soft2, part, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -16,7 +16,8 @@ from paper_2106_11143_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6}
+TOL = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6}
+ALL = ["fp64", "df64", "mixed", "mixed_split"]
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +49,7 @@ def gpu_forces(nb, phys, pos, q=None, precision="fp64", total=False, vel=None, s
 SIZES = [1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 129, 255, 257, 1000, 1024, 2049, 4097, 8191, 9000]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_split"])
+@pytest.mark.parametrize("precision", ALL)
 def test_forces_ragged_sizes(nb, orc, precision):
     phys = W.phys()
     worst = 0.0
@@ -65,7 +66,7 @@ def test_forces_ragged_sizes(nb, orc, precision):
     print("max conditioned error %s: %.3g" % (precision, worst))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_split"])
+@pytest.mark.parametrize("precision", ALL)
 def test_forces_charges_and_softening(nb, orc, precision):
     rng = np.random.default_rng(7)
     n = 3001
@@ -172,8 +173,8 @@ def _traj_errs(sysm, ref):
     return np.max(np.abs(gp - rp)), np.max(np.abs(gv - rv))
 
 
-@pytest.mark.parametrize("which", ["harmonic", "rf"])
-def test_trajectory_parity(nb, orc, which):
+@pytest.mark.parametrize("which,precision", [("harmonic", "fp64"), ("rf", "fp64"), ("harmonic", "df64")])
+def test_trajectory_parity(nb, orc, which, precision):
     """Trajectories: GPU vs oracle within 10x the oracle's own divergence (see
     _self_divergence), with a floor of 1e-14 of the cloud size / thermal speed."""
     if which == "harmonic":
@@ -184,7 +185,7 @@ def test_trajectory_parity(nb, orc, which):
         nsteps = 200
     phys = w["phys"]
     ref = _oracle_traj(orc, phys, w["pos"], w["vel"], nsteps)
-    sysm = _gpu_traj(nb, phys, w["pos"], w["vel"], nsteps, chunks=2)
+    sysm = _gpu_traj(nb, phys, w["pos"], w["vel"], nsteps, precision=precision, chunks=2)
     assert sysm.step == nsteps
     dp_self, dv_self = _self_divergence(orc, phys, w["pos"], w["vel"], nsteps, ref)
     dp, dv = _traj_errs(sysm, ref)
@@ -229,7 +230,7 @@ def test_step_determinism_and_resume(nb):
         assert torch.equal(getattr(a, t), getattr(c, t))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_split"])
+@pytest.mark.parametrize("precision", ALL)
 def test_full_size_sampled(nb, orc, precision):
     """N = 1e5 (the large-cloud workload, launch configuration of the bench):
     all forces on the GPU, a sample of 192 ions (spread over tiles and the
@@ -250,7 +251,7 @@ def test_full_size_sampled(nb, orc, precision):
     assert max(errs) <= TOL[precision]
     # Newton's third law over all ions (uniform mass: sum a_i = 0)
     tot = np.abs(g).sum(axis=1)
-    assert np.all(np.abs(g.sum(axis=1)) <= (1e-12 if precision == "fp64" else 1e-6) * tot)
+    assert np.all(np.abs(g.sum(axis=1)) <= (1e-12 if precision in ("fp64", "df64") else 1e-6) * tot)
 
 
 def test_argument_errors(nb):
