@@ -60,6 +60,7 @@ def lib():
         _lib.or_philox4x32_10.argtypes = [u32, u32, u32]
         _lib.or_normals3.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int64, d]
         _lib.or_set_threads.argtypes = [C.c_int]
+        _lib.or_set_masses.argtypes = [C.POINTER(C.c_double)]
         _lib.or_get_threads.restype = C.c_int
     return _lib
 
@@ -89,6 +90,20 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+class _Masses:
+    """Per-ion masses (two species) for the duration of one oracle call."""
+
+    def __init__(self, masses):
+        self.m = None if masses is None else _f64(masses)
+
+    def __enter__(self):
+        lib().or_set_masses(_ptr(self.m))
+        return self
+
+    def __exit__(self, *a):
+        lib().or_set_masses(None)
+
+
 def set_threads(n):
     lib().or_set_threads(int(n))
 
@@ -97,7 +112,8 @@ def get_threads():
     return lib().or_get_threads()
 
 
-def coulomb(p, x, y, z, q=None, reverse=False, i0=0, i1=None, want_phi=False, want_absf=False):
+def coulomb(p, x, y, z, q=None, reverse=False, i0=0, i1=None, want_phi=False, want_absf=False,
+            masses=None):
     """Coulomb acceleration of particles [i0, i1) (Eq. 1, j != i).
 
     Returns (ax, ay, az, phi or None, absf or None); phi = sum q_j/s_ij,
@@ -110,8 +126,9 @@ def coulomb(p, x, y, z, q=None, reverse=False, i0=0, i1=None, want_phi=False, wa
     ax, ay, az = np.empty(m), np.empty(m), np.empty(m)
     phi = np.empty(m) if want_phi else None
     absf = np.empty(m) if want_absf else None
-    lib().or_coulomb_range(C.byref(p), n, i0, i1, _ptr(x), _ptr(y), _ptr(z), _ptr(q),
-                           _ptr(ax), _ptr(ay), _ptr(az), _ptr(phi), _ptr(absf), int(reverse))
+    with _Masses(masses):
+        lib().or_coulomb_range(C.byref(p), n, i0, i1, _ptr(x), _ptr(y), _ptr(z), _ptr(q),
+                               _ptr(ax), _ptr(ay), _ptr(az), _ptr(phi), _ptr(absf), int(reverse))
     return ax, ay, az, phi, absf
 
 
@@ -123,53 +140,57 @@ def trap(p, t, x, y, z):
     return ax, ay, az
 
 
-def accel(p, t, x, y, z, vx=None, vy=None, vz=None, q=None, reverse=False):
+def accel(p, t, x, y, z, vx=None, vy=None, vz=None, q=None, reverse=False, masses=None):
     """Total Verlet-state acceleration: Coulomb + trap(t) - (gamma/m) v."""
     x, y, z = _f64(x), _f64(y), _f64(z)
     n = x.shape[0]
     vs = [None, None, None] if vx is None else [_f64(vx), _f64(vy), _f64(vz)]
     q = None if q is None else _f64(q)
     ax, ay, az = np.empty(n), np.empty(n), np.empty(n)
-    lib().or_accel(C.byref(p), t, n, _ptr(x), _ptr(y), _ptr(z), _ptr(vs[0]), _ptr(vs[1]),
-                   _ptr(vs[2]), _ptr(q), _ptr(ax), _ptr(ay), _ptr(az), int(reverse))
+    with _Masses(masses):
+        lib().or_accel(C.byref(p), t, n, _ptr(x), _ptr(y), _ptr(z), _ptr(vs[0]), _ptr(vs[1]),
+                       _ptr(vs[2]), _ptr(q), _ptr(ax), _ptr(ay), _ptr(az), int(reverse))
     return ax, ay, az
 
 
-def run(p, state, nsteps, q=None, reverse=False):
+def run(p, state, nsteps, q=None, reverse=False, masses=None):
     """Velocity Verlet for nsteps (Sec. II).  state: dict with x,y,z,vx,vy,vz,
     ax,ay,az (float64 arrays, updated copies are returned) and 'step'."""
     s = {k: _f64(state[k]).copy() for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")}
     step = C.c_int64(int(state.get("step", 0)))
     q = None if q is None else _f64(q)
     n = s["x"].shape[0]
-    rc = lib().or_run(C.byref(p), n, _ptr(q), *[_ptr(s[k]) for k in
-                      ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")],
-                      C.byref(step), int(nsteps), int(reverse))
+    with _Masses(masses):
+        rc = lib().or_run(C.byref(p), n, _ptr(q), *[_ptr(s[k]) for k in
+                          ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")],
+                          C.byref(step), int(nsteps), int(reverse))
     if rc != 0:
         raise MemoryError("oracle run failed")
     s["step"] = step.value
     return s
 
 
-def energy(p, step, x, y, z, vx, vy, vz, q=None):
+def energy(p, step, x, y, z, vx, vy, vz, q=None, masses=None):
     """(kinetic, trap, Coulomb, total) energies in J at time t0 + step*dt."""
     out = np.empty(4)
     q = None if q is None else _f64(q)
     arrs = [_f64(a) for a in (x, y, z, vx, vy, vz)]
-    lib().or_energy(C.byref(p), int(step), arrs[0].shape[0], *[_ptr(a) for a in arrs], _ptr(q),
-                    _ptr(out))
+    with _Masses(masses):
+        lib().or_energy(C.byref(p), int(step), arrs[0].shape[0], *[_ptr(a) for a in arrs], _ptr(q),
+                        _ptr(out))
     return out
 
 
-def forces_vjp(p, t, x, y, z, lx, ly, lz, q=None, include_trap=False):
+def forces_vjp(p, t, x, y, z, lx, ly, lz, q=None, include_trap=False, masses=None):
     """J^T lambda of the acceleration with respect to positions."""
     arrs = [_f64(a) for a in (x, y, z)]
     lam = [_f64(a) for a in (lx, ly, lz)]
     n = arrs[0].shape[0]
     q = None if q is None else _f64(q)
     gx, gy, gz = np.empty(n), np.empty(n), np.empty(n)
-    lib().or_forces_vjp(C.byref(p), t, n, *[_ptr(a) for a in arrs], _ptr(q),
-                        *[_ptr(a) for a in lam], _ptr(gx), _ptr(gy), _ptr(gz), int(include_trap))
+    with _Masses(masses):
+        lib().or_forces_vjp(C.byref(p), t, n, *[_ptr(a) for a in arrs], _ptr(q),
+                            *[_ptr(a) for a in lam], _ptr(gx), _ptr(gy), _ptr(gz), int(include_trap))
     return gx, gy, gz
 
 

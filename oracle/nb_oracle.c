@@ -97,6 +97,20 @@ static double or_charge(const or_params *p, const double *q, int64_t i) {
   return q ? q[i] : p->charge;
 }
 
+/* Per-ion mass for two-species systems (Sec. II: two species interact as
+ * three N-body problems, 1-1, 2-2 and 1-2; with a per-ion charge and mass the
+ * single all-pairs sum covers all three).  NULL = params mass for all.     */
+static const double *g_mass = NULL;
+void or_set_masses(const double *m) { g_mass = m; }
+static double or_mass(const or_params *p, int64_t i) { return g_mass ? g_mass[i] : p->mass; }
+
+/* The trap's electric field is fixed, so an ion's trap acceleration scales
+ * with its charge-to-mass ratio relative to the reference species that the
+ * trap parameters describe (params charge and mass).                      */
+static double or_trap_scale(const or_params *p, const double *q, int64_t i) {
+  return (or_charge(p, q, i) / or_mass(p, i)) / (p->charge / p->mass);
+}
+
 /* ------------------------------------------------------------------ */
 /* Coulomb acceleration of every particle in [i0, i1) from all n.
  * ax/ay/az receive k_C q_i/m * sum_{j != i} q_j d_ij / s_ij^3 with
@@ -132,7 +146,7 @@ void or_coulomb_range(const or_params *p, int64_t n, int64_t i0, int64_t i1,
       if (absf) or_add(&sa, fabs(qj) * sqrt(dx * dx + dy * dy + dz * dz) * inv3);
     }
     double qi = or_charge(p, q, i);
-    double pref = p->k_coulomb * qi / p->mass;
+    double pref = p->k_coulomb * qi / or_mass(p, i);
     ax[i - i0] = pref * or_val(sx);
     ay[i - i0] = pref * or_val(sy);
     az[i - i0] = pref * or_val(sz);
@@ -183,13 +197,14 @@ void or_accel(const or_params *p, double t, int64_t n, const double *x,
               const double *vy, const double *vz, const double *q, double *ax,
               double *ay, double *az, int reverse) {
   or_coulomb(p, n, x, y, z, q, ax, ay, az, NULL, NULL, reverse);
-  double g = p->gamma / p->mass;
   for (int64_t i = 0; i < n; i++) {
     double tx, ty, tz;
+    double g = p->gamma / or_mass(p, i);
+    double ts = or_trap_scale(p, q, i);
     or_trap_one(p, t, x[i], y[i], z[i], &tx, &ty, &tz);
-    ax[i] += tx;
-    ay[i] += ty;
-    az[i] += tz;
+    ax[i] += ts * tx;
+    ay[i] += ts * ty;
+    az[i] += ts * tz;
     if (vx) {
       ax[i] -= g * vx[i];
       ay[i] -= g * vy[i];
@@ -260,10 +275,6 @@ int or_run(const or_params *p, int64_t n, const double *q, double *x, double *y,
            double *z, double *vx, double *vy, double *vz, double *ax,
            double *ay, double *az, int64_t *step, int64_t nsteps, int reverse) {
   double dt = p->dt;
-  double c = p->gamma * dt / (2.0 * p->mass);
-  double g = p->gamma / p->mass;
-  double sig = 0.0;
-  if (p->noise_T > 0.0) sig = sqrt(2.0 * p->gamma * OR_KB * p->noise_T * dt) / p->mass;
   double *cx = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
   if (!cx) return 1;
   double *cy = cx + n, *cz = cy + n;
@@ -278,8 +289,13 @@ int or_run(const or_params *p, int64_t n, const double *q, double *x, double *y,
     or_coulomb(p, n, x, y, z, q, cx, cy, cz, NULL, NULL, reverse);
     for (int64_t i = 0; i < n; i++) {
       double tx, ty, tz;
+      double mi = or_mass(p, i), ts = or_trap_scale(p, q, i);
+      double c = p->gamma * dt / (2.0 * mi);
+      double g = p->gamma / mi;
+      double sig = 0.0;
+      if (p->noise_T > 0.0) sig = sqrt(2.0 * p->gamma * OR_KB * p->noise_T * dt) / mi;
       or_trap_one(p, tnew, x[i], y[i], z[i], &tx, &ty, &tz);
-      double ux = cx[i] + tx, uy = cy[i] + ty, uz = cz[i] + tz;
+      double ux = cx[i] + ts * tx, uy = cy[i] + ts * ty, uz = cz[i] + ts * tz;
       double nvx = (vx[i] + 0.5 * dt * (ax[i] + ux)) / (1.0 + c);
       double nvy = (vy[i] + 0.5 * dt * (ay[i] + uy)) / (1.0 + c);
       double nvz = (vz[i] + 0.5 * dt * (az[i] + uz)) / (1.0 + c);
@@ -315,15 +331,16 @@ void or_energy(const or_params *p, int64_t step, int64_t n, const double *x,
   double *t1 = phi + n, *t2 = t1 + n, *t3 = t2 + n;
   or_coulomb(p, n, x, y, z, q, t1, t2, t3, phi, NULL, 0);
   for (int64_t i = 0; i < n; i++) {
-    or_add(&ke, 0.5 * p->mass * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]));
+    double mi = or_mass(p, i), ts = or_trap_scale(p, q, i);
+    or_add(&ke, 0.5 * mi * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]));
     if (p->trap == 1) {
       double c = 0.5 * p->q_mathieu * p->omega_rf * p->omega_rf *
                  cos(p->omega_rf * t + p->rf_phase);
       double wz = or_omega(p, 2, t);
-      or_add(&tp, 0.5 * p->mass * (c * (x[i] * x[i] - y[i] * y[i]) + wz * wz * z[i] * z[i]));
+      or_add(&tp, 0.5 * mi * ts * (c * (x[i] * x[i] - y[i] * y[i]) + wz * wz * z[i] * z[i]));
     } else {
       double wx = or_omega(p, 0, t), wy = or_omega(p, 1, t), wz = or_omega(p, 2, t);
-      or_add(&tp, 0.5 * p->mass *
+      or_add(&tp, 0.5 * mi * ts *
                       (wx * wx * x[i] * x[i] + wy * wy * y[i] * y[i] + wz * wz * z[i] * z[i]));
     }
     or_add(&cp, 0.5 * p->k_coulomb * or_charge(p, q, i) * phi[i]);
@@ -363,23 +380,25 @@ void or_forces_vjp(const or_params *p, double t, int64_t n, const double *x,
       or_add(&sy, qj * (ey * inv3 - 3.0 * dy * dot * inv5));
       or_add(&sz, qj * (ez * inv3 - 3.0 * dz * dot * inv5));
     }
-    double pref = p->k_coulomb * or_charge(p, q, i) / p->mass;
+    double pref = p->k_coulomb * or_charge(p, q, i) / or_mass(p, i);
+    double ts = or_trap_scale(p, q, i);
     gx[i] = pref * or_val(sx);
     gy[i] = pref * or_val(sy);
     gz[i] = pref * or_val(sz);
     if (include_trap) {
+      double tx0 = gx[i], ty0 = gy[i], tz0 = gz[i];
       if (p->trap == 1) {
         double c = 0.5 * p->q_mathieu * p->omega_rf * p->omega_rf *
                    cos(p->omega_rf * t + p->rf_phase);
         double wz = or_omega(p, 2, t);
-        gx[i] += -c * lx[i];
-        gy[i] += c * ly[i];
-        gz[i] += -wz * wz * lz[i];
+        gx[i] = tx0 + ts * (-c * lx[i]);
+        gy[i] = ty0 + ts * (c * ly[i]);
+        gz[i] = tz0 + ts * (-wz * wz * lz[i]);
       } else {
         double wx = or_omega(p, 0, t), wy = or_omega(p, 1, t), wz = or_omega(p, 2, t);
-        gx[i] += -wx * wx * lx[i];
-        gy[i] += -wy * wy * ly[i];
-        gz[i] += -wz * wz * lz[i];
+        gx[i] = tx0 + ts * (-wx * wx * lx[i]);
+        gy[i] = ty0 + ts * (-wy * wy * ly[i]);
+        gz[i] = tz0 + ts * (-wz * wz * lz[i]);
       }
     }
   }
@@ -402,7 +421,7 @@ int or_trajectory_grad(const or_params *p, int64_t n, const double *q,
                        const double *x0, const double *v0, int64_t nsteps,
                        const double *target, double *loss, double *grad_x0,
                        double *grad_v0, double grad_omega[3]) {
-  if (p->trap != 0 || p->gamma != 0.0 || p->noise_T != 0.0 ||
+  if (g_mass || p->trap != 0 || p->gamma != 0.0 || p->noise_T != 0.0 ||
       p->omega_rate[0] != 0.0 || p->omega_rate[1] != 0.0 || p->omega_rate[2] != 0.0)
     return 2;
   size_t N3 = 3 * (size_t)n;

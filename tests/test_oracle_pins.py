@@ -447,3 +447,75 @@ def test_langevin_equipartition(orc):
     v2 = np.concatenate([st["vx"], st["vy"], st["vz"]]) ** 2
     T_est = m * v2.mean() / W.K_B
     assert abs(T_est / T - 1) < 0.1
+
+
+# --------------------------------------------------------------------------
+# Two species (Sec. II: interactions 1-1, 2-2 and 1-2 in one all-pairs sum).
+def test_two_species_equilibrium(orc):
+    """Ions of charge q1, q2 in the trap of the reference species (Q, M):
+    the trap field is fixed, so force balance gives
+    d^3 = k_C Q (q1 + q2) / (M w_z^2) and z1 = q2 d/(q1 + q2) -- independent
+    of the masses."""
+    wz = 2 * math.pi * 200e3
+    p = P(orc, omega=(2 * math.pi * 1e6, 2 * math.pi * 1e6, wz))
+    Q, M = W.E_CHARGE, W.MASS_40U
+    q = np.array([Q, 2 * Q])
+    m = np.array([M, 9 * W.AMU])
+    d = (W.K_COULOMB * Q * (q[0] + q[1]) / (M * wz * wz)) ** (1 / 3)
+    z = np.array([q[1] * d / (q[0] + q[1]), -q[0] * d / (q[0] + q[1])])
+    a = np.stack(orc.accel(p, 0.0, np.zeros(2), np.zeros(2), z, q=q, masses=m))
+    aC = W.K_COULOMB * q[0] * q[1] / (m * d * d)
+    assert np.all(np.abs(a[2]) <= 1e-12 * aC)
+    # and the same positions are NOT a balance if the masses are ignored in the trap term
+    a_bad = np.stack(orc.accel(p, 0.0, np.zeros(2), np.zeros(2), np.array([d / 2, -d / 2]), q=q, masses=m))
+    assert np.max(np.abs(a_bad[2]) / aC) > 1e-3
+
+
+def test_two_species_momentum(orc):
+    rng = np.random.default_rng(12)
+    n = 500
+    pos = W.ellipsoid_uniform(n, (20e-6, 20e-6, 100e-6), rng)
+    q = W.E_CHARGE * rng.choice([1.0, 2.0], size=n)
+    m = W.AMU * rng.choice([40.0, 9.0, 138.0], size=n)
+    ax, ay, az, _, absf = orc.coulomb(P(orc), *pos, q=q, masses=m, want_absf=True)
+    F = m * np.stack([ax, ay, az])
+    tot = np.abs(F).sum(axis=1)
+    assert np.all(np.abs(F.sum(axis=1)) <= 1e-12 * tot)
+
+
+def test_two_species_harmonic_verlet(orc):
+    """A single ion of charge q_i and mass m_i oscillates at w_i^2 = s_i w^2,
+    s_i = (q_i/m_i)/(Q/M); Verlet reproduces the exact discrete solution."""
+    w, dt = 2 * math.pi * 300e3, 4e-9
+    p = P(orc, omega=(w, w, w), dt=dt)
+    q, m = np.array([2 * W.E_CHARGE]), np.array([9 * W.AMU])
+    s = (q[0] / m[0]) / (W.E_CHARGE / W.MASS_40U)
+    x0 = np.array([3e-6]); v0 = np.array([0.2]); zero = np.zeros(1)
+    ax, ay, az = orc.accel(p, 0.0, x0, zero, zero, q=q, masses=m)
+    st = dict(x=x0, y=zero, z=zero, vx=v0, vy=zero, vz=zero, ax=ax, ay=ay, az=az, step=0)
+    nsteps = 2000
+    st = orc.run(p, st, nsteps, q=q, masses=m)
+    th = math.acos(1 - s * (w * dt) ** 2 / 2)
+    xn = x0[0] * math.cos(nsteps * th) + dt * v0[0] * math.sin(nsteps * th) / math.sin(th)
+    assert abs(st["x"][0] - xn) <= 1e-11 * math.hypot(x0[0], dt * v0[0] / math.sin(th))
+
+
+def test_two_species_energy_is_potential_of_force(orc):
+    rng = np.random.default_rng(14)
+    n = 5
+    pos = W.ellipsoid_uniform(n, (10e-6, 10e-6, 30e-6), rng)
+    q = W.E_CHARGE * np.array([1.0, 2.0, 1.0, 1.0, 2.0])
+    m = W.AMU * np.array([40.0, 9.0, 9.0, 138.0, 40.0])
+    zero = np.zeros((3, n))
+    p = P(orc, omega=(2 * math.pi * 1e6, 2 * math.pi * 0.8e6, 2 * math.pi * 200e3))
+    a = np.stack(orc.accel(p, 0.0, *pos, q=q, masses=m))
+    h = 1e-11
+    for i in range(n):
+        for c in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[c, i] += h
+            pm[c, i] -= h
+            up = orc.energy(p, 0, *pp, *zero, q=q, masses=m)
+            um = orc.energy(p, 0, *pm, *zero, q=q, masses=m)
+            g = ((up[1] + up[2]) - (um[1] + um[2])) / (2 * h)
+            assert abs(-g / m[i] - a[c, i]) <= 1e-6 * np.abs(a).max()
