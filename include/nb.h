@@ -66,8 +66,24 @@ typedef enum {
  *                   double-float sums added in FP64.  Per-pair relative
  *                   error about 2^-44.  Needs |r_i - r_j| >= 2.3e-13 and
  *                   r^2 within the FP32 normal range (SI ion-trap scales).
+ * The 1/sqrt ladder of the paper (Sec. IV-VI), FP64 pair arithmetic with
+ * r^-3 = y^3 and y from:
+ *  NB_FP64_SQRTDIV -- 1.0 / sqrt(r^2) (the classical loop, "SQRT+DIV")
+ *  NB_FP64_RSQ     -- the FP32 hardware seed alone (relative error ~2^-22;
+ *                     the GPU counterpart of RSQRT14)
+ *  NB_FP64_RSQ_NR1 -- seed + one Newton-Raphson step y (3 - r^2 y^2)/2
+ *  NB_FP64_RSQ_NR2 -- seed + two Newton-Raphson steps
  * Positions, velocities, the integrator and energies are FP64 in all modes. */
-typedef enum { NB_FP64 = 0, NB_MIXED = 1, NB_MIXED_SPLIT = 2, NB_DF64 = 3 } nb_precision;
+typedef enum {
+  NB_FP64 = 0,
+  NB_MIXED = 1,
+  NB_MIXED_SPLIT = 2,
+  NB_DF64 = 3,
+  NB_FP64_SQRTDIV = 4,
+  NB_FP64_RSQ = 5,
+  NB_FP64_RSQ_NR1 = 6,
+  NB_FP64_RSQ_NR2 = 7
+} nb_precision;
 
 /* Confinement (Eq. 1 of the paper).
  *  NB_TRAP_HARMONIC -- static pseudopotential: a_k = -omega_k(t)^2 x_k.
@@ -105,6 +121,14 @@ typedef struct nb_system {
   double *ax, *ay, *az; /* acceleration (m/s^2), device: the Verlet state */
   const double *q;      /* per-ion charge (C), device, or NULL = params.charge */
   int64_t step;         /* step counter; time t = t0 + step * dt */
+  const double *m;      /* per-ion mass (kg), device, or NULL = params.mass.
+                           With several species (Sec. II: 1-1, 2-2 and 1-2
+                           interactions in one all-pairs sum), the trap's field
+                           is that of params (charge, mass): ion i's trap
+                           acceleration is scaled by (q_i/m_i)/(charge/mass),
+                           its friction is -(gamma/m_i) v_i and its Langevin
+                           kick uses m_i.  Not supported by nb_step_batched and
+                           nb_traj_* (NB_ENOTSUP). */
 } nb_system;
 
 /* nb_forces flags */

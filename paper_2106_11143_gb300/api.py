@@ -15,7 +15,8 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnb.so")
 
-PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_split": 2, "df64": 3}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_split": 2, "df64": 3, "sqrtdiv": 4, "rsq": 5,
+              "rsq_nr1": 6, "rsq_nr2": 7}
 TRAPS = {"harmonic": 0, "rf": 1}
 NB_ACC_COULOMB, NB_ACC_TOTAL = 0, 1
 
@@ -41,7 +42,7 @@ class NbSystem(C.Structure):
         ("x", _dp), ("y", _dp), ("z", _dp),
         ("vx", _dp), ("vy", _dp), ("vz", _dp),
         ("ax", _dp), ("ay", _dp), ("az", _dp),
-        ("q", _dp), ("step", C.c_int64),
+        ("q", _dp), ("step", C.c_int64), ("m", _dp),
     ]
 
 
@@ -168,11 +169,11 @@ def _stream(stream):
 
 class System:
     """Ion state in device memory: SoA float64 tensors x, y, z, vx, vy, vz,
-    ax, ay, az (length n), optional per-ion charges q, and the step counter.
-    The constructor copies pos/vel/q: the library updates its own arrays in
-    place, never the caller's."""
+    ax, ay, az (length n), optional per-ion charges q and masses m (several
+    species), and the step counter.  The constructor copies pos/vel/q/m: the
+    library updates its own arrays in place, never the caller's."""
 
-    def __init__(self, pos, vel=None, q=None, device="cuda", step=0):
+    def __init__(self, pos, vel=None, q=None, device="cuda", step=0, m=None):
         pos = _dev(pos, device).reshape(3, -1)
         n = pos.shape[1]
         vel = torch.zeros(3, n, dtype=torch.float64, device=device) if vel is None else \
@@ -183,6 +184,7 @@ class System:
         self.ax, self.ay, self.az = (torch.zeros(n, dtype=torch.float64, device=device)
                                      for _ in range(3))
         self.q = None if q is None else _dev(q, device).reshape(n).clone()
+        self.m = None if m is None else _dev(m, device).reshape(n).clone()
         self.step = int(step)
 
     def to_c(self):
@@ -191,6 +193,7 @@ class System:
         for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
             setattr(s, k, _ptr(getattr(self, k)))
         s.q = _ptr(self.q)
+        s.m = _ptr(self.m)
         s.step = self.step
         return s
 
@@ -201,6 +204,7 @@ class System:
         for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
             setattr(v, k, getattr(self, k)[i0:i1])
         v.q = None if self.q is None else self.q[i0:i1]
+        v.m = None if self.m is None else self.m[i0:i1]
         v.step = self.step
         return v
 

@@ -104,7 +104,7 @@ nb_status check_params(const nb_params *p) {
   if (!finite(p->k_coulomb) || !finite(p->charge) || !finite(p->soft2) || p->soft2 < 0.0)
     return fail(NB_EINVAL, "k_coulomb, charge and soft2 must be finite (soft2 >= 0)");
   if (p->trap != NB_TRAP_HARMONIC && p->trap != NB_TRAP_RF) return fail(NB_EINVAL, "unknown trap %d", p->trap);
-  if (p->precision < NB_FP64 || p->precision > NB_DF64)
+  if (p->precision < NB_FP64 || p->precision > NB_FP64_RSQ_NR2)
     return fail(NB_EINVAL, "unknown precision %d", p->precision);
   for (int k = 0; k < 3; ++k)
     if (!finite(p->omega[k]) || !finite(p->omega_rate[k])) return fail(NB_EINVAL, "omega must be finite");
@@ -150,6 +150,7 @@ nb_status check_system(const nb_system *s, bool need_v, bool need_a) {
     NB_TRY(check_array(s->az, "az"));
   }
   if (s->q && !aligned8(s->q)) return fail(NB_EINVAL, "q is not 8-byte aligned");
+  if (s->m && !aligned8(s->m)) return fail(NB_EINVAL, "m is not 8-byte aligned");
   return NB_OK;
 }
 
@@ -184,6 +185,7 @@ StateView to_view(const nb_system *s) {
   v.vx = s->vx; v.vy = s->vy; v.vz = s->vz;
   v.ax = s->ax; v.ay = s->ay; v.az = s->az;
   v.q = s->q;
+  v.m = s->m;
   return v;
 }
 
@@ -392,6 +394,7 @@ nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t
   NB_TRY(check_params(params));
   NB_TRY(check_system(packed, true, true));
   if (params->precision != NB_FP64) return fail(NB_ENOTSUP, "the ensemble kernel is FP64 only");
+  if (packed->m) return fail(NB_ENOTSUP, "the ensemble kernel has one species (m must be NULL)");
   if (nsteps < 0) return fail(NB_EINVAL, "nsteps must be >= 0");
   if (!(params->dt > 0.0)) return fail(NB_EINVAL, "dt must be > 0");
   if (n_inst < 0 || n_inst > BATCH_LIMIT_INST)
@@ -445,7 +448,7 @@ nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n
     return NB_OK;
   }
   if (kind < 0 || kind > 3) return fail(NB_EINVAL, "kind must be 0..3");
-  if (precision < NB_FP64 || precision > NB_DF64) return fail(NB_EINVAL, "bad precision");
+  if (precision < NB_FP64 || precision > NB_FP64_RSQ_NR2) return fail(NB_EINVAL, "bad precision");
   if (n_lo < 0 || n_hi < n_lo) return fail(NB_EINVAL, "bad n range");
   if (kind == 3) {
     if (block < 32 || block > 512 || block % 32) return fail(NB_EINVAL, "block must be 32..512, a multiple of 32");
@@ -494,6 +497,7 @@ extern "C" nb_status nb_traj_forward(const nb_params *params, nb_system *sys, in
                                      void *stream) {
   NB_TRY(check_adjoint(params));
   NB_TRY(check_system(sys, true, true));
+  if (sys->m) return fail(NB_ENOTSUP, "the trajectory adjoint has one species (m must be NULL)");
   if (nsteps < 0 || every < 1) return fail(NB_EINVAL, "nsteps must be >= 0 and every >= 1");
   const int64_t n = sys->n;
   if (n == 0) return fail(NB_EINVAL, "the trajectory loss needs n >= 1");
@@ -536,6 +540,7 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
                                       void *stream) {
   NB_TRY(check_adjoint(params));
   if (!sys) return fail(NB_EINVAL, "system is NULL");
+  if (sys->m) return fail(NB_ENOTSUP, "the trajectory adjoint has one species (m must be NULL)");
   if (nsteps < 0 || every < 1) return fail(NB_EINVAL, "nsteps must be >= 0 and every >= 1");
   const int64_t n = sys->n;
   if (n < 1) return fail(NB_EINVAL, "the trajectory loss needs n >= 1");

@@ -18,7 +18,18 @@ enum : unsigned { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
 constexpr double KB = 1.380649e-23;
 
 // Pair-arithmetic modes (nb_precision).
-enum Mode : int { MODE_FP64 = 0, MODE_MIXED = 1, MODE_SPLIT = 2, MODE_DF64 = 3 };
+enum Mode : int {
+  MODE_FP64 = 0,
+  MODE_MIXED = 1,
+  MODE_SPLIT = 2,
+  MODE_DF64 = 3,
+  // the 1/sqrt ladder of Sec. IV-VI, all FP64 pair arithmetic:
+  MODE_SQRTDIV = 4,  // 1.0 / sqrt(r^2)
+  MODE_RSQ = 5,      // hardware seed only (relative error ~2^-22)
+  MODE_RSQ_NR1 = 6,  // seed + one FP64 Newton-Raphson step
+  MODE_RSQ_NR2 = 7   // seed + two FP64 Newton-Raphson steps
+};
+__host__ __device__ constexpr bool fp64_like(int m) { return m == MODE_FP64 || m >= MODE_SQRTDIV; }
 
 // ---------------------------------------------------------------------------
 // Integer-only conversions between FP64 and FP32 bit patterns.  On this GPU
@@ -231,7 +242,19 @@ struct StateView {
   int64_t n;
   double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az;
   const double *q;
+  const double *m = nullptr;  // per-ion mass (two species) or nullptr
 };
+
+// Mass of ion i, and the scale of its trap acceleration relative to the
+// reference species of the trap parameters: (q_i/m_i) / (charge/mass).
+__device__ __forceinline__ double ion_mass(const Phys &p, const StateView &s, int64_t i) {
+  return s.m ? s.m[i] : p.mass;
+}
+__device__ __forceinline__ double trap_scale(const Phys &p, const StateView &s, int64_t i) {
+  if (!s.m && !s.q) return 1.0;
+  const double qi = s.q ? s.q[i] : p.charge;
+  return (qi / ion_mass(p, s, i)) / (p.charge / p.mass);
+}
 cudaError_t launch_epi_forces(const Phys &p, const StateView &s, const double *part, int n_jc,
                               int flags, double t, unsigned *err, cudaStream_t st);
 cudaError_t launch_epi_vjp(const Phys &p, const StateView &s, const double *part, int n_jc,

@@ -15,10 +15,11 @@ __device__ __forceinline__ double chunk_sum(const double *__restrict__ part, int
   return s;
 }
 
-// Coulomb prefactor k_C q_i w / m, where the pair sums carry w_j = q_j when
+// Coulomb prefactor k_C q_i w / m_i, where the pair sums carry w_j = q_j when
 // per-ion charges are given and w_j = 1 otherwise.
-__device__ __forceinline__ double coulomb_pref(const Phys &p, const double *q, int64_t i) {
-  return q ? p.k_coulomb * q[i] / p.mass : p.k_coulomb * p.charge * p.charge / p.mass;
+__device__ __forceinline__ double coulomb_pref(const Phys &p, const StateView &s, int64_t i) {
+  const double m = ion_mass(p, s, i);
+  return s.q ? p.k_coulomb * s.q[i] / m : p.k_coulomb * p.charge * p.charge / m;
 }
 
 // ---------------------------------------------------------------------------
@@ -61,17 +62,18 @@ __global__ void k_epi_forces(Phys p, StateView s, const double *__restrict__ par
                              int flags, double t, unsigned *err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
-  const double pref = coulomb_pref(p, s.q, i);
+  const double pref = coulomb_pref(p, s, i);
   double a[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) a[c] = pref * chunk_sum(part, n_jc, 3, c, s.n, i);
   if (flags & NB_ACC_TOTAL) {
     double tx, ty, tz;
     trap_accel(p, t, s.x[i], s.y[i], s.z[i], tx, ty, tz);
-    const double g = p.gamma / p.mass;
-    a[0] += tx - g * s.vx[i];
-    a[1] += ty - g * s.vy[i];
-    a[2] += tz - g * s.vz[i];
+    const double ts = trap_scale(p, s, i);
+    const double g = p.gamma / ion_mass(p, s, i);
+    a[0] += ts * tx - g * s.vx[i];
+    a[1] += ts * ty - g * s.vy[i];
+    a[2] += ts * tz - g * s.vz[i];
   }
   s.ax[i] = a[0];
   s.ay[i] = a[1];
@@ -93,16 +95,17 @@ __global__ void k_epi_vjp(Phys p, StateView s, const double *__restrict__ part, 
                           int flags, double t) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
-  const double pref = coulomb_pref(p, s.q, i);
+  const double pref = coulomb_pref(p, s, i);
   double g[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) g[c] = pref * chunk_sum(part, n_jc, 3, c, s.n, i);
   if (flags & NB_ACC_TOTAL) {
     double tx, ty, tz;  // the trap term is linear: its Jacobian applied to lambda
     trap_accel(p, t, lx[i], ly[i], lz[i], tx, ty, tz);
-    g[0] += tx;
-    g[1] += ty;
-    g[2] += tz;
+    const double ts = trap_scale(p, s, i);
+    g[0] += ts * tx;
+    g[1] += ts * ty;
+    g[2] += ts * tz;
   }
   gx[i] = g[0];
   gy[i] = g[1];
@@ -151,16 +154,21 @@ __global__ void k_epi_step(Phys p, StateView s, const double *__restrict__ cx,
   if (i >= s.n) return;
   const double dt = p.dt;
   const double t = p.t0 + (double)snew * dt;
-  const double pref = coulomb_pref(p, s.q, i);
+  const double pref = coulomb_pref(p, s, i);
   const double r[3] = {cx[i], cy[i], cz[i]};
   double tr[3];
   trap_accel(p, t, r[0], r[1], r[2], tr[0], tr[1], tr[2]);
-  const double c = p.gamma * dt / (2.0 * p.mass);
-  const double g = p.gamma / p.mass;
+  const double ts = trap_scale(p, s, i);
+  tr[0] *= ts;
+  tr[1] *= ts;
+  tr[2] *= ts;
+  const double mi = ion_mass(p, s, i);
+  const double c = p.gamma * dt / (2.0 * mi);
+  const double g = p.gamma / mi;
   double xi[3] = {0.0, 0.0, 0.0};
   double sig = 0.0;
   if (p.noise_T > 0.0) {
-    sig = sqrt(2.0 * p.gamma * KB * p.noise_T * dt) / p.mass;
+    sig = sqrt(2.0 * p.gamma * KB * p.noise_T * dt) / mi;
     normals3(p.seed, p.instance, snew, i, xi);
   }
   double *vs[3] = {s.vx, s.vy, s.vz};
@@ -228,11 +236,12 @@ __global__ void __launch_bounds__(ENERGY_THREADS) k_energy_part(Phys p, StateVie
   for (int64_t i = (int64_t)blockIdx.x * ENERGY_THREADS + threadIdx.x; i < s.n; i += stride) {
     const double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
     const double x = s.x[i], y = s.y[i], z = s.z[i];
-    acc[0] += 0.5 * p.mass * (vx * vx + vy * vy + vz * vz);
+    const double mi = ion_mass(p, s, i), ts = trap_scale(p, s, i);
+    acc[0] += 0.5 * mi * (vx * vx + vy * vy + vz * vz);
     if (p.trap == NB_TRAP_RF)
-      acc[1] += 0.5 * p.mass * (ctrap * (x * x - y * y) + w2[2] * z * z);
+      acc[1] += 0.5 * mi * ts * (ctrap * (x * x - y * y) + w2[2] * z * z);
     else
-      acc[1] += 0.5 * p.mass * (w2[0] * x * x + w2[1] * y * y + w2[2] * z * z);
+      acc[1] += 0.5 * mi * ts * (w2[0] * x * x + w2[1] * y * y + w2[2] * z * z);
     const double qi = s.q ? s.q[i] : p.charge;
     const double qw = s.q ? qi : qi * p.charge;  // phi carries w_j = q_j or 1
     acc[2] += 0.5 * p.k_coulomb * qw * chunk_sum(phi, n_jc, 1, 0, s.n, i);

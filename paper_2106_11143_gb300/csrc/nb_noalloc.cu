@@ -118,6 +118,7 @@ extern "C" nb_status nb_energy_noalloc(const nb_params *params, const nb_system 
   v.vx = sys->vx; v.vy = sys->vy; v.vz = sys->vz;
   v.ax = sys->ax; v.ay = sys->ay; v.az = sys->az;
   v.q = sys->q;
+  v.m = sys->m;
   const double t = params->t0 + (double)sys->step * params->dt;
   cudaStream_t st = (cudaStream_t)stream;
   if (launch_pair_phi(pl, n, sys->x, sys->y, sys->z, sys->q, params->charge, params->soft2,

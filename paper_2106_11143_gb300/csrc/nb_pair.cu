@@ -56,6 +56,34 @@ __device__ __forceinline__ void pair_f64(double xi, double yi, double zi, const 
   az = fma(dz, s, az);
 }
 
+// FP64 pair term with the 1/sqrt method of the ladder (Sec. IV): SQRT+DIV,
+// the bare seed, or the seed refined by y <- y (3 - r^2 y^2) / 2 once or
+// twice (the recurrence of Sec. IV); then r^-3 = y^3.
+template <int MODE, bool QARR>
+__device__ __forceinline__ void pair_ladder(double xi, double yi, double zi, const D4 &pj,
+                                            double soft2, double &ax, double &ay, double &az) {
+  const double dx = xi - pj.x;
+  const double dy = yi - pj.y;
+  const double dz = zi - pj.z;
+  const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
+  double y;
+  if (MODE == MODE_SQRTDIV) {
+    y = (r2 > 0.0) ? 1.0 / sqrt(r2) : 0.0;
+  } else {
+    y = rsqrt_seed_f64(r2);
+    if (MODE == MODE_RSQ_NR1 || MODE == MODE_RSQ_NR2) {
+      const double h = 0.5 * r2;
+      y = y * fma(-h * y, y, 1.5);
+      if (MODE == MODE_RSQ_NR2) y = y * fma(-h * y, y, 1.5);
+    }
+  }
+  double s = (y * y) * y;
+  if (QARR) s *= pj.w;
+  ax = fma(dx, s, ax);
+  ay = fma(dy, s, ay);
+  az = fma(dz, s, az);
+}
+
 // FP32 bulk shared by the two mixed modes: given the FP32 displacement,
 // acc += w_j d / s^3 with s^-3 = y^3 (1 + 3/2 e), y = MUFU.RSQ(s^2),
 // e = 1 - s^2 y^2 (one first-order correction in FP32).
@@ -232,6 +260,15 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
         for (int r = 0; r < R; ++r)
           pair_f64<QARR>(xi[r], yi[r], zi[r], pj, soft2, ad[r][0], ad[r][1], ad[r][2]);
       }
+    } else if (MODE >= MODE_SQRTDIV) {
+      const D4 *s4 = reinterpret_cast<const D4 *>(smem_raw);
+#pragma unroll 2
+      for (int k = 0; k < cnt; ++k) {
+        const D4 pj = s4[k];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          pair_ladder<MODE, QARR>(xi[r], yi[r], zi[r], pj, soft2, ad[r][0], ad[r][1], ad[r][2]);
+      }
     } else if (MODE == MODE_DF64) {
       const D4 *s4 = reinterpret_cast<const D4 *>(smem_raw);
       float al[R][3];
@@ -296,7 +333,7 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         part[((int64_t)blockIdx.y * 3 + c) * n + i] =
-            (MODE == MODE_FP64 || MODE == MODE_DF64) ? ad[r][c] : ad[r][c] + cd[r][c];
+            (fp64_like(MODE) || MODE == MODE_DF64) ? ad[r][c] : ad[r][c] + cd[r][c];
     }
   }
 }
@@ -461,6 +498,10 @@ cudaError_t launch_pair_force(const Plan &pl, int mode, int64_t n, const double 
     case MODE_MIXED: return launch_force_m<MODE_MIXED>(pl, n, x, y, z, q, pf, soft2, part, st);
     case MODE_SPLIT: return launch_force_m<MODE_SPLIT>(pl, n, x, y, z, q, pf, soft2, part, st);
     case MODE_DF64: return launch_force_m<MODE_DF64>(pl, n, x, y, z, q, pf, soft2, part, st);
+    case MODE_SQRTDIV: return launch_force_m<MODE_SQRTDIV>(pl, n, x, y, z, q, pf, soft2, part, st);
+    case MODE_RSQ: return launch_force_m<MODE_RSQ>(pl, n, x, y, z, q, pf, soft2, part, st);
+    case MODE_RSQ_NR1: return launch_force_m<MODE_RSQ_NR1>(pl, n, x, y, z, q, pf, soft2, part, st);
+    case MODE_RSQ_NR2: return launch_force_m<MODE_RSQ_NR2>(pl, n, x, y, z, q, pf, soft2, part, st);
     default: return cudaErrorInvalidValue;
   }
 }

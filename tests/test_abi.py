@@ -48,7 +48,9 @@ def test_struct_layout_matches_header():
     # nb_params: 4 doubles, 2 int32, 6 doubles, 7 doubles, uint64, 2 uint32
     assert ctypes.sizeof(api.NbParams) == 4 * 8 + 8 + 6 * 8 + 7 * 8 + 8 + 8
     assert api.NbParams.seed.offset == 4 * 8 + 8 + 6 * 8 + 7 * 8
-    assert ctypes.sizeof(api.NbSystem) == 8 + 10 * 8 + 8
+    # n, 9 state pointers, q, step, m
+    assert ctypes.sizeof(api.NbSystem) == 8 + 10 * 8 + 8 + 8
+    assert api.NbSystem.m.offset == 8 + 10 * 8 + 8
 
 
 def test_invalid_arguments_rejected_on_host(libnb):

@@ -1,0 +1,52 @@
+"""The 1/sqrt precision ladder (Sec. IV): every method against the oracle,
+with the error each one's arithmetic allows, and their ordering."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2106_11143_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# conditioned-error bounds: the seed's ~2^-22 error, tripled by the cube
+# (rsq); one Newton step squares it (about 1.5 e^2, x3); two steps and
+# SQRT+DIV reach FP64 rounding.
+BOUND = {"sqrtdiv": 2e-14, "rsq": 3e-6, "rsq_nr1": 1e-11, "rsq_nr2": 2e-14}
+
+
+@pytest.fixture(scope="module")
+def nb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_11143_gb300 as nbm
+    nbm.lib()
+    return nbm
+
+
+def test_ladder_accuracy_and_order(nb, orc):
+    n = 2049
+    pos, _ = W.random_cloud(n, seed=13)
+    phys = W.phys()
+    ax, ay, az, _, absf = orc.coulomb(orc.make_params(**phys), *pos, want_absf=True)
+    ref = np.stack([ax, ay, az])
+    errs = {}
+    for m, bound in BOUND.items():
+        s = nb.System(pos)
+        nb.forces(nb.Params.from_phys(phys, precision=m), s)
+        nb.sync_status()
+        g = s.acc().cpu().numpy()
+        errs[m] = float(np.max(np.sqrt(np.sum((g - ref) ** 2, axis=0)) / absf))
+        assert errs[m] <= bound, (m, errs[m])
+    print(errs)
+    assert errs["rsq"] > 1e3 * errs["rsq_nr1"]
+    assert errs["rsq_nr1"] > errs["rsq_nr2"]
+
+
+def test_ladder_chain_experiment_runs(nb):
+    from paper_2106_11143_gb300 import ladder
+    r = ladder.chain(methods=["sqrtdiv", "rsq", "rsq_nr1", "fp64"], steps=400)
+    print(r)
+    assert r["sqrtdiv"] == 0.0
+    assert 0.0 < r["rsq"] < 1e-3
+    assert r["rsq_nr1"] < r["rsq"]
+    assert 0.12 < r["q_mathieu"] < 0.25
