@@ -142,6 +142,53 @@ __device__ __forceinline__ void split_f64(double d, float &h, float &l) {
   l = __int2float_rn(r) * scale;
 }
 
+// Error-free FP32 sum: s + e == a + b exactly (Knuth TwoSum).
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Double-float pair term: y larger than 2^42 would overflow y^3 (1 + c) in
+// FP32; real pairs need |r_i - r_j| >= 2.3e-13 (caller's length unit).
+constexpr float DF_YMAX = 4.398046511104e12f;  // 2^42
+
+// Double-float r^-3 (sh + sl) of the FP64 displacement split into FP32
+// (hi, lo) parts dh, dl (see pair_df64): double-float r^2 from exact
+// products and TwoSums, FP32 seed, compensated Newton residual, y^3 as a
+// double-float.  Relative error about 2^-44.
+__device__ __forceinline__ void df_rinv3(const float dh[3], const float dl[3], float s2h, float s2l,
+                                         float &sh, float &sl) {
+  const float p0 = dh[0] * dh[0], p1 = dh[1] * dh[1], p2 = dh[2] * dh[2];
+  const float e0 = fmaf(dh[0], dh[0], -p0), e1 = fmaf(dh[1], dh[1], -p1), e2 = fmaf(dh[2], dh[2], -p2);
+  float h, t1, t2;
+  two_sum_f(p0, p1, h, t1);
+  two_sum_f(h, p2, h, t2);
+  float l = (t1 + t2) + (e0 + e1 + e2);
+  l = fmaf(dh[0] + dh[0], dl[0], l);
+  l = fmaf(dh[1] + dh[1], dl[1], l);
+  l = fmaf(dh[2] + dh[2], dl[2], l);
+  if (s2h != 0.0f) {
+    float t3;
+    two_sum_f(h, s2h, h, t3);
+    l += t3 + s2l;
+  }
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(h));
+  y = fminf(y, DF_YMAX);
+  const float y2 = y * y;
+  const float y2e = fmaf(y, y, -y2);
+  float r = fmaf(-h, y2, 1.0f);
+  r = fmaf(-h, y2e, r);
+  r = fmaf(-l, y2, r);
+  const float c = r * fmaf(r, 1.875f, 1.5f);
+  const float y3h = y2 * y;
+  float y3e = fmaf(y2, y, -y3h);
+  y3e = fmaf(y2e, y, y3e);
+  sh = y3h;
+  sl = fmaf(y3h, c, y3e);
+}
+
 // Exact FP32 -> FP64 widening by integer ops, for normal or zero inputs
 // (subnormal FP32 inputs flush to zero).
 __device__ __forceinline__ double f32_to_f64(float f) {
@@ -207,6 +254,10 @@ struct Plan {
   int64_t jchunk = 0;
   int n_it = 0;
   int n_jc = 0;
+  // symmetric (half-pair) force kernel: blocks of 32 G ions; n_jc = number
+  // of blocks (one partial per partner block)
+  int sym = 0;
+  int G = 0;
 };
 
 Plan make_plan(int64_t n, int mode, int kind);  // kind: 0 force, 1 phi, 2 vjp
@@ -236,6 +287,9 @@ cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const do
                             cudaStream_t st);
 cudaError_t launch_split_positions(int64_t n, const double *x, const double *y,
                                    const double *z, float *out6, cudaStream_t st);
+cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
+                            const double *z, const double *q, double soft2, double *part,
+                            cudaStream_t st);
 
 // Epilogue kernels (nb_integrate.cu).
 struct StateView {

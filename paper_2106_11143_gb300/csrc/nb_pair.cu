@@ -114,16 +114,6 @@ __device__ __forceinline__ void pair_f32_bulk(float fx, float fy, float fz, floa
 // TwoSum into a per-tile double-float, flushed into FP64 once per tile.
 // Relative error per pair about 2^-44 (the residual's FP32 roundings).
 
-__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// y larger than 2^42 would overflow y^3 (1 + c) in FP32; real pairs need
-// |r_i - r_j| >= 2.3e-13 (in the caller's length unit) for this mode.
-constexpr float DF_YMAX = 4.398046511104e12f;  // 2^42
-
 template <bool QARR>
 __device__ __forceinline__ void pair_df64(double xi, double yi, double zi, const D4 &pj,
                                           float s2h, float s2l, float ah[3], float al[3]) {
@@ -131,36 +121,8 @@ __device__ __forceinline__ void pair_df64(double xi, double yi, double zi, const
   split_f64(xi - pj.x, dh[0], dl[0]);
   split_f64(yi - pj.y, dh[1], dl[1]);
   split_f64(zi - pj.z, dh[2], dl[2]);
-  // r^2 = sum_k (dh + dl)^2 (+ soft2) as a double-float (h, l)
-  const float p0 = dh[0] * dh[0], p1 = dh[1] * dh[1], p2 = dh[2] * dh[2];
-  const float e0 = fmaf(dh[0], dh[0], -p0), e1 = fmaf(dh[1], dh[1], -p1), e2 = fmaf(dh[2], dh[2], -p2);
-  float h, t1, t2;
-  two_sum_f(p0, p1, h, t1);
-  two_sum_f(h, p2, h, t2);
-  float l = (t1 + t2) + (e0 + e1 + e2);
-  l = fmaf(dh[0] + dh[0], dl[0], l);
-  l = fmaf(dh[1] + dh[1], dl[1], l);
-  l = fmaf(dh[2] + dh[2], dl[2], l);
-  if (s2h != 0.0f) {
-    float t3;
-    two_sum_f(h, s2h, h, t3);
-    l += t3 + s2l;
-  }
-  // r^-3 = y^3 (1 + c), y = MUFU.RSQ(h), c from the residual 1 - (h + l) y^2
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(h));
-  y = fminf(y, DF_YMAX);
-  const float y2 = y * y;
-  const float y2e = fmaf(y, y, -y2);
-  float r = fmaf(-h, y2, 1.0f);
-  r = fmaf(-h, y2e, r);
-  r = fmaf(-l, y2, r);
-  const float c = r * fmaf(r, 1.875f, 1.5f);
-  const float y3h = y2 * y;
-  float y3e = fmaf(y2, y, -y3h);
-  y3e = fmaf(y2e, y, y3e);
-  float sh = y3h;
-  float sl = fmaf(y3h, c, y3e);
+  float sh, sl;
+  df_rinv3(dh, dl, s2h, s2l, sh, sl);
   if (QARR) {  // times q_j, carried as an FP32 pair in the staged entry's w
     const float2 q = *reinterpret_cast<const float2 *>(&pj.w);
     const float ph = sh * q.x;
@@ -493,6 +455,7 @@ static cudaError_t launch_force_m(const Plan &pl, int64_t n, const double *x, co
 cudaError_t launch_pair_force(const Plan &pl, int mode, int64_t n, const double *x,
                               const double *y, const double *z, const double *q,
                               const PosF32 &pf, double soft2, double *part, cudaStream_t st) {
+  if (pl.sym) return launch_pair_sym(mode, n, pl.n_jc, pl.G, x, y, z, q, soft2, part, st);
   switch (mode) {
     case MODE_FP64: return launch_force_m<MODE_FP64>(pl, n, x, y, z, q, pf, soft2, part, st);
     case MODE_MIXED: return launch_force_m<MODE_MIXED>(pl, n, x, y, z, q, pf, soft2, part, st);
@@ -584,6 +547,25 @@ bool tuning_lookup(int kind, int mode, int64_t n, int *block, int *R, int *bps) 
 
 Plan make_plan(int64_t n, int mode, int kind) {
   Plan pl;
+  // Symmetric half-pair kernel for the FP64-pipe-bound force paths, when the
+  // per-partner-block partials (nbk * 3n doubles) stay below 2 GB.
+  if (kind == 0 && (mode == MODE_FP64 || mode == MODE_DF64)) {
+    int G = n >= 60000 ? 32 : (n >= 30000 ? 16 : 8);
+    bool use = n >= 16384;
+    int tb = 0, tr = 0, tbps = 0;
+    if (tuning_lookup(4, mode, n, &tb, &tr, &tbps)) {
+      use = tr != 0;
+      G = tb / 32;
+    }
+    const int64_t nbk = (n + 32 * G - 1) / (32 * G);
+    if (use && (double)nbk * 3.0 * (double)n * 8.0 <= 2e9) {
+      pl.sym = 1;
+      pl.G = G;
+      pl.n_jc = (int)nbk;
+      pl.block = 256;
+      return pl;
+    }
+  }
   int bps;
   if (kind == 0) {
     // force kernel: shapes found by the autotuner on GB300 (tune.py)

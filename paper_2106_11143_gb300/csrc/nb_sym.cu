@@ -1,0 +1,328 @@
+// nb_sym.cu -- symmetric (half-pair) force kernel: each unordered pair of ions
+// is evaluated once and its force is applied to both ions with opposite
+// signs (Newton's third law), halving the pair arithmetic of the FP64-pipe
+// bound precisions (fp64, df64).
+//
+// Ions are grouped in blocks of BI = 32 G ions (G tiles of one warp).  One
+// CTA handles one work item, a block pair (P, Q) with P <= Q:
+//  - P < Q: both blocks' positions are staged in shared memory together with
+//    FP64 accumulators for P.  Each warp takes Q-tiles; for a Q-tile it
+//    visits the G P-tiles in the staggered order pt = (qs + k) mod G, one
+//    per __syncthreads-separated step k, so at any step the warps hold
+//    distinct P-tiles.  Within a step lane l holds P-ion l; the Q-tile's
+//    positions and its force accumulators rotate one lane per iteration
+//    (warp shuffles), so after 32 iterations every (P-ion, Q-ion) pair of
+//    the two tiles has been evaluated once and the Q data is back home.
+//  - P == Q: the block's internal pairs, one-sided (each ion against all
+//    others of the block).
+// Output: ion i of block B gets one partial sum per partner block X, in
+// part[(X*3 + c)*n + i]; the epilogue kernels add the nbk partials in block
+// order.  No atomics; the order of every sum is fixed, so the result is
+// bitwise reproducible.
+//
+// With per-ion charges the two sides carry different weights: ion i gets
+// q_j d/r^3 and ion j gets -q_i d/r^3 (the partial sums exclude the ion's own
+// charge, as in the one-sided kernel).  The ragged last block is padded with
+// weight-0 ions far away; only items that touch it apply the weights when
+// the charge is uniform.
+#include <algorithm>
+#include <mutex>
+
+#include "nb_common.cuh"
+
+namespace nb {
+
+constexpr int SYM_THREADS = 256;
+constexpr int SYM_W = SYM_THREADS / 32;
+constexpr double SYM_FAR = 1e18;
+
+struct __align__(16) SD4 {
+  double x, y, z, w;
+};
+
+__device__ __forceinline__ double shfl_next(double v, int lane) {
+  return __shfl_sync(0xffffffffu, v, (lane + 1) & 31);
+}
+__device__ __forceinline__ float shfl_next(float v, int lane) {
+  return __shfl_sync(0xffffffffu, v, (lane + 1) & 31);
+}
+
+// One 32x32 tile step for the FP64 pair arithmetic.  pp: this lane's P-ion;
+// qd: the Q-ion currently held (rotating); b: its accumulators
+// (rotating); a: the P-ion's accumulators.
+template <bool W>
+__device__ __forceinline__ void sym_step_fp64(const SD4 &pp, SD4 qd, double soft2, int lane,
+                                              double a[3], double b[3]) {
+#pragma unroll 2
+  for (int r = 0; r < 32; ++r) {
+    const double dx = pp.x - qd.x, dy = pp.y - qd.y, dz = pp.z - qd.z;
+    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
+    const double s = rinv3_f64(r2);
+    const double sp = W ? s * qd.w : s;
+    const double sq = W ? s * pp.w : s;
+    a[0] = fma(dx, sp, a[0]);
+    a[1] = fma(dy, sp, a[1]);
+    a[2] = fma(dz, sp, a[2]);
+    b[0] = fma(-dx, sq, b[0]);
+    b[1] = fma(-dy, sq, b[1]);
+    b[2] = fma(-dz, sq, b[2]);
+    qd.x = shfl_next(qd.x, lane);
+    qd.y = shfl_next(qd.y, lane);
+    qd.z = shfl_next(qd.z, lane);
+    if (W) qd.w = shfl_next(qd.w, lane);
+    b[0] = shfl_next(b[0], lane);
+    b[1] = shfl_next(b[1], lane);
+    b[2] = shfl_next(b[2], lane);
+  }
+}
+
+// The same step with double-float pair arithmetic (see pair_df64).  The
+// weights w (charge, or 1 / 0 for real / padding ions) are FP64; a, b are
+// double-float (h, l) accumulators for this step.
+template <bool W>
+__device__ __forceinline__ void sym_step_df64(const SD4 &pp, SD4 qd, float s2h, float s2l, int lane,
+                                              float ah[3], float al[3], float bh[3], float bl[3]) {
+  float wph = 1.0f, wpl = 0.0f;
+  if (W) split_f64(pp.w, wph, wpl);
+#pragma unroll 1
+  for (int r = 0; r < 32; ++r) {
+    float dh[3], dl[3];
+    split_f64(pp.x - qd.x, dh[0], dl[0]);
+    split_f64(pp.y - qd.y, dh[1], dl[1]);
+    split_f64(pp.z - qd.z, dh[2], dl[2]);
+    float sh, sl;
+    df_rinv3(dh, dl, s2h, s2l, sh, sl);
+    // weights: P-side times w_q, Q-side times w_p (double-float products)
+    float sph = sh, spl = sl, sqh = sh, sql = sl;
+    if (W) {
+      float wqh, wql;
+      split_f64(qd.w, wqh, wql);
+      sph = sh * wqh;
+      spl = fmaf(sh, wql, fmaf(sl, wqh, fmaf(sh, wqh, -sph)));
+      sqh = sh * wph;
+      sql = fmaf(sh, wpl, fmaf(sl, wph, fmaf(sh, wph, -sqh)));
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float ph = dh[k] * sph;
+      float pl = fmaf(dh[k], spl, fmaf(dl[k], sph, fmaf(dh[k], sph, -ph)));
+      float s, t;
+      two_sum_f(ah[k], ph, s, t);
+      ah[k] = s;
+      al[k] += t + pl;
+      if (W) {
+        ph = dh[k] * sqh;
+        pl = fmaf(dh[k], sql, fmaf(dl[k], sqh, fmaf(dh[k], sqh, -ph)));
+      }
+      two_sum_f(bh[k], -ph, s, t);
+      bh[k] = s;
+      bl[k] += t - pl;
+    }
+    qd.x = shfl_next(qd.x, lane);
+    qd.y = shfl_next(qd.y, lane);
+    qd.z = shfl_next(qd.z, lane);
+    if (W) qd.w = shfl_next(qd.w, lane);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      bh[k] = shfl_next(bh[k], lane);
+      bl[k] = shfl_next(bl[k], lane);
+    }
+  }
+}
+
+template <int MODE, bool W>
+__device__ __forceinline__ void sym_offdiag(const SD4 *posP, const SD4 *posQ, double *accP, int G,
+                                            int BI, double soft2, float s2h, float s2l, int64_t n,
+                                            int P, int64_t q0, int nq, double *part) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int qs = warp; qs < G; qs += SYM_W) {
+    const SD4 qh = posQ[qs * 32 + lane];
+    double aq[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < G; ++k) {
+      const int pt = (qs + k) % G;
+      __syncthreads();  // all warps are at step k: their P-tiles are distinct
+      const SD4 pp = posP[pt * 32 + lane];
+      const int ip = pt * 32 + lane;
+      if (MODE == MODE_DF64) {
+        float ah[3] = {0, 0, 0}, al[3] = {0, 0, 0}, bh[3] = {0, 0, 0}, bl[3] = {0, 0, 0};
+        sym_step_df64<W>(pp, qh, s2h, s2l, lane, ah, al, bh, bl);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          accP[c * BI + ip] += f32_to_f64(ah[c]) + f32_to_f64(al[c]);
+          aq[c] += f32_to_f64(bh[c]) + f32_to_f64(bl[c]);
+        }
+      } else {
+        double a[3] = {0.0, 0.0, 0.0}, b[3] = {0.0, 0.0, 0.0};
+        sym_step_fp64<W>(pp, qh, soft2, lane, a, b);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          accP[c * BI + ip] += a[c];
+          aq[c] += b[c];
+        }
+      }
+    }
+    const int iq = qs * 32 + lane;
+    if (iq < nq)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + q0 + iq] = aq[c];
+  }
+}
+
+template <int MODE, bool QARR>
+__global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, int G,
+                                                         const double *__restrict__ x,
+                                                         const double *__restrict__ y,
+                                                         const double *__restrict__ z,
+                                                         const double *__restrict__ q, double soft2,
+                                                         double *__restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int BI = 32 * G;
+  SD4 *posP = reinterpret_cast<SD4 *>(smem_raw);
+  SD4 *posQ = posP + BI;
+  double *accP = reinterpret_cast<double *>(posQ + BI);  // [3][BI]
+  int t = blockIdx.x, P = 0;
+  while (t >= nbk - P) {  // item -> (P, Q), P <= Q, row by row
+    t -= nbk - P;
+    ++P;
+  }
+  const int Q = P + t;
+  const int64_t p0 = (int64_t)P * BI, q0 = (int64_t)Q * BI;
+  const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < BI; i += SYM_THREADS) {
+    SD4 e;
+    if (i < np) {
+      e.x = x[p0 + i]; e.y = y[p0 + i]; e.z = z[p0 + i]; e.w = QARR ? q[p0 + i] : 1.0;
+    } else {
+      e.x = SYM_FAR; e.y = SYM_FAR; e.z = SYM_FAR; e.w = 0.0;
+    }
+    posP[i] = e;
+    if (P != Q) {
+      if (i < nq) {
+        e.x = x[q0 + i]; e.y = y[q0 + i]; e.z = z[q0 + i]; e.w = QARR ? q[q0 + i] : 1.0;
+      } else {
+        e.x = SYM_FAR; e.y = SYM_FAR; e.z = SYM_FAR; e.w = 0.0;
+      }
+      posQ[i] = e;
+    }
+    accP[i] = 0.0;
+    accP[BI + i] = 0.0;
+    accP[2 * BI + i] = 0.0;
+  }
+  float s2h = 0.0f, s2l = 0.0f;
+  if (MODE == MODE_DF64) split_f64(soft2, s2h, s2l);
+  __syncthreads();
+
+  if (P == Q) {  // the block's own pairs, one-sided
+    for (int i = tid; i < np; i += SYM_THREADS) {
+      const SD4 pi = posP[i];
+      double a[3] = {0.0, 0.0, 0.0};
+      if (MODE == MODE_DF64) {
+        float ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
+        for (int j = 0; j < np; ++j) {
+          const SD4 pj = posP[j];
+          float dh[3], dl[3];
+          split_f64(pi.x - pj.x, dh[0], dl[0]);
+          split_f64(pi.y - pj.y, dh[1], dl[1]);
+          split_f64(pi.z - pj.z, dh[2], dl[2]);
+          float sh, sl;
+          df_rinv3(dh, dl, s2h, s2l, sh, sl);
+          if (QARR) {
+            float wh, wl;
+            split_f64(pj.w, wh, wl);
+            const float ph = sh * wh;
+            sl = fmaf(sh, wl, fmaf(sl, wh, fmaf(sh, wh, -ph)));
+            sh = ph;
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float ph = dh[k] * sh;
+            const float pl = fmaf(dh[k], sl, fmaf(dl[k], sh, fmaf(dh[k], sh, -ph)));
+            float s, tt;
+            two_sum_f(ah[k], ph, s, tt);
+            ah[k] = s;
+            al[k] += tt + pl;
+          }
+          if ((j & 255) == 255) {  // flush the double-float sum every 256 pairs
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              a[k] += f32_to_f64(ah[k]) + f32_to_f64(al[k]);
+              ah[k] = al[k] = 0.0f;
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] += f32_to_f64(ah[k]) + f32_to_f64(al[k]);
+      } else {
+        for (int j = 0; j < np; ++j) {
+          const SD4 pj = posP[j];
+          const double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+          const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
+          double s = rinv3_f64(r2);
+          if (QARR) s *= pj.w;
+          a[0] = fma(dx, s, a[0]);
+          a[1] = fma(dy, s, a[1]);
+          a[2] = fma(dz, s, a[2]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + p0 + i] = a[c];
+    }
+    return;
+  }
+
+  const bool weighted = QARR || np < BI || nq < BI;
+  if (weighted)
+    sym_offdiag<MODE, true>(posP, posQ, accP, G, BI, soft2, s2h, s2l, n, P, q0, nq, part);
+  else
+    sym_offdiag<MODE, false>(posP, posQ, accP, G, BI, soft2, s2h, s2l, n, P, q0, nq, part);
+  __syncthreads();
+  for (int i = tid; i < np; i += SYM_THREADS)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) part[((int64_t)Q * 3 + c) * n + p0 + i] = accP[c * BI + i];
+}
+
+size_t sym_smem_bytes(int G) { return (size_t)32 * G * (2 * sizeof(SD4) + 3 * sizeof(double)); }
+
+template <int MODE>
+static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, const double *y,
+                                const double *z, const double *q, double soft2, double *part,
+                                cudaStream_t st) {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!done[dev]) {
+      const int lim = (int)sym_smem_bytes(32);
+      e = cudaFuncSetAttribute(k_pair_sym<MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pair_sym<MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e != cudaSuccess) return e;
+      done[dev] = true;
+    }
+  }
+  const int items = nbk * (nbk + 1) / 2;
+  const size_t smem = sym_smem_bytes(G);
+  if (q)
+    k_pair_sym<MODE, true><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, soft2, part);
+  else
+    k_pair_sym<MODE, false><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, soft2, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
+                            const double *z, const double *q, double soft2, double *part,
+                            cudaStream_t st) {
+  if (G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
+  switch (mode) {
+    case MODE_FP64: return launch_sym_m<MODE_FP64>(n, nbk, G, x, y, z, q, soft2, part, st);
+    case MODE_DF64: return launch_sym_m<MODE_DF64>(n, nbk, G, x, y, z, q, soft2, part, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace nb

@@ -279,3 +279,41 @@ def test_nonfinite_detected(nb):
         nb.sync_status()
     assert ei.value.status == 3
     nb.sync_status()  # cleared
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_symmetric_kernel_small_and_ragged(nb, orc, precision):
+    """The half-pair kernel (Newton's third law), forced on at small n with
+    every block size, including ragged last blocks, charges and softening."""
+    rng = np.random.default_rng(17)
+    try:
+        for k, (n, block) in enumerate([(2, 256), (257, 256), (1000, 256), (2049, 512), (4100, 1024),
+                                        (6000, 512)]):
+            nb.set_tuning("symmetric", precision, 1, 1 << 40, block, R=1)
+            pos, _ = W.random_cloud(n, seed=300 + k)
+            q = W.E_CHARGE * rng.choice([-1.0, 1.0, 2.0], size=n) if k % 2 else None
+            soft2 = (0.1e-6) ** 2 if k == 3 else 0.0
+            phys = W.phys(soft2=soft2)
+            g = gpu_forces(nb, phys, pos, q=q, precision=precision)
+            ax, ay, az, _, absf = orc.coulomb(oparams(orc, phys), *pos, q=q, want_absf=True)
+            e = cond_err(g, np.stack([ax, ay, az]), absf)
+            assert e <= 1e-12, (n, block, e)
+            g2 = gpu_forces(nb, phys, pos, q=q, precision=precision)
+            assert np.array_equal(g, g2)
+    finally:
+        nb.set_tuning("force", "fp64", 0, 0, 0)
+
+
+def test_symmetric_matches_one_sided_at_scale(nb):
+    """At N = 20000 (symmetric by default) the half-pair and the one-sided
+    kernels agree to FP64 rounding (conditioned by the largest force)."""
+    pos, _ = W.random_cloud(20000, seed=41, semi_axes=(200e-6, 200e-6, 1000e-6))
+    phys = W.phys()
+    a = gpu_forces(nb, phys, pos, precision="fp64")
+    try:
+        nb.set_tuning("symmetric", "fp64", 1, 1 << 40, 256, R=0)
+        b = gpu_forces(nb, phys, pos, precision="fp64")
+    finally:
+        nb.set_tuning("force", "fp64", 0, 0, 0)
+    assert not np.array_equal(a, b)  # genuinely different summation orders
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
