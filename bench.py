@@ -250,7 +250,7 @@ def run_e2e(nb, w, precision, steps, world, flush):
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
 
-SYMMETRIC = {"fp64", "df64"}  # half-pair kernel at N >= 16384
+SYMMETRIC = {"fp64", "df64", "mixed", "mixed_split"}  # half-pair kernel at N >= 16384
 
 
 def roofline(path, n, kernel_ms):
@@ -263,8 +263,9 @@ def roofline(path, n, kernel_ms):
                         % ("2 FP64" if PATH_PEAK[path] == "fp64" else "128 FP32"),
          "convention": "A: 20 flops per pair interaction"}
     if path in SYMMETRIC and n >= 16384:
-        r["note"] = ("half-pair kernel: one evaluation serves both ions of a pair, so convention-A "
-                     "flops per second can exceed the pipe peak; pipe utilisation is in profiles/")
+        r["note"] = ("half-pair kernel: one pair evaluation serves both ions, so convention-A flops "
+                     "(20 per interaction) per second can exceed the pipe peak; per-pipe "
+                     "utilisation from ncu is in profiles/")
     return r
 
 

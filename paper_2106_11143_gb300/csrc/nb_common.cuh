@@ -189,6 +189,40 @@ __device__ __forceinline__ void df_rinv3(const float dh[3], const float dl[3], f
   sl = fmaf(y3h, c, y3e);
 }
 
+// FP32 bulk shared by the two mixed modes: given the FP32 displacement,
+// acc += w_j d / s^3 with s^-3 = y^3 (1 + 3/2 e), y = MUFU.RSQ(s^2),
+// e = 1 - s^2 y^2 (one first-order correction in FP32).
+template <bool QARR>
+__device__ __forceinline__ void pair_f32_bulk(float fx, float fy, float fz, float qj,
+                                              float soft2f, float &ax, float &ay, float &az) {
+  const float r2 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, soft2f)));
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+  y = (r2 > 0.0f) ? y : 0.0f;
+  const float y2 = y * y;
+  const float e15 = fmaf(-1.5f * r2, y2, 1.5f);
+  const float y3 = y2 * y;
+  float s = fmaf(y3, e15, y3);
+  if (QARR) s *= qj;
+  ax = fmaf(fx, s, ax);
+  ay = fmaf(fy, s, ay);
+  az = fmaf(fz, s, az);
+}
+
+// FP32 r^-3 of an FP32 displacement (the mixed modes' bulk without the
+// accumulation): y = MUFU.RSQ(r^2) clamped against FP32 overflow, corrected
+// once: s = y^3 (1 + 3/2 e), e = 1 - r^2 y^2.
+__device__ __forceinline__ float f32_rinv3(float fx, float fy, float fz, float soft2f) {
+  const float r2 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, soft2f)));
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+  y = (r2 > 0.0f) ? y : 0.0f;
+  const float y2 = y * y;
+  const float e15 = fmaf(-1.5f * r2, y2, 1.5f);
+  const float y3 = y2 * y;
+  return fmaf(y3, e15, y3);
+}
+
 // Exact FP32 -> FP64 widening by integer ops, for normal or zero inputs
 // (subnormal FP32 inputs flush to zero).
 __device__ __forceinline__ double f32_to_f64(float f) {
@@ -288,8 +322,8 @@ cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const do
 cudaError_t launch_split_positions(int64_t n, const double *x, const double *y,
                                    const double *z, float *out6, cudaStream_t st);
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
-                            const double *z, const double *q, double soft2, double *part,
-                            cudaStream_t st);
+                            const double *z, const double *q, const PosF32 &pf, double soft2,
+                            double *part, cudaStream_t st);
 
 // Epilogue kernels (nb_integrate.cu).
 struct StateView {

@@ -84,26 +84,6 @@ __device__ __forceinline__ void pair_ladder(double xi, double yi, double zi, con
   az = fma(dz, s, az);
 }
 
-// FP32 bulk shared by the two mixed modes: given the FP32 displacement,
-// acc += w_j d / s^3 with s^-3 = y^3 (1 + 3/2 e), y = MUFU.RSQ(s^2),
-// e = 1 - s^2 y^2 (one first-order correction in FP32).
-template <bool QARR>
-__device__ __forceinline__ void pair_f32_bulk(float fx, float fy, float fz, float qj,
-                                              float soft2f, float &ax, float &ay, float &az) {
-  const float r2 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, soft2f)));
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
-  y = (r2 > 0.0f) ? y : 0.0f;
-  const float y2 = y * y;
-  const float e15 = fmaf(-1.5f * r2, y2, 1.5f);
-  const float y3 = y2 * y;
-  float s = fmaf(y3, e15, y3);
-  if (QARR) s *= qj;
-  ax = fmaf(fx, s, ax);
-  ay = fmaf(fy, s, ay);
-  az = fmaf(fz, s, az);
-}
-
 // ---------------------------------------------------------------------------
 // FP64-class pair term on the FP32 pipe ("double-float", MODE_DF64).
 // The displacement is an FP64 subtraction (exact for close pairs), split into
@@ -455,7 +435,7 @@ static cudaError_t launch_force_m(const Plan &pl, int64_t n, const double *x, co
 cudaError_t launch_pair_force(const Plan &pl, int mode, int64_t n, const double *x,
                               const double *y, const double *z, const double *q,
                               const PosF32 &pf, double soft2, double *part, cudaStream_t st) {
-  if (pl.sym) return launch_pair_sym(mode, n, pl.n_jc, pl.G, x, y, z, q, soft2, part, st);
+  if (pl.sym) return launch_pair_sym(mode, n, pl.n_jc, pl.G, x, y, z, q, pf, soft2, part, st);
   switch (mode) {
     case MODE_FP64: return launch_force_m<MODE_FP64>(pl, n, x, y, z, q, pf, soft2, part, st);
     case MODE_MIXED: return launch_force_m<MODE_MIXED>(pl, n, x, y, z, q, pf, soft2, part, st);
@@ -549,8 +529,8 @@ Plan make_plan(int64_t n, int mode, int kind) {
   Plan pl;
   // Symmetric half-pair kernel for the FP64-pipe-bound force paths, when the
   // per-partner-block partials (nbk * 3n doubles) stay below 2 GB.
-  if (kind == 0 && (mode == MODE_FP64 || mode == MODE_DF64)) {
-    int G = n >= 60000 ? 32 : (n >= 30000 ? 16 : 8);
+  if (kind == 0 && (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || mode == MODE_SPLIT)) {
+    int G = n >= 60000 ? 16 : 8;  // the fastest block sizes measured on GB300
     bool use = n >= 16384;
     int tb = 0, tr = 0, tbps = 0;
     if (tuning_lookup(4, mode, n, &tb, &tr, &tbps)) {

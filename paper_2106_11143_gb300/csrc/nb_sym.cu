@@ -3,6 +3,9 @@
 // signs (Newton's third law), halving the pair arithmetic of the FP64-pipe
 // bound precisions (fp64, df64).
 //
+// The split and literal mixed precisions use it too (FP32 pair arithmetic
+// with per-step FP32 partials added into FP64).
+//
 // Ions are grouped in blocks of BI = 32 G ions (G tiles of one warp).  One
 // CTA handles one work item, a block pair (P, Q) with P <= Q:
 //  - P < Q: both blocks' positions are staged in shared memory together with
@@ -130,6 +133,70 @@ __device__ __forceinline__ void sym_step_df64(const SD4 &pp, SD4 qd, float s2h, 
   }
 }
 
+// FP32 weight kept in the low word of a staged entry's w (mixed modes).
+__device__ __forceinline__ float wf32(double w) { return __int_as_float(__double2loint(w)); }
+__device__ __forceinline__ double wpack(float w) { return __hiloint2double(0, __float_as_int(w)); }
+
+// Literal mixed step: FP64 displacement, FP32 bulk, FP32 partials for this
+// step (a: the P-ion, b: the rotating Q-ion).
+template <bool W>
+__device__ __forceinline__ void sym_step_mixed(const SD4 &pp, SD4 qd, float soft2f, int lane,
+                                               float a[3], float b[3]) {
+  const float wp = wf32(pp.w);
+  float wq = wf32(qd.w);
+#pragma unroll 2
+  for (int r = 0; r < 32; ++r) {
+    const float fx = f64_to_f32_rn(pp.x - qd.x);
+    const float fy = f64_to_f32_rn(pp.y - qd.y);
+    const float fz = f64_to_f32_rn(pp.z - qd.z);
+    const float s = f32_rinv3(fx, fy, fz, soft2f);
+    const float sp = W ? s * wq : s, sq = W ? s * wp : s;
+    a[0] = fmaf(fx, sp, a[0]);
+    a[1] = fmaf(fy, sp, a[1]);
+    a[2] = fmaf(fz, sp, a[2]);
+    b[0] = fmaf(-fx, sq, b[0]);
+    b[1] = fmaf(-fy, sq, b[1]);
+    b[2] = fmaf(-fz, sq, b[2]);
+    qd.x = shfl_next(qd.x, lane);
+    qd.y = shfl_next(qd.y, lane);
+    qd.z = shfl_next(qd.z, lane);
+    if (W) wq = shfl_next(wq, lane);
+    b[0] = shfl_next(b[0], lane);
+    b[1] = shfl_next(b[1], lane);
+    b[2] = shfl_next(b[2], lane);
+  }
+}
+
+// Split mixed step: positions as FP32 (hi, lo) pairs (hi.w = weight).
+template <bool W>
+__device__ __forceinline__ void sym_step_split(const float4 &ph, const float4 &pl, float4 qh, float4 ql,
+                                               float soft2f, int lane, float a[3], float b[3]) {
+#pragma unroll 2
+  for (int r = 0; r < 32; ++r) {
+    const float fx = (ph.x - qh.x) + (pl.x - ql.x);
+    const float fy = (ph.y - qh.y) + (pl.y - ql.y);
+    const float fz = (ph.z - qh.z) + (pl.z - ql.z);
+    const float s = f32_rinv3(fx, fy, fz, soft2f);
+    const float sp = W ? s * qh.w : s, sq = W ? s * ph.w : s;
+    a[0] = fmaf(fx, sp, a[0]);
+    a[1] = fmaf(fy, sp, a[1]);
+    a[2] = fmaf(fz, sp, a[2]);
+    b[0] = fmaf(-fx, sq, b[0]);
+    b[1] = fmaf(-fy, sq, b[1]);
+    b[2] = fmaf(-fz, sq, b[2]);
+    qh.x = shfl_next(qh.x, lane);
+    qh.y = shfl_next(qh.y, lane);
+    qh.z = shfl_next(qh.z, lane);
+    if (W) qh.w = shfl_next(qh.w, lane);
+    ql.x = shfl_next(ql.x, lane);
+    ql.y = shfl_next(ql.y, lane);
+    ql.z = shfl_next(ql.z, lane);
+    b[0] = shfl_next(b[0], lane);
+    b[1] = shfl_next(b[1], lane);
+    b[2] = shfl_next(b[2], lane);
+  }
+}
+
 template <int MODE, bool W>
 __device__ __forceinline__ void sym_offdiag(const SD4 *posP, const SD4 *posQ, double *accP, int G,
                                             int BI, double soft2, float s2h, float s2l, int64_t n,
@@ -143,7 +210,22 @@ __device__ __forceinline__ void sym_offdiag(const SD4 *posP, const SD4 *posQ, do
       __syncthreads();  // all warps are at step k: their P-tiles are distinct
       const SD4 pp = posP[pt * 32 + lane];
       const int ip = pt * 32 + lane;
-      if (MODE == MODE_DF64) {
+      if (MODE == MODE_MIXED || MODE == MODE_SPLIT) {
+        float a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+        if (MODE == MODE_MIXED) {
+          sym_step_mixed<W>(pp, qh, (float)soft2, lane, a, b);
+        } else {
+          const float4 *fP = reinterpret_cast<const float4 *>(posP);
+          const float4 *fQ = reinterpret_cast<const float4 *>(posQ);
+          sym_step_split<W>(fP[2 * ip], fP[2 * ip + 1], fQ[2 * (qs * 32 + lane)],
+                            fQ[2 * (qs * 32 + lane) + 1], (float)soft2, lane, a, b);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          accP[c * BI + ip] += f32_to_f64(a[c]);
+          aq[c] += f32_to_f64(b[c]);
+        }
+      } else if (MODE == MODE_DF64) {
         float ah[3] = {0, 0, 0}, al[3] = {0, 0, 0}, bh[3] = {0, 0, 0}, bl[3] = {0, 0, 0};
         sym_step_df64<W>(pp, qh, s2h, s2l, lane, ah, al, bh, bl);
 #pragma unroll
@@ -168,13 +250,43 @@ __device__ __forceinline__ void sym_offdiag(const SD4 *posP, const SD4 *posQ, do
   }
 }
 
+// Staged entry of ion g (or a padding entry when g >= n): FP64 position and
+// weight for fp64/df64; FP64 position and FP32 weight (low word of w) for
+// mixed; two float4 (hi x, y, z, weight; lo x, y, z) for split.
+template <int MODE, bool QARR>
+__device__ __forceinline__ void sym_stage(SD4 *dst, int i, int64_t g, int64_t n, const double *x,
+                                          const double *y, const double *z, const double *q,
+                                          const PosF32 &pf) {
+  const bool real = g < n;
+  const double w = real ? (QARR ? q[g] : 1.0) : 0.0;
+  if (MODE == MODE_SPLIT) {
+    float4 *f = reinterpret_cast<float4 *>(dst);
+    if (real) {
+      f[2 * i] = make_float4(pf.xh[g], pf.yh[g], pf.zh[g], (float)w);
+      f[2 * i + 1] = make_float4(pf.xl[g], pf.yl[g], pf.zl[g], 0.0f);
+    } else {
+      f[2 * i] = make_float4((float)SYM_FAR, (float)SYM_FAR, (float)SYM_FAR, 0.0f);
+      f[2 * i + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    return;
+  }
+  SD4 e;
+  if (real) {
+    e.x = x[g]; e.y = y[g]; e.z = z[g];
+  } else {
+    e.x = SYM_FAR; e.y = SYM_FAR; e.z = SYM_FAR;
+  }
+  e.w = (MODE == MODE_MIXED) ? wpack((float)w) : w;
+  dst[i] = e;
+}
+
 template <int MODE, bool QARR>
 __global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ y,
                                                          const double *__restrict__ z,
-                                                         const double *__restrict__ q, double soft2,
-                                                         double *__restrict__ part) {
+                                                         const double *__restrict__ q, PosF32 pf,
+                                                         double soft2, double *__restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int BI = 32 * G;
   SD4 *posP = reinterpret_cast<SD4 *>(smem_raw);
@@ -190,21 +302,8 @@ __global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, in
   const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
   const int tid = threadIdx.x;
   for (int i = tid; i < BI; i += SYM_THREADS) {
-    SD4 e;
-    if (i < np) {
-      e.x = x[p0 + i]; e.y = y[p0 + i]; e.z = z[p0 + i]; e.w = QARR ? q[p0 + i] : 1.0;
-    } else {
-      e.x = SYM_FAR; e.y = SYM_FAR; e.z = SYM_FAR; e.w = 0.0;
-    }
-    posP[i] = e;
-    if (P != Q) {
-      if (i < nq) {
-        e.x = x[q0 + i]; e.y = y[q0 + i]; e.z = z[q0 + i]; e.w = QARR ? q[q0 + i] : 1.0;
-      } else {
-        e.x = SYM_FAR; e.y = SYM_FAR; e.z = SYM_FAR; e.w = 0.0;
-      }
-      posQ[i] = e;
-    }
+    sym_stage<MODE, QARR>(posP, i, p0 + i, n, x, y, z, q, pf);
+    if (P != Q) sym_stage<MODE, QARR>(posQ, i, q0 + i, n, x, y, z, q, pf);
     accP[i] = 0.0;
     accP[BI + i] = 0.0;
     accP[2 * BI + i] = 0.0;
@@ -217,7 +316,40 @@ __global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, in
     for (int i = tid; i < np; i += SYM_THREADS) {
       const SD4 pi = posP[i];
       double a[3] = {0.0, 0.0, 0.0};
-      if (MODE == MODE_DF64) {
+      if (MODE == MODE_MIXED || MODE == MODE_SPLIT) {
+        float af[3] = {0, 0, 0};
+        const float4 *f = reinterpret_cast<const float4 *>(posP);
+        for (int j = 0; j < np; ++j) {
+          float fx, fy, fz, wj;
+          if (MODE == MODE_MIXED) {
+            const SD4 pj = posP[j];
+            fx = f64_to_f32_rn(pi.x - pj.x);
+            fy = f64_to_f32_rn(pi.y - pj.y);
+            fz = f64_to_f32_rn(pi.z - pj.z);
+            wj = wf32(pj.w);
+          } else {
+            const float4 ih = f[2 * i], il = f[2 * i + 1], jh = f[2 * j], jl = f[2 * j + 1];
+            fx = (ih.x - jh.x) + (il.x - jl.x);
+            fy = (ih.y - jh.y) + (il.y - jl.y);
+            fz = (ih.z - jh.z) + (il.z - jl.z);
+            wj = jh.w;
+          }
+          float sj = f32_rinv3(fx, fy, fz, (float)soft2);
+          if (QARR) sj *= wj;
+          af[0] = fmaf(fx, sj, af[0]);
+          af[1] = fmaf(fy, sj, af[1]);
+          af[2] = fmaf(fz, sj, af[2]);
+          if ((j & 31) == 31) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              a[k] += f32_to_f64(af[k]);
+              af[k] = 0.0f;
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] += f32_to_f64(af[k]);
+      } else if (MODE == MODE_DF64) {
         float ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
         for (int j = 0; j < np; ++j) {
           const SD4 pj = posP[j];
@@ -286,8 +418,8 @@ size_t sym_smem_bytes(int G) { return (size_t)32 * G * (2 * sizeof(SD4) + 3 * si
 
 template <int MODE>
 static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, const double *y,
-                                const double *z, const double *q, double soft2, double *part,
-                                cudaStream_t st) {
+                                const double *z, const double *q, const PosF32 &pf, double soft2,
+                                double *part, cudaStream_t st) {
   static std::mutex mu;
   static bool done[64] = {false};
   int dev = 0;
@@ -308,19 +440,21 @@ static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, cons
   const int items = nbk * (nbk + 1) / 2;
   const size_t smem = sym_smem_bytes(G);
   if (q)
-    k_pair_sym<MODE, true><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, soft2, part);
+    k_pair_sym<MODE, true><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
   else
-    k_pair_sym<MODE, false><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, soft2, part);
+    k_pair_sym<MODE, false><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
-                            const double *z, const double *q, double soft2, double *part,
-                            cudaStream_t st) {
+                            const double *z, const double *q, const PosF32 &pf, double soft2,
+                            double *part, cudaStream_t st) {
   if (G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
   switch (mode) {
-    case MODE_FP64: return launch_sym_m<MODE_FP64>(n, nbk, G, x, y, z, q, soft2, part, st);
-    case MODE_DF64: return launch_sym_m<MODE_DF64>(n, nbk, G, x, y, z, q, soft2, part, st);
+    case MODE_FP64: return launch_sym_m<MODE_FP64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_DF64: return launch_sym_m<MODE_DF64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_MIXED: return launch_sym_m<MODE_MIXED>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_SPLIT: return launch_sym_m<MODE_SPLIT>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -281,7 +281,7 @@ def test_nonfinite_detected(nb):
     nb.sync_status()  # cleared
 
 
-@pytest.mark.parametrize("precision", ["fp64", "df64"])
+@pytest.mark.parametrize("precision", ALL)
 def test_symmetric_kernel_small_and_ragged(nb, orc, precision):
     """The half-pair kernel (Newton's third law), forced on at small n with
     every block size, including ragged last blocks, charges and softening."""
@@ -297,7 +297,7 @@ def test_symmetric_kernel_small_and_ragged(nb, orc, precision):
             g = gpu_forces(nb, phys, pos, q=q, precision=precision)
             ax, ay, az, _, absf = orc.coulomb(oparams(orc, phys), *pos, q=q, want_absf=True)
             e = cond_err(g, np.stack([ax, ay, az]), absf)
-            assert e <= 1e-12, (n, block, e)
+            assert e <= TOL[precision], (n, block, e)
             g2 = gpu_forces(nb, phys, pos, q=q, precision=precision)
             assert np.array_equal(g, g2)
     finally:
