@@ -364,7 +364,8 @@ def main_kz(args):
     w = W.kz_ensemble()
     off = w["offsets"]
     pairs = float(np.sum(np.diff(off).astype(np.float64) ** 2))
-    par = nb.Params.from_phys(w["phys"])
+    prec = args.precision if args.precision in ("fp64", "df64") else "fp64"
+    par = nb.Params.from_phys(w["phys"], precision=prec)
     sysm = nb.System(w["pos"], w["vel"])
     nb.init_batched(par, sysm, off)
     nb.step_batched(par, sysm, off, args.warmup)
@@ -388,16 +389,17 @@ def main_kz(args):
     sizes = np.diff(off)
     order, start, mx, mean = nb.plan_batched(off, min(len(sizes), torch.cuda.get_device_properties(0).multi_processor_count))
     print(json.dumps({
-        "metric": "G pair-interactions/s, FP64 Kibble-Zurek ensemble (extra line, not the headline)",
+        "metric": "G pair-interactions/s, Kibble-Zurek ensemble (extra line, not the headline)",
         "value": round(pairs * args.steps / (ms / 1e3) / 1e9, 3), "unit": UNIT,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
-        "dtype": "f64", "data": "synthetic",
+        "dtype": DTYPE[prec], "precision": prec, "data": "synthetic",
         "config": {"workload": w["name"], "instances": int(len(sizes)), "ions": int(off[-1]),
                    "pairs_per_step": pairs, "launches": int(lib.nb_launch_count() - l0),
                    "lpt_max_over_mean_load": round(mx / mean, 4)},
         "roofline": {"bound": "alu", "achieved": round(FLOPS_PER_PAIR * pairs * args.steps / (ms / 1e3) / 1e12, 4),
-                     "peak": round(PEAK_TFLOPS["fp64"], 3), "unit": "TFLOP/s",
-                     "frac": round(FLOPS_PER_PAIR * pairs * args.steps / (ms / 1e3) / 1e12 / PEAK_TFLOPS["fp64"], 4)},
+                     "peak": round(PEAK_TFLOPS[PATH_PEAK[prec]], 3), "unit": "TFLOP/s",
+                     "frac": round(FLOPS_PER_PAIR * pairs * args.steps / (ms / 1e3) / 1e12
+                                   / PEAK_TFLOPS[PATH_PEAK[prec]], 4)},
         "clocks": clk}))
 
 

@@ -192,8 +192,8 @@ nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys,
  * steps exactly as nb_step defines them, with the shared params; instance k
  * draws its Langevin noise with instance word params->instance + k and ion
  * index local to the instance, so it reproduces a standalone nb_step run of
- * that instance.  One persistent kernel launch for all steps (FP64 only,
- * otherwise NB_ENOTSUP); each instance lives in one thread block's shared
+ * that instance.  One persistent kernel launch for all steps (NB_FP64 or
+ * NB_DF64 pair arithmetic, otherwise NB_ENOTSUP); each instance lives in one thread block's shared
  * memory, so n_inst <= 1024 and every instance <= 6144 ions (NB_EINVAL
  * otherwise).  Instances are packed onto the SMs by the longest-processing-
  * time rule on n^2 (nb_plan_batched).  The launch copies nothing from the

@@ -393,7 +393,8 @@ nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t
                           nb_system *packed, int64_t nsteps, void *stream) {
   NB_TRY(check_params(params));
   NB_TRY(check_system(packed, true, true));
-  if (params->precision != NB_FP64) return fail(NB_ENOTSUP, "the ensemble kernel is FP64 only");
+  if (params->precision != NB_FP64 && params->precision != NB_DF64)
+    return fail(NB_ENOTSUP, "the ensemble kernel supports NB_FP64 and NB_DF64");
   if (packed->m) return fail(NB_ENOTSUP, "the ensemble kernel has one species (m must be NULL)");
   if (nsteps < 0) return fail(NB_EINVAL, "nsteps must be >= 0");
   if (!(params->dt > 0.0)) return fail(NB_EINVAL, "dt must be > 0");
@@ -419,7 +420,7 @@ nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t
   Arena *a = nullptr;
   NB_TRY(get_arena(st, 256, &a));
   int threads = 256, R = 1, bps = 1;  // 256 threads: fastest in the autotuner on GB300
-  tuning_lookup(3, NB_FP64, packed->n, &threads, &R, &bps);
+  tuning_lookup(3, params->precision, packed->n, &threads, &R, &bps);
   const int n_bins = std::min(n_inst, device_sm_count());
   NB_CUDA_TRY(launch_batched(to_phys(params), to_view(packed), n_inst, offsets, n_bins, threads,
                              packed->step, nsteps, a->err, st));

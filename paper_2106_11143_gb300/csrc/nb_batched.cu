@@ -7,7 +7,8 @@
 // exactly one CTA, which keeps the instance's positions (and charges) in
 // shared memory for the whole run, so no CTA ever waits on another CTA.
 // Per step the CTA runs: drift of its ions, __syncthreads, the all-pairs
-// FP64 Coulomb sum (the same pair term as the single-system kernel) and the
+// Coulomb sum (the FP64 or the double-float pair term of the single-system
+// kernels) and the
 // kick/trap/friction/Langevin update of each ion, __syncthreads.  Velocities
 // and accelerations stay in global memory (L2-resident).
 //
@@ -59,6 +60,34 @@ __device__ __forceinline__ void bpair(double xi, double yi, double zi, const BD4
   az = fma(dz, s, az);
 }
 
+// Double-float (FP64-class) pair term, as in the single-system df64 kernel;
+// w carries q_j as an FP32 (hi, lo) pair in its bits.
+template <bool QARR>
+__device__ __forceinline__ void bpair_df64(double xi, double yi, double zi, const BD4 &pj,
+                                           float s2h, float s2l, float ah[3], float al[3]) {
+  float dh[3], dl[3];
+  split_f64(xi - pj.x, dh[0], dl[0]);
+  split_f64(yi - pj.y, dh[1], dl[1]);
+  split_f64(zi - pj.z, dh[2], dl[2]);
+  float sh, sl;
+  df_rinv3(dh, dl, s2h, s2l, sh, sl);
+  if (QARR) {
+    const float2 q = *reinterpret_cast<const float2 *>(&pj.w);
+    const float ph = sh * q.x;
+    sl = fmaf(sh, q.y, fmaf(sl, q.x, fmaf(sh, q.x, -ph)));
+    sh = ph;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float ph = dh[k] * sh;
+    const float pl = fmaf(dh[k], sl, fmaf(dl[k], sh, fmaf(dh[k], sh, -ph)));
+    float s, t;
+    two_sum_f(ah[k], ph, s, t);
+    ah[k] = s;
+    al[k] += t + pl;
+  }
+}
+
 // Philox4x32-10 and Box-Muller as in the single-system epilogue.
 __device__ __forceinline__ void bphilox(uint32_t c[4], uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -89,7 +118,7 @@ __device__ __forceinline__ void bnormals3(unsigned long long seed, unsigned inst
   out[2] = m1 * c3;
 }
 
-template <bool QARR>
+template <bool QARR, bool DF>
 __global__ void __launch_bounds__(512) k_batched(Phys p, StateView s,
                                                   const __grid_constant__ BatchSched sch,
                                                   int64_t step0, int64_t nsteps, unsigned *err) {
@@ -101,6 +130,8 @@ __global__ void __launch_bounds__(512) k_batched(Phys p, StateView s,
   const double cfr = p.gamma * dt / (2.0 * p.mass), g = p.gamma / p.mass;
   const double sig = p.noise_T > 0.0 ? sqrt(2.0 * p.gamma * KB * p.noise_T * dt) / p.mass : 0.0;
   const double pref_u = p.k_coulomb * p.charge * p.charge / p.mass;
+  float s2h = 0.0f, s2l = 0.0f;
+  if (DF) split_f64(p.soft2, s2h, s2l);
   bool bad = false;
 
   for (int kk = sch.bin_start[blockIdx.x]; kk < sch.bin_start[blockIdx.x + 1]; ++kk) {
@@ -113,6 +144,11 @@ __global__ void __launch_bounds__(512) k_batched(Phys p, StateView s,
       BD4 r;
       r.x = s.x[i0 + i]; r.y = s.y[i0 + i]; r.z = s.z[i0 + i];
       r.w = QARR ? s.q[i0 + i] : 0.0;
+      if (DF && QARR) {  // q as an FP32 (hi, lo) pair for the double-float pair term
+        float qh, ql;
+        split_f64(s.q[i0 + i], qh, ql);
+        *reinterpret_cast<float2 *>(&r.w) = make_float2(qh, ql);
+      }
       sp[i] = r;
     }
     __syncthreads();
@@ -133,11 +169,23 @@ __global__ void __launch_bounds__(512) k_batched(Phys p, StateView s,
         const int i = ib + tid;
         const BD4 ri = sp[min(i, n - 1)];
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        if (DF) {
+          float ah[3] = {0.0f, 0.0f, 0.0f}, al[3] = {0.0f, 0.0f, 0.0f};
+          for (int j0 = 0; j0 < n; j0 += 256) {  // double-float sums flushed every 256 partners
+            const int j1 = min(n, j0 + 256);
+            for (int j = j0; j < j1; ++j) bpair_df64<QARR>(ri.x, ri.y, ri.z, sp[j], s2h, s2l, ah, al);
+            a0 += f32_to_f64(ah[0]) + f32_to_f64(al[0]);
+            a1 += f32_to_f64(ah[1]) + f32_to_f64(al[1]);
+            a2 += f32_to_f64(ah[2]) + f32_to_f64(al[2]);
+            ah[0] = ah[1] = ah[2] = al[0] = al[1] = al[2] = 0.0f;
+          }
+        } else {
 #pragma unroll 2
-        for (int j = 0; j < n; ++j) bpair<QARR>(ri.x, ri.y, ri.z, sp[j], p.soft2, a0, a1, a2);
+          for (int j = 0; j < n; ++j) bpair<QARR>(ri.x, ri.y, ri.z, sp[j], p.soft2, a0, a1, a2);
+        }
         if (i < n) {
           const int64_t gi = i0 + i;
-          const double pref = QARR ? p.k_coulomb * ri.w / p.mass : pref_u;
+          const double pref = QARR ? p.k_coulomb * s.q[gi] / p.mass : pref_u;
           double tr[3];
           trap_accel(p, t, ri.x, ri.y, ri.z, tr[0], tr[1], tr[2]);
           double xi[3] = {0.0, 0.0, 0.0};
@@ -224,17 +272,26 @@ cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const 
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_done[dev]) {
       const int lim = 200 * 1024;
-      e = cudaFuncSetAttribute(k_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      e = cudaFuncSetAttribute(k_batched<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        e = cudaFuncSetAttribute(k_batched<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batched<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batched<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e != cudaSuccess) return e;
       attr_done[dev] = true;
     }
   }
-  if (s.q)
-    k_batched<true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
+  const bool df = p.precision == MODE_DF64;
+  if (s.q && df)
+    k_batched<true, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
+  else if (s.q)
+    k_batched<true, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
+  else if (df)
+    k_batched<false, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
   else
-    k_batched<false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
+    k_batched<false, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
   return cudaGetLastError();
 }
 
