@@ -189,6 +189,12 @@ __device__ __forceinline__ void df_rinv3(const float dh[3], const float dl[3], f
   sl = fmaf(y3h, c, y3e);
 }
 
+// Mixed-mode clamp of the FP32 seed: a zero displacement (the self pair, r2 =
+// soft2 = 0) gives s = 2.5 * 2^120, finite even times a weight |w_j| < 100, so
+// the term is d * s = 0.  Real pairs with |r_i - r_j| >= 2^-40 (9.1e-13 in the
+// caller's length unit) never reach the clamp.
+constexpr float F32_YMAX = 1.099511627776e12f;  // 2^40
+
 // FP32 bulk shared by the two mixed modes: given the FP32 displacement,
 // acc += w_j d / s^3 with s^-3 = y^3 (1 + 3/2 e), y = MUFU.RSQ(s^2),
 // e = 1 - s^2 y^2 (one first-order correction in FP32).
@@ -198,7 +204,7 @@ __device__ __forceinline__ void pair_f32_bulk(float fx, float fy, float fz, floa
   const float r2 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, soft2f)));
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
-  y = (r2 > 0.0f) ? y : 0.0f;
+  y = fminf(y, F32_YMAX);
   const float y2 = y * y;
   const float e15 = fmaf(-1.5f * r2, y2, 1.5f);
   const float y3 = y2 * y;
@@ -216,7 +222,7 @@ __device__ __forceinline__ float f32_rinv3(float fx, float fy, float fz, float s
   const float r2 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, soft2f)));
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
-  y = (r2 > 0.0f) ? y : 0.0f;
+  y = fminf(y, F32_YMAX);
   const float y2 = y * y;
   const float e15 = fmaf(-1.5f * r2, y2, 1.5f);
   const float y3 = y2 * y;

@@ -167,12 +167,19 @@ __device__ __forceinline__ void sym_step_mixed(const SD4 &pp, SD4 qd, float soft
   }
 }
 
-// Split mixed step: positions as FP32 (hi, lo) pairs (hi.w = weight).
+// Split mixed step: positions as FP32 (hi, lo) pairs (hi.w = weight).  The
+// Q-tile's positions are read from shared memory at the rotated index
+// (lane + r) mod 32 (two conflict-free 128-bit loads per pair); only the Q
+// accumulators rotate through shuffles.
 template <bool W>
-__device__ __forceinline__ void sym_step_split(const float4 &ph, const float4 &pl, float4 qh, float4 ql,
-                                               float soft2f, int lane, float a[3], float b[3]) {
-#pragma unroll 2
+__device__ __forceinline__ void sym_step_split(const float4 &ph, const float4 &pl, const float4 *qhi,
+                                               const float4 *qlo, float soft2f, int lane, float a[3],
+                                               float b[3]) {
+  // qhi, qlo point at this lane's entry of the duplicated tile: entry r of the
+  // rotation is qhi[r] (a compile-time offset once the loop is unrolled)
+#pragma unroll
   for (int r = 0; r < 32; ++r) {
+    const float4 qh = qhi[r], ql = qlo[r];
     const float fx = (ph.x - qh.x) + (pl.x - ql.x);
     const float fy = (ph.y - qh.y) + (pl.y - ql.y);
     const float fz = (ph.z - qh.z) + (pl.z - ql.z);
@@ -184,13 +191,6 @@ __device__ __forceinline__ void sym_step_split(const float4 &ph, const float4 &p
     b[0] = fmaf(-fx, sq, b[0]);
     b[1] = fmaf(-fy, sq, b[1]);
     b[2] = fmaf(-fz, sq, b[2]);
-    qh.x = shfl_next(qh.x, lane);
-    qh.y = shfl_next(qh.y, lane);
-    qh.z = shfl_next(qh.z, lane);
-    if (W) qh.w = shfl_next(qh.w, lane);
-    ql.x = shfl_next(ql.x, lane);
-    ql.y = shfl_next(ql.y, lane);
-    ql.z = shfl_next(ql.z, lane);
     b[0] = shfl_next(b[0], lane);
     b[1] = shfl_next(b[1], lane);
     b[2] = shfl_next(b[2], lane);
@@ -217,8 +217,8 @@ __device__ __forceinline__ void sym_offdiag(const SD4 *posP, const SD4 *posQ, do
         } else {
           const float4 *fP = reinterpret_cast<const float4 *>(posP);
           const float4 *fQ = reinterpret_cast<const float4 *>(posQ);
-          sym_step_split<W>(fP[2 * ip], fP[2 * ip + 1], fQ[2 * (qs * 32 + lane)],
-                            fQ[2 * (qs * 32 + lane) + 1], (float)soft2, lane, a, b);
+          sym_step_split<W>(fP[ip], fP[BI + ip], fQ + qs * 64 + lane, fQ + 2 * BI + qs * 64 + lane,
+                            (float)soft2, lane, a, b);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -254,19 +254,28 @@ __device__ __forceinline__ void sym_offdiag(const SD4 *posP, const SD4 *posQ, do
 // weight for fp64/df64; FP64 position and FP32 weight (low word of w) for
 // mixed; two float4 (hi x, y, z, weight; lo x, y, z) for split.
 template <int MODE, bool QARR>
-__device__ __forceinline__ void sym_stage(SD4 *dst, int i, int64_t g, int64_t n, const double *x,
+__device__ __forceinline__ void sym_stage(SD4 *dst, int i, int BI, int64_t g, int64_t n, const double *x,
                                           const double *y, const double *z, const double *q,
-                                          const PosF32 &pf) {
+                                          const PosF32 &pf, bool dup) {
   const bool real = g < n;
   const double w = real ? (QARR ? q[g] : 1.0) : 0.0;
   if (MODE == MODE_SPLIT) {
+    // P side: [BI hi entries][BI lo entries].  Q side (dup): every 32-ion
+    // tile stored twice back to back, [2 BI hi][2 BI lo], so that the entry
+    // (lane + r) of a rotation is at a fixed offset r from the lane's base.
     float4 *f = reinterpret_cast<float4 *>(dst);
-    if (real) {
-      f[2 * i] = make_float4(pf.xh[g], pf.yh[g], pf.zh[g], (float)w);
-      f[2 * i + 1] = make_float4(pf.xl[g], pf.yl[g], pf.zl[g], 0.0f);
+    const float4 hi = real ? make_float4(pf.xh[g], pf.yh[g], pf.zh[g], (float)w)
+                           : make_float4((float)SYM_FAR, (float)SYM_FAR, (float)SYM_FAR, 0.0f);
+    const float4 lo = real ? make_float4(pf.xl[g], pf.yl[g], pf.zl[g], 0.0f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (dup) {
+      const int k = (i >> 5) * 64 + (i & 31);
+      f[k] = hi;
+      f[k + 32] = hi;
+      f[2 * BI + k] = lo;
+      f[2 * BI + k + 32] = lo;
     } else {
-      f[2 * i] = make_float4((float)SYM_FAR, (float)SYM_FAR, (float)SYM_FAR, 0.0f);
-      f[2 * i + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      f[i] = hi;
+      f[BI + i] = lo;
     }
     return;
   }
@@ -291,7 +300,7 @@ __global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, in
   const int BI = 32 * G;
   SD4 *posP = reinterpret_cast<SD4 *>(smem_raw);
   SD4 *posQ = posP + BI;
-  double *accP = reinterpret_cast<double *>(posQ + BI);  // [3][BI]
+  double *accP = reinterpret_cast<double *>(posQ + (MODE == MODE_SPLIT ? 2 * BI : BI));  // [3][BI]
   int t = blockIdx.x, P = 0;
   while (t >= nbk - P) {  // item -> (P, Q), P <= Q, row by row
     t -= nbk - P;
@@ -302,8 +311,8 @@ __global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, in
   const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
   const int tid = threadIdx.x;
   for (int i = tid; i < BI; i += SYM_THREADS) {
-    sym_stage<MODE, QARR>(posP, i, p0 + i, n, x, y, z, q, pf);
-    if (P != Q) sym_stage<MODE, QARR>(posQ, i, q0 + i, n, x, y, z, q, pf);
+    sym_stage<MODE, QARR>(posP, i, BI, p0 + i, n, x, y, z, q, pf, false);
+    if (P != Q) sym_stage<MODE, QARR>(posQ, i, BI, q0 + i, n, x, y, z, q, pf, true);
     accP[i] = 0.0;
     accP[BI + i] = 0.0;
     accP[2 * BI + i] = 0.0;
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, in
             fz = f64_to_f32_rn(pi.z - pj.z);
             wj = wf32(pj.w);
           } else {
-            const float4 ih = f[2 * i], il = f[2 * i + 1], jh = f[2 * j], jl = f[2 * j + 1];
+            const float4 ih = f[i], il = f[BI + i], jh = f[j], jl = f[BI + j];
             fx = (ih.x - jh.x) + (il.x - jl.x);
             fy = (ih.y - jh.y) + (il.y - jl.y);
             fz = (ih.z - jh.z) + (il.z - jl.z);
@@ -414,7 +423,9 @@ __global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, in
     for (int c = 0; c < 3; ++c) part[((int64_t)Q * 3 + c) * n + p0 + i] = accP[c * BI + i];
 }
 
-size_t sym_smem_bytes(int G) { return (size_t)32 * G * (2 * sizeof(SD4) + 3 * sizeof(double)); }
+size_t sym_smem_bytes(int G, int mode) {
+  return (size_t)32 * G * ((mode == MODE_SPLIT ? 3 : 2) * sizeof(SD4) + 3 * sizeof(double));
+}
 
 template <int MODE>
 static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, const double *y,
@@ -429,7 +440,7 @@ static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, cons
     std::lock_guard<std::mutex> lk(mu);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!done[dev]) {
-      const int lim = (int)sym_smem_bytes(32);
+      const int lim = (int)sym_smem_bytes(32, MODE);
       e = cudaFuncSetAttribute(k_pair_sym<MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_pair_sym<MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -438,7 +449,7 @@ static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, cons
     }
   }
   const int items = nbk * (nbk + 1) / 2;
-  const size_t smem = sym_smem_bytes(G);
+  const size_t smem = sym_smem_bytes(G, MODE);
   if (q)
     k_pair_sym<MODE, true><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
   else
