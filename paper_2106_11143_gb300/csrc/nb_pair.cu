@@ -527,10 +527,12 @@ bool tuning_lookup(int kind, int mode, int64_t n, int *block, int *R, int *bps) 
 
 Plan make_plan(int64_t n, int mode, int kind) {
   Plan pl;
-  // Symmetric half-pair kernel for the FP64-pipe-bound force paths, when the
-  // per-partner-block partials (nbk * 3n doubles) stay below 2 GB.
+  // Symmetric half-pair kernel for the force paths from n = 16384 on, when
+  // the per-partner-block partials (nbk * 3n doubles) stay below 2 GB.  Block
+  // sizes: the fastest measured on GB300 (split: 512 ions, whose two-ion-per-
+  // lane P-tiles need G >= 16).
   if (kind == 0 && (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || mode == MODE_SPLIT)) {
-    int G = n >= 60000 ? 16 : 8;  // the fastest block sizes measured on GB300
+    int G = (n >= 60000 || mode == MODE_SPLIT) ? 16 : 8;
     bool use = n >= 16384;
     int tb = 0, tr = 0, tbps = 0;
     if (tuning_lookup(4, mode, n, &tb, &tr, &tbps)) {

@@ -167,33 +167,95 @@ __device__ __forceinline__ void sym_step_mixed(const SD4 &pp, SD4 qd, float soft
   }
 }
 
-// Split mixed step: positions as FP32 (hi, lo) pairs (hi.w = weight).  The
-// Q-tile's positions are read from shared memory at the rotated index
-// (lane + r) mod 32 (two conflict-free 128-bit loads per pair); only the Q
-// accumulators rotate through shuffles.
+// One split-precision pair evaluation: P-ion (ph, pl) against Q-ion (qh, ql),
+// positions as FP32 (hi, lo) pairs with the weight in hi.w; the force goes
+// into a (P side) and, with the opposite sign, into b (Q side).
+template <bool W>
+__device__ __forceinline__ void split_eval(const float4 &ph, const float4 &pl, const float4 &qh,
+                                           const float4 &ql, float soft2f, float a[3], float b[3]) {
+  const float fx = (ph.x - qh.x) + (pl.x - ql.x);
+  const float fy = (ph.y - qh.y) + (pl.y - ql.y);
+  const float fz = (ph.z - qh.z) + (pl.z - ql.z);
+  const float s = f32_rinv3(fx, fy, fz, soft2f);
+  const float sp = W ? s * qh.w : s, sq = W ? s * ph.w : s;
+  a[0] = fmaf(fx, sp, a[0]);
+  a[1] = fmaf(fy, sp, a[1]);
+  a[2] = fmaf(fz, sp, a[2]);
+  b[0] = fmaf(-fx, sq, b[0]);
+  b[1] = fmaf(-fy, sq, b[1]);
+  b[2] = fmaf(-fz, sq, b[2]);
+}
+
+// Split mixed step: the Q-tile's positions are read from shared memory at
+// the rotated index (lane + r) mod 32 (two conflict-free 128-bit loads per
+// pair); only the Q accumulators rotate through shuffles.  qhi, qlo point at
+// this lane's entry of the duplicated tile, so entry r of the rotation is
+// qhi[r] (a compile-time offset once the loop is unrolled).
 template <bool W>
 __device__ __forceinline__ void sym_step_split(const float4 &ph, const float4 &pl, const float4 *qhi,
                                                const float4 *qlo, float soft2f, int lane, float a[3],
                                                float b[3]) {
-  // qhi, qlo point at this lane's entry of the duplicated tile: entry r of the
-  // rotation is qhi[r] (a compile-time offset once the loop is unrolled)
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
-    const float4 qh = qhi[r], ql = qlo[r];
-    const float fx = (ph.x - qh.x) + (pl.x - ql.x);
-    const float fy = (ph.y - qh.y) + (pl.y - ql.y);
-    const float fz = (ph.z - qh.z) + (pl.z - ql.z);
-    const float s = f32_rinv3(fx, fy, fz, soft2f);
-    const float sp = W ? s * qh.w : s, sq = W ? s * ph.w : s;
-    a[0] = fmaf(fx, sp, a[0]);
-    a[1] = fmaf(fy, sp, a[1]);
-    a[2] = fmaf(fz, sp, a[2]);
-    b[0] = fmaf(-fx, sq, b[0]);
-    b[1] = fmaf(-fy, sq, b[1]);
-    b[2] = fmaf(-fz, sq, b[2]);
+    split_eval<W>(ph, pl, qhi[r], qlo[r], soft2f, a, b);
     b[0] = shfl_next(b[0], lane);
     b[1] = shfl_next(b[1], lane);
     b[2] = shfl_next(b[2], lane);
+  }
+}
+
+// The same with two P-ions per lane (a 64-ion P-tile): one pair of Q loads
+// and one round of accumulator shuffles serve two pair evaluations, which
+// are independent up to their adds into b.
+template <bool W>
+__device__ __forceinline__ void sym_step_split2(const float4 &h1, const float4 &l1, const float4 &h2,
+                                                const float4 &l2, const float4 *qhi, const float4 *qlo,
+                                                float soft2f, int lane, float a1[3], float a2[3],
+                                                float b[3]) {
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const float4 qh = qhi[r], ql = qlo[r];
+    split_eval<W>(h1, l1, qh, ql, soft2f, a1, b);
+    split_eval<W>(h2, l2, qh, ql, soft2f, a2, b);
+    b[0] = shfl_next(b[0], lane);
+    b[1] = shfl_next(b[1], lane);
+    b[2] = shfl_next(b[2], lane);
+  }
+}
+
+// Off-diagonal item, split precision with 64-ion P-tiles (G >= 16, so that
+// the G/2 P-tiles outnumber the warps): warp w takes the Q-tiles qs = w,
+// w + 8, ...; at step k it holds P-tile (qs + k) mod G/2, distinct across
+// warps because all warps advance in lockstep through the barriers.
+template <bool W>
+__device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, const SD4 *posQ, double *accP,
+                                                   int G, int BI, double soft2, int64_t n, int P,
+                                                   int64_t q0, int nq, double *part) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int GP = G >> 1;
+  const float4 *fP = reinterpret_cast<const float4 *>(posP);
+  const float4 *fQ = reinterpret_cast<const float4 *>(posQ);
+  for (int qs = warp; qs < G; qs += SYM_W) {
+    double aq[3] = {0.0, 0.0, 0.0};
+    const float4 *qhi = fQ + qs * 64 + lane, *qlo = fQ + 2 * BI + qs * 64 + lane;
+    for (int k = 0; k < GP; ++k) {
+      const int pt = (qs + k) % GP;
+      __syncthreads();  // all warps are at step k: their P-tiles are distinct
+      const int i1 = pt * 64 + lane, i2 = i1 + 32;
+      float a1[3] = {0, 0, 0}, a2[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+      sym_step_split2<W>(fP[i1], fP[BI + i1], fP[i2], fP[BI + i2], qhi, qlo, (float)soft2, lane, a1, a2,
+                         b);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        accP[c * BI + i1] += f32_to_f64(a1[c]);
+        accP[c * BI + i2] += f32_to_f64(a2[c]);
+        aq[c] += f32_to_f64(b[c]);
+      }
+    }
+    const int iq = qs * 32 + lane;
+    if (iq < nq)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + q0 + iq] = aq[c];
   }
 }
 
@@ -289,7 +351,7 @@ __device__ __forceinline__ void sym_stage(SD4 *dst, int i, int BI, int64_t g, in
   dst[i] = e;
 }
 
-template <int MODE, bool QARR>
+template <int MODE, bool QARR, bool P2>
 __global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ y,
@@ -413,10 +475,16 @@ __global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, in
   }
 
   const bool weighted = QARR || np < BI || nq < BI;
-  if (weighted)
+  if (P2) {
+    if (weighted)
+      sym_offdiag_split2<true>(posP, posQ, accP, G, BI, soft2, n, P, q0, nq, part);
+    else
+      sym_offdiag_split2<false>(posP, posQ, accP, G, BI, soft2, n, P, q0, nq, part);
+  } else if (weighted) {
     sym_offdiag<MODE, true>(posP, posQ, accP, G, BI, soft2, s2h, s2l, n, P, q0, nq, part);
-  else
+  } else {
     sym_offdiag<MODE, false>(posP, posQ, accP, G, BI, soft2, s2h, s2l, n, P, q0, nq, part);
+  }
   __syncthreads();
   for (int i = tid; i < np; i += SYM_THREADS)
 #pragma unroll
@@ -427,7 +495,7 @@ size_t sym_smem_bytes(int G, int mode) {
   return (size_t)32 * G * ((mode == MODE_SPLIT ? 3 : 2) * sizeof(SD4) + 3 * sizeof(double));
 }
 
-template <int MODE>
+template <int MODE, bool P2>
 static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, const double *y,
                                 const double *z, const double *q, const PosF32 &pf, double soft2,
                                 double *part, cudaStream_t st) {
@@ -441,9 +509,10 @@ static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, cons
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!done[dev]) {
       const int lim = (int)sym_smem_bytes(32, MODE);
-      e = cudaFuncSetAttribute(k_pair_sym<MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      e = cudaFuncSetAttribute(k_pair_sym<MODE, true, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pair_sym<MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        e = cudaFuncSetAttribute(k_pair_sym<MODE, false, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 lim);
       if (e != cudaSuccess) return e;
       done[dev] = true;
     }
@@ -451,9 +520,9 @@ static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, cons
   const int items = nbk * (nbk + 1) / 2;
   const size_t smem = sym_smem_bytes(G, MODE);
   if (q)
-    k_pair_sym<MODE, true><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
+    k_pair_sym<MODE, true, P2><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
   else
-    k_pair_sym<MODE, false><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
+    k_pair_sym<MODE, false, P2><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
   return cudaGetLastError();
 }
 
@@ -462,10 +531,12 @@ cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x
                             double *part, cudaStream_t st) {
   if (G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
   switch (mode) {
-    case MODE_FP64: return launch_sym_m<MODE_FP64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
-    case MODE_DF64: return launch_sym_m<MODE_DF64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
-    case MODE_MIXED: return launch_sym_m<MODE_MIXED>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
-    case MODE_SPLIT: return launch_sym_m<MODE_SPLIT>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_FP64: return launch_sym_m<MODE_FP64, false>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_DF64: return launch_sym_m<MODE_DF64, false>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_MIXED: return launch_sym_m<MODE_MIXED, false>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_SPLIT:  // 64-ion P-tiles once the G/2 P-tiles outnumber the warps
+      return G >= 2 * SYM_W ? launch_sym_m<MODE_SPLIT, true>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
+                            : launch_sym_m<MODE_SPLIT, false>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
     default: return cudaErrorInvalidValue;
   }
 }
