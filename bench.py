@@ -54,7 +54,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed_split", choices=["fp64", "df64", "mixed", "mixed_split"])
-    ap.add_argument("--n", type=int, default=100000, help="ions (default: the 1e5 workload)")
+    ap.add_argument("--ions", "--n", dest="n", type=int, default=100000,
+                    help="ions (default: the 1e5 workload); spelled --ions under torchrun, whose "
+                         "parser takes --n for an abbreviation of its own options")
     ap.add_argument("--no-paths", action="store_true", help="skip the secondary precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--workload", default="large", choices=["large", "kz"],
@@ -143,6 +145,12 @@ def allreduce_max(x, world, device="cuda"):
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def pair_rate(world, pairs_per_step, steps, ms):
+    """Whole-job G pair-interactions/s: every rank advances its own problem of
+    pairs_per_step pairs by `steps` steps; ms is the max over ranks."""
+    return world * pairs_per_step * steps / (ms / 1e3) / 1e9
 
 
 def cpu_baseline(w, target_s=12.0):
@@ -246,7 +254,7 @@ def run_e2e(nb, w, precision, steps, world, flush):
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ms = allreduce_max(ms, world)
     nbytes = len(names) * n * 8
-    return {"value": world * n * n * steps / (ms / 1e3) / 1e9, "unit": UNIT,
+    return {"value": pair_rate(world, n * n, steps, ms), "unit": UNIT,
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
 
@@ -280,7 +288,7 @@ def main_ours(args):
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     head = run_path(nb, w, args.precision, args.steps, args.warmup, world, flush, clocks)
     ms = allreduce_max(head["ms"], world)
-    value = world * n * n * args.steps / (ms / 1e3) / 1e9
+    value = pair_rate(world, n * n, args.steps, ms)
     e2e = run_e2e(nb, w, args.precision, min(args.steps, 20), world, flush)
     paths = {}
     if not args.no_paths:
