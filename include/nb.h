@@ -279,6 +279,28 @@ nb_status nb_traj_backward(const nb_params *params, const nb_system *sys, int64_
 nb_status nb_energy_noalloc(const nb_params *params, const nb_system *sys,
                             double out[4], void *stream);
 
+/* ---- Arithmetic probes (steps a1-a3 of one pair, Sec. III-IV) ---------- */
+
+/* out[i] = the r^-3 that precision mode `precision` (an nb_precision value)
+ * forms for one pair with FP64 displacement (dx[i], dy[i], dz[i]) and
+ * softening soft2 >= 0: r^2 = dx^2 + dy^2 + dz^2 + soft2, then the mode's
+ * 1/sqrt and cube -- the same device functions as the pair kernels, before the
+ * charge weight.  NB_MIXED and NB_MIXED_SPLIT share their FP32 bulk; here
+ * both start from the displacement rounded to FP32 (the split mode's own
+ * displacement comes from FP32 position pairs instead).  NB_DF64 returns
+ * its double-float result summed into one double.  r^2 == 0 gives 0 in the
+ * FP64 modes and a finite value (times the zero displacement in a pair) in
+ * the FP32 ones.  All arrays are device memory of n doubles, caller-owned;
+ * asynchronous on `stream`.  NB_EINVAL for n < 0, a NULL array with n > 0,
+ * soft2 < 0 or NaN, or an unknown precision.                                */
+nb_status nb_rinv3_probe(int precision, int64_t n, const double *dx, const double *dy,
+                         const double *dz, double soft2, double *out, void *stream);
+
+/* y[i] = the FP32 hardware reciprocal-square-root seed of x[i]
+ * (rsqrt.approx.ftz.f32, Sec. IV's counterpart of RSQRT14), for the seed's
+ * error bound.  Device arrays of n floats, caller-owned; asynchronous.      */
+nb_status nb_rsqrt_seed_probe(int64_t n, const float *x, float *y, void *stream);
+
 /* Synchronises `stream`, then returns and clears its device error word:
  * NB_OK, NB_ENONFINITE or NB_ETIMEOUT (or NB_ECUDA if the stream failed). */
 nb_status nb_sync_status(void *stream);

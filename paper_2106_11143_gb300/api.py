@@ -88,10 +88,12 @@ def lib():
         L.nb_timing_enable.argtypes = [C.c_int64]
         L.nb_timing_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
         L.nb_launch_count.restype = C.c_uint64
+        L.nb_rinv3_probe.argtypes = [C.c_int32, C.c_int64, _dp, _dp, _dp, C.c_double, _dp, V]
+        L.nb_rsqrt_seed_probe.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, V]
         for f in ("nb_forces", "nb_step", "nb_energy", "nb_forces_vjp", "nb_sync_status",
                   "nb_release", "nb_timing_enable", "nb_timing_read", "nb_step_batched",
                   "nb_plan_batched", "nb_set_tuning", "nb_energy_noalloc", "nb_traj_forward",
-                  "nb_traj_backward"):
+                  "nb_traj_backward", "nb_rinv3_probe", "nb_rsqrt_seed_probe"):
             getattr(L, f).restype = C.c_int
         _LIB = L
     return _LIB
@@ -304,6 +306,31 @@ def set_tuning(kind, precision, n_lo, n_hi, block, R=1, blocks_per_sm=16):
     _check(lib().nb_set_tuning(KINDS[kind] if isinstance(kind, str) else int(kind),
                                PRECISIONS[precision], int(n_lo), int(n_hi), int(block), int(R),
                                int(blocks_per_sm)), "nb_set_tuning")
+
+
+def rinv3_probe(precision, d, soft2=0.0, stream=None):
+    """nb_rinv3_probe: the r^-3 that `precision` forms for each displacement
+    column of d (shape (3, n), FP64); returns a device tensor of n doubles."""
+    d = torch.as_tensor(d, dtype=torch.float64).reshape(3, -1)
+    if d.device.type != "cuda":
+        d = d.to("cuda")
+    dx, dy, dz = (d[k].contiguous() for k in range(3))
+    out = torch.empty(dx.numel(), dtype=torch.float64, device=dx.device)
+    _check(lib().nb_rinv3_probe(PRECISIONS[precision], dx.numel(), _ptr(dx), _ptr(dy), _ptr(dz),
+                                float(soft2), _ptr(out), _stream(stream)), "nb_rinv3_probe")
+    return out
+
+
+def rsqrt_seed_probe(x, stream=None):
+    """nb_rsqrt_seed_probe: the FP32 hardware 1/sqrt seed of each element."""
+    x = torch.as_tensor(x, dtype=torch.float32).reshape(-1)
+    if x.device.type != "cuda":
+        x = x.to("cuda")
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check(lib().nb_rsqrt_seed_probe(x.numel(), x.data_ptr(), y.data_ptr(), _stream(stream)),
+           "nb_rsqrt_seed_probe")
+    return y
 
 
 def sync_status(stream=None):

@@ -103,6 +103,25 @@ __device__ __forceinline__ double rinv3_f64(double r2) {
   return fma(Y3, C, Y3);
 }
 
+// r2^(-3/2) by the precision-ladder methods of Sec. IV: SQRT+DIV (1/sqrt in
+// FP64), the bare FP32 seed, or the seed refined by one or two Newton steps
+// y <- y (3/2 - (r2/2) y^2); then the cube y^3.  r2 == 0 gives 0.
+template <int MODE>
+__device__ __forceinline__ double ladder_rinv3(double r2) {
+  double y;
+  if (MODE == MODE_SQRTDIV) {
+    y = (r2 > 0.0) ? 1.0 / sqrt(r2) : 0.0;
+  } else {
+    y = rsqrt_seed_f64(r2);
+    if (MODE == MODE_RSQ_NR1 || MODE == MODE_RSQ_NR2) {
+      const double h = 0.5 * r2;
+      y = y * fma(-h * y, y, 1.5);
+      if (MODE == MODE_RSQ_NR2) y = y * fma(-h * y, y, 1.5);
+    }
+  }
+  return (y * y) * y;
+}
+
 // FP64 -> FP32 rounded to nearest (ties away from zero) with 32-bit integer
 // ops only: 64-bit integer adds and masks would issue on the FP64 pipe.  The
 // rounding increment at mantissa bit 29 is a carry-chained 32-bit add.

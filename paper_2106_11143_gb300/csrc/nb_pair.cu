@@ -66,18 +66,7 @@ __device__ __forceinline__ void pair_ladder(double xi, double yi, double zi, con
   const double dy = yi - pj.y;
   const double dz = zi - pj.z;
   const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
-  double y;
-  if (MODE == MODE_SQRTDIV) {
-    y = (r2 > 0.0) ? 1.0 / sqrt(r2) : 0.0;
-  } else {
-    y = rsqrt_seed_f64(r2);
-    if (MODE == MODE_RSQ_NR1 || MODE == MODE_RSQ_NR2) {
-      const double h = 0.5 * r2;
-      y = y * fma(-h * y, y, 1.5);
-      if (MODE == MODE_RSQ_NR2) y = y * fma(-h * y, y, 1.5);
-    }
-  }
-  double s = (y * y) * y;
+  double s = ladder_rinv3<MODE>(r2);
   if (QARR) s *= pj.w;
   ax = fma(dx, s, ax);
   ay = fma(dy, s, ay);

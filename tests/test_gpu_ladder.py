@@ -50,3 +50,27 @@ def test_ladder_chain_experiment_runs(nb):
     assert 0.0 < r["rsq"] < 1e-3
     assert r["rsq_nr1"] < r["rsq"]
     assert 0.12 < r["q_mathieu"] < 0.25
+
+
+def test_ladder_pancake_experiment(nb):
+    """The N = 128 radial-plane crystal: SQRT+DIV is the reference, the bare
+    seed differs most, one Newton step brings the difference down, and the
+    crystal stays in one radial plane."""
+    from paper_2106_11143_gb300 import ladder
+    r = ladder.pancake(methods=["sqrtdiv", "rsq", "rsq_nr1"], steps=3000)
+    print(r)
+    assert r["sqrtdiv"] == 0.0
+    assert 0.0 < r["rsq"] < 1e-3
+    assert r["rsq_nr1"] < r["rsq"]
+    assert r["flatness"] < 0.01
+
+
+def test_ladder_speed_runs_every_method_one_sided(nb):
+    from paper_2106_11143_gb300 import ladder
+    out = ladder.speed(sizes=(1000, 16384), reps=1)
+    assert set(out["1000"]) == set(ladder.METHODS)
+    assert set(out["16384"]) == set(ladder.METHODS) | {"fp64_sym", "df64_sym"}
+    row = out["16384"]
+    assert row["sqrtdiv"]["speedup_vs_sqrtdiv_pct"] == 0.0
+    # the half-pair kernel does about half the pair arithmetic
+    assert row["fp64_sym"]["ms"] < 0.8 * row["fp64"]["ms"]
