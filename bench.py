@@ -260,12 +260,20 @@ def run_e2e(nb, w, precision, steps, world, flush):
 
 SYMMETRIC = {"fp64", "df64", "mixed", "mixed_split"}  # half-pair kernel at N >= 16384
 
+# DRAM bytes (read + write) per launch of the pair kernel, from one ncu capture
+# of this bench's command (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass;
+# profiles/bench_N100000_launch_list.md), keyed by (precision, n).  Almost all
+# of it is the symmetric kernel's per-partner-block partial sums written for
+# the epilogue.  An entry is valid only for the kernel code it was taken on:
+# remove it when that kernel changes.
+NCU_TRAFFIC = {("mixed_split", 100000): 409584128}
+
 
 def roofline(path, n, kernel_ms):
     achieved = FLOPS_PER_PAIR * n * n / (kernel_ms / 1e3) / 1e12
     peak = PEAK_TFLOPS[PATH_PEAK[path]]
     r = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-         "frac": round(achieved / peak, 4), "traffic": None,
+         "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get((path, n)),
          "kernel": ("k_pair_sym<%s>" if path in SYMMETRIC and n >= 16384 else "k_pair_force<%s>") % path,
          "peak_source": "%s FMA lanes x 2 flops x 152 SMs x 2070 MHz (unit counts and max clock)"
                         % ("2 FP64" if PATH_PEAK[path] == "fp64" else "128 FP32"),
