@@ -52,8 +52,7 @@ __device__ __forceinline__ void bpair(double xi, double yi, double zi, const BD4
   const double dx = xi - pj.x;
   const double dy = yi - pj.y;
   const double dz = zi - pj.z;
-  const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
-  double s = rinv3_f64(r2);
+  double s = rinv3_fp64(dx, dy, dz, soft2);
   if (QARR) s *= pj.w;
   ax = fma(dx, s, ax);
   ay = fma(dy, s, ay);

@@ -214,6 +214,68 @@ __device__ __forceinline__ void df_rinv3(const float dh[3], const float dl[3], f
 // caller's length unit) never reach the clamp.
 constexpr float F32_YMAX = 1.099511627776e12f;  // 2^40
 
+// FP32 (hi, lo) split of d * 2^-sc, sc an integer: split_f64 with the scale
+// applied to the exponent fields.  A value that the scale takes below the FP32
+// normal range becomes a zero or subnormal (only components negligible next to
+// a scaled largest component in [1, 2) do).
+__device__ __forceinline__ void split_f64_scaled(double d, int sc, float &h, float &l) {
+  const unsigned lo = (unsigned)__double2loint(d);
+  const unsigned hi = (unsigned)__double2hiint(d);
+  unsigned lo2, ahi2;
+  asm("add.cc.u32 %0, %2, 0x10000000;\n\taddc.u32 %1, %3, 0;"
+      : "=r"(lo2), "=r"(ahi2)
+      : "r"(lo), "r"(hi & 0x7fffffffu));
+  const int t = max((int)ahi2 - (896 + sc) * (1 << 20), 0);
+  const unsigned sign = hi & 0x80000000u;
+  h = __uint_as_float(__funnelshift_l(lo2, (unsigned)t, 3) | sign);
+  const int r = ((int)(lo << 3)) >> 3;
+  const int e64 = (int)((hi >> 20) & 0x7ffu);
+  const int se = max(e64 - 948 - sc, 0);
+  l = __int2float_rn(r) * __uint_as_float(((unsigned)se << 23) | sign);
+}
+
+// Exact FP32 -> FP64 widening of f * 2^sc by integer ops: a zero or
+// subnormal f gives a signed zero, and a result outside the FP64 normal range
+// gives a signed zero or infinity.
+__device__ __forceinline__ double f32_to_f64_scaled(float f, int sc) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned a = b & 0x7fffffffu;
+  const unsigned sign = b & 0x80000000u;
+  const int e = (int)(a >> 23) + 896 + sc;
+  const int hi = (int)(sign | ((unsigned)e << 20) | ((a >> 3) & 0xfffffu));
+  const int lo = (int)(b << 29);
+  if (a < 0x00800000u || e <= 0) return __hiloint2double((int)sign, 0);
+  if (e >= 2047) return __hiloint2double((int)(sign | 0x7ff00000u), 0);
+  return __hiloint2double(hi, lo);
+}
+
+// (|d|^2 + soft2)^(-3/2) for an FP64 displacement d, with the r^2, 1/sqrt and
+// cube arithmetic on the FP32 pipe and one FP64 add.  d (and soft2) are scaled
+// by 2^-sc so that the largest of |d_k| and sqrt(soft2) lies in [1, 2): the
+// double-float r^2, residual and y^3 of df_rinv3 then stay far from FP32
+// overflow and underflow for any FP64 input, and the double-float result is
+// widened to FP64 with the scale 2^(-3 sc) put back in the exponent.
+// Relative error about 2^-44 (the double-float residual).  A zero
+// displacement without softening (the self pair) gives 0.
+__device__ __forceinline__ double rinv3_fp64(double dx, double dy, double dz, double soft2) {
+  const int ex = (__double2hiint(dx) >> 20) & 0x7ff;
+  const int ey = (__double2hiint(dy) >> 20) & 0x7ff;
+  const int ez = (__double2hiint(dz) >> 20) & 0x7ff;
+  const int e2 = (__double2hiint(soft2) >> 20) & 0x7ff;
+  const int es = e2 ? ((e2 - 1023) >> 1) + 1023 : 0;  // biased exponent of sqrt(soft2)
+  const int em = max(max(ex, ey), max(ez, es));
+  const int sc = em - 1023;
+  float dh[3], dl[3], s2h = 0.0f, s2l = 0.0f;
+  split_f64_scaled(dx, sc, dh[0], dl[0]);
+  split_f64_scaled(dy, sc, dh[1], dl[1]);
+  split_f64_scaled(dz, sc, dh[2], dl[2]);
+  if (e2) split_f64_scaled(soft2, 2 * sc, s2h, s2l);
+  float sh, sl;
+  df_rinv3(dh, dl, s2h, s2l, sh, sl);
+  const double s = f32_to_f64_scaled(sh, -3 * sc) + f32_to_f64_scaled(sl, -3 * sc);
+  return em ? s : 0.0;
+}
+
 // FP32 bulk shared by the two mixed modes: given the FP32 displacement,
 // acc += w_j d / s^3 with s^-3 = y^3 (1 + 3/2 e), y = MUFU.RSQ(s^2),
 // e = 1 - s^2 y^2 (one first-order correction in FP32).

@@ -48,8 +48,7 @@ __device__ __forceinline__ void pair_f64(double xi, double yi, double zi, const 
   const double dx = xi - pj.x;
   const double dy = yi - pj.y;
   const double dz = zi - pj.z;
-  const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
-  double s = rinv3_f64(r2);
+  double s = rinv3_fp64(dx, dy, dz, soft2);
   if (QARR) s *= pj.w;
   ax = fma(dx, s, ax);
   ay = fma(dy, s, ay);

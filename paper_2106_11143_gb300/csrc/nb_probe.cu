@@ -15,7 +15,7 @@ __global__ void k_rinv3_probe(int64_t n, const double *__restrict__ dx, const do
   const double x = dx[i], y = dy[i], z = dz[i];
   double s;
   if (MODE == MODE_FP64) {
-    s = rinv3_f64(fma(x, x, fma(y, y, fma(z, z, soft2))));
+    s = rinv3_fp64(x, y, z, soft2);
   } else if (fp64_like(MODE)) {
     s = ladder_rinv3<MODE>(fma(x, x, fma(y, y, fma(z, z, soft2))));
   } else if (MODE == MODE_DF64) {

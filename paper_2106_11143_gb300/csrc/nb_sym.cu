@@ -59,8 +59,7 @@ __device__ __forceinline__ void sym_step_fp64(const SD4 &pp, SD4 qd, double soft
 #pragma unroll 2
   for (int r = 0; r < 32; ++r) {
     const double dx = pp.x - qd.x, dy = pp.y - qd.y, dz = pp.z - qd.z;
-    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
-    const double s = rinv3_f64(r2);
+    const double s = rinv3_fp64(dx, dy, dz, soft2);
     const double sp = W ? s * qd.w : s;
     const double sq = W ? s * pp.w : s;
     a[0] = fma(dx, sp, a[0]);
@@ -352,7 +351,7 @@ __device__ __forceinline__ void sym_stage(SD4 *dst, int i, int BI, int64_t g, in
 }
 
 template <int MODE, bool QARR, bool P2>
-__global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, int G,
+__global__ void __launch_bounds__(SYM_THREADS, MODE == MODE_FP64 ? 2 : 0) k_pair_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ y,
                                                          const double *__restrict__ z,
@@ -460,8 +459,7 @@ __global__ void __launch_bounds__(SYM_THREADS) k_pair_sym(int64_t n, int nbk, in
         for (int j = 0; j < np; ++j) {
           const SD4 pj = posP[j];
           const double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-          const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
-          double s = rinv3_f64(r2);
+          double s = rinv3_fp64(dx, dy, dz, soft2);
           if (QARR) s *= pj.w;
           a[0] = fma(dx, s, a[0]);
           a[1] = fma(dy, s, a[1]);
