@@ -61,48 +61,6 @@ __device__ __forceinline__ double rsqrt_seed_f64(double r2) {
   return (e == 0) ? 0.0 : __hiloint2double(yhi, ylo);
 }
 
-// r2^(-3/2) for an FP64 r2 >= 0 with three FP64 instructions.
-// r2 = 2^(2k) r2s, r2s in [1, 4), is split by integer ops into FP32 parts
-// h (the top 24 significand bits) and l (the next 29 bits, rounded to 24):
-// r2s = h + l up to 2^-47 relative.  With y = MUFU.RSQ(h) and the exact
-// square y^2 = y2 + y2e (FMA), the Newton residual e = 1 - r2s y^2 is formed
-// in FP32 from the five products, each of which is computed exactly inside an
-// FFMA; the only roundings are of values near |e| < 2^-20, so e is accurate
-// to about 2^-44 absolute.  Then r2s^(-3/2) = y^3 (1 - e)^(-3/2) =
-// y^3 (1 + c), c = 3/2 e + 15/8 e^2 (truncation (35/16)|e|^3 < 2^-60), and
-// the FP64 part is Y = y 2^-k, Y^3 (1 + c) = fma(Y^3, c, Y^3).
-// Relative error <= ~2^-42 (worst case), ~2^-45 typical.
-// r2 == 0 or subnormal returns 0 (the pair then contributes nothing).
-__device__ __forceinline__ double rinv3_f64(double r2) {
-  const int hi = __double2hiint(r2);
-  const unsigned lo = (unsigned)__double2loint(r2);
-  const int e = hi >> 20;
-  const int k = (e - 1023) >> 1;
-  const unsigned fs = __funnelshift_l(lo, (unsigned)hi, 3);
-  const bool odd = (e & 1) != 0;  // e - 1023 even: r2s in [1, 2)
-  const float h = __uint_as_float((fs & 0x007fffffu) | (odd ? 0x3f800000u : 0x40000000u));
-  const float l = __uint2float_rn(lo & 0x1fffffffu) * (odd ? 0x1p-52f : 0x1p-51f);
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(h));
-  const float y2 = y * y;
-  const float y2e = fmaf(y, y, -y2);
-  float r = fmaf(-h, y2, 1.0f);
-  r = fmaf(-h, y2e, r);
-  r = fmaf(-l, y2, r);
-  const float c = r * fmaf(r, 1.875f, 1.5f);
-  const unsigned yb = __float_as_uint(y);
-  const int yhi = (int)(yb >> 3) + ((896 - k) << 20);
-  const int ylo = (int)(yb << 29);
-  const double Y = (e == 0) ? 0.0 : __hiloint2double(yhi, ylo);
-  const double Y3 = (Y * Y) * Y;
-  const unsigned cb = __float_as_uint(c);
-  const unsigned ca = cb & 0x7fffffffu;
-  const double C = (ca < 0x00800000u) ? 0.0
-                                      : __hiloint2double((int)((cb & 0x80000000u) | ((ca >> 3) + (896u << 20))),
-                                                         (int)(cb << 29));
-  return fma(Y3, C, Y3);
-}
-
 // r2^(-3/2) by the precision-ladder methods of Sec. IV: SQRT+DIV (1/sqrt in
 // FP64), the bare FP32 seed, or the seed refined by one or two Newton steps
 // y <- y (3/2 - (r2/2) y^2); then the cube y^3.  r2 == 0 gives 0.
@@ -274,6 +232,67 @@ __device__ __forceinline__ double rinv3_fp64(double dx, double dy, double dz, do
   df_rinv3(dh, dl, s2h, s2l, sh, sl);
   const double s = f32_to_f64_scaled(sh, -3 * sc) + f32_to_f64_scaled(sl, -3 * sc);
   return em ? s : 0.0;
+}
+
+// r^-3 and r^-5 together for the pair VJP, as rinv3_fp64 does r^-3: the
+// double-float r^-5 = y^5 (1 + 5/2 e + 35/8 e^2) shares the seed, residual and
+// y^2 of r^-3.  Returns r^-3 in s3 and 3 r^-5 in s5x3 (the factor of the VJP's
+// second term, applied exactly in double-float before the widening), 0 for a
+// zero displacement without softening.
+__device__ __forceinline__ void rinv35_fp64(double dx, double dy, double dz, double soft2, double &s3,
+                                            double &s5x3) {
+  const int ex = (__double2hiint(dx) >> 20) & 0x7ff;
+  const int ey = (__double2hiint(dy) >> 20) & 0x7ff;
+  const int ez = (__double2hiint(dz) >> 20) & 0x7ff;
+  const int e2 = (__double2hiint(soft2) >> 20) & 0x7ff;
+  const int es = e2 ? ((e2 - 1023) >> 1) + 1023 : 0;
+  const int em = max(max(ex, ey), max(ez, es));
+  const int sc = em - 1023;
+  float dh[3], dl[3], s2h = 0.0f, s2l = 0.0f;
+  split_f64_scaled(dx, sc, dh[0], dl[0]);
+  split_f64_scaled(dy, sc, dh[1], dl[1]);
+  split_f64_scaled(dz, sc, dh[2], dl[2]);
+  if (e2) split_f64_scaled(soft2, 2 * sc, s2h, s2l);
+  // double-float r^2 = h + l from exact products (as in df_rinv3)
+  const float p0 = dh[0] * dh[0], p1 = dh[1] * dh[1], p2 = dh[2] * dh[2];
+  const float q0 = fmaf(dh[0], dh[0], -p0), q1 = fmaf(dh[1], dh[1], -p1), q2 = fmaf(dh[2], dh[2], -p2);
+  float h, t1, t2;
+  two_sum_f(p0, p1, h, t1);
+  two_sum_f(h, p2, h, t2);
+  float l = (t1 + t2) + (q0 + q1 + q2);
+  l = fmaf(dh[0] + dh[0], dl[0], l);
+  l = fmaf(dh[1] + dh[1], dl[1], l);
+  l = fmaf(dh[2] + dh[2], dl[2], l);
+  if (e2) {
+    float t3;
+    two_sum_f(h, s2h, h, t3);
+    l += t3 + s2l;
+  }
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(h));
+  const float y2 = y * y;
+  const float y2e = fmaf(y, y, -y2);
+  float r = fmaf(-h, y2, 1.0f);
+  r = fmaf(-h, y2e, r);
+  r = fmaf(-l, y2, r);
+  const float c3 = r * fmaf(r, 1.875f, 1.5f);
+  const float c5 = r * fmaf(r, 4.375f, 2.5f);
+  // y^3 and y^5 as double-floats
+  const float y3h = y2 * y;
+  float y3e = fmaf(y2, y, -y3h);
+  y3e = fmaf(y2e, y, y3e);
+  const float y5h = y3h * y2;
+  float y5e = fmaf(y3h, y2, -y5h);
+  y5e = fmaf(y3h, y2e, fmaf(y3e, y2, y5e));
+  const float s3l = fmaf(y3h, c3, y3e);
+  const float s5l = fmaf(y5h, c5, y5e);
+  // 3 s5 exactly as a double-float: 3 y5h = m + me (TwoProd)
+  const float m = 3.0f * y5h;
+  const float me = fmaf(3.0f, y5h, -m) + 3.0f * s5l;
+  const double a3 = f32_to_f64_scaled(y3h, -3 * sc) + f32_to_f64_scaled(s3l, -3 * sc);
+  const double a5 = f32_to_f64_scaled(m, -5 * sc) + f32_to_f64_scaled(me, -5 * sc);
+  s3 = em ? a3 : 0.0;
+  s5x3 = em ? a5 : 0.0;
 }
 
 // FP32 bulk shared by the two mixed modes: given the FP32 displacement,

@@ -77,7 +77,7 @@ __device__ __forceinline__ void pair_ladder(double xi, double yi, double zi, con
 // The displacement is an FP64 subtraction (exact for close pairs), split into
 // FP32 (hi, lo) parts.  r^2 is summed as a double-float from exact products
 // (FMA) and TwoSums; r^-3 takes the FP32 seed of its high part and the
-// compensated residual of rinv3_f64, with y^3 kept as a double-float; the
+// Newton residual formed in compensated FP32, with y^3 kept as a double-float; the
 // three force products are exact-product double-floats accumulated with
 // TwoSum into a per-tile double-float, flushed into FP64 once per tile.
 // Relative error per pair about 2^-44 (the residual's FP32 roundings).
@@ -312,6 +312,8 @@ __global__ void __launch_bounds__(256) k_pair_phi(int64_t n, int64_t jchunk,
 // ---------------------------------------------------------------------------
 // VJP kernel (FP64): part[(jc*3+c)*n + i] =
 //   sum_{j in chunk} w_j [ dl^c / s^3 - 3 d^c (d . dl) / s^5 ],  dl = lam_i - lam_j.
+// FP64 for the differences, the dot product and the accumulation; s^-3 and
+// 3 s^-5 come from the FP32 pipe (rinv35_fp64).
 template <bool QARR>
 __global__ void __launch_bounds__(256) k_pair_vjp(int64_t n, int64_t jchunk,
                                                   const double *__restrict__ x,
@@ -346,18 +348,15 @@ __global__ void __launch_bounds__(256) k_pair_vjp(int64_t n, int64_t jchunk,
       const D4 pj = s4[2 * k];
       const D4 lj = s4[2 * k + 1];
       const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-      const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
-      const double Y = rsqrt_seed_f64(r2);
-      const double e = fma(-r2, Y * Y, 1.0);
-      const double p = fma(e, 0.375, 0.5);
-      const double inv = fma(Y * e, p, Y);
-      const double inv2 = inv * inv;
-      double s3 = inv2 * inv;
-      if (QARR) s3 *= pj.w;
-      const double s5 = s3 * inv2;
+      double s3, s5x3;
+      rinv35_fp64(dx, dy, dz, soft2, s3, s5x3);
+      if (QARR) {
+        s3 *= pj.w;
+        s5x3 *= pj.w;
+      }
       const double ex = mi - lj.x, ey = ni - lj.y, ez = oi - lj.z;
       const double dot = fma(dx, ex, fma(dy, ey, dz * ez));
-      const double w3 = 3.0 * (dot * s5);
+      const double w3 = dot * s5x3;
       gx = fma(ex, s3, gx);
       gy = fma(ey, s3, gy);
       gz = fma(ez, s3, gz);
