@@ -234,6 +234,49 @@ __device__ __forceinline__ double rinv3_fp64(double dx, double dy, double dz, do
   return em ? s : 0.0;
 }
 
+// (|d|^2 + soft2)^(-1/2) for the potential, as rinv3_fp64 does r^-3: the
+// double-float r^2 and compensated residual e of df_rinv3, then
+// r^-1 = y (1 + 1/2 e + 3/8 e^2) as the double-float (y, y c) widened with one
+// FP64 add.  0 for a zero displacement without softening.
+__device__ __forceinline__ double rinv1_fp64(double dx, double dy, double dz, double soft2) {
+  const int ex = (__double2hiint(dx) >> 20) & 0x7ff;
+  const int ey = (__double2hiint(dy) >> 20) & 0x7ff;
+  const int ez = (__double2hiint(dz) >> 20) & 0x7ff;
+  const int e2 = (__double2hiint(soft2) >> 20) & 0x7ff;
+  const int es = e2 ? ((e2 - 1023) >> 1) + 1023 : 0;
+  const int em = max(max(ex, ey), max(ez, es));
+  const int sc = em - 1023;
+  float dh[3], dl[3], s2h = 0.0f, s2l = 0.0f;
+  split_f64_scaled(dx, sc, dh[0], dl[0]);
+  split_f64_scaled(dy, sc, dh[1], dl[1]);
+  split_f64_scaled(dz, sc, dh[2], dl[2]);
+  if (e2) split_f64_scaled(soft2, 2 * sc, s2h, s2l);
+  const float p0 = dh[0] * dh[0], p1 = dh[1] * dh[1], p2 = dh[2] * dh[2];
+  const float q0 = fmaf(dh[0], dh[0], -p0), q1 = fmaf(dh[1], dh[1], -p1), q2 = fmaf(dh[2], dh[2], -p2);
+  float h, t1, t2;
+  two_sum_f(p0, p1, h, t1);
+  two_sum_f(h, p2, h, t2);
+  float l = (t1 + t2) + (q0 + q1 + q2);
+  l = fmaf(dh[0] + dh[0], dl[0], l);
+  l = fmaf(dh[1] + dh[1], dl[1], l);
+  l = fmaf(dh[2] + dh[2], dl[2], l);
+  if (e2) {
+    float t3;
+    two_sum_f(h, s2h, h, t3);
+    l += t3 + s2l;
+  }
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(h));
+  const float y2 = y * y;
+  const float y2e = fmaf(y, y, -y2);
+  float r = fmaf(-h, y2, 1.0f);
+  r = fmaf(-h, y2e, r);
+  r = fmaf(-l, y2, r);
+  const float c = r * fmaf(r, 0.375f, 0.5f);
+  const double a = f32_to_f64_scaled(y, -sc) + f32_to_f64_scaled(y * c, -sc);
+  return em ? a : 0.0;
+}
+
 // r^-3 and r^-5 together for the pair VJP, as rinv3_fp64 does r^-3: the
 // double-float r^-5 = y^5 (1 + 5/2 e + 35/8 e^2) shares the seed, residual and
 // y^2 of r^-3.  Returns r^-3 in s3 and 3 r^-5 in s5x3 (the factor of the VJP's

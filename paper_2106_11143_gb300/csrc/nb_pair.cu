@@ -297,11 +297,7 @@ __global__ void __launch_bounds__(256) k_pair_phi(int64_t n, int64_t jchunk,
     for (int k = 0; k < cnt; ++k) {
       const D4 pj = s4[k];
       const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-      const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
-      const double Y = rsqrt_seed_f64(r2);
-      const double e = fma(-r2, Y * Y, 1.0);
-      const double p = fma(e, 0.375, 0.5);
-      double inv = fma(Y * e, p, Y);
+      double inv = rinv1_fp64(dx, dy, dz, soft2);
       inv = (j0 + k == ic) ? 0.0 : inv;  // self pair (matters when soft2 > 0)
       acc = QARR ? fma(pj.w, inv, acc) : acc + inv;
     }
@@ -512,10 +508,26 @@ bool tuning_lookup(int kind, int mode, int64_t n, int *block, int *R, int *bps) 
   return false;
 }
 
+// Largest scratch the symmetric kernel's per-partner-block partials may take:
+// a quarter of the current device's memory (queried once per device), 2 GB if
+// the query fails.
+static double sym_partial_cap() {
+  static std::mutex mu;
+  static double cap[64] = {0.0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 2e9;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cap[dev] == 0.0) {
+    cudaDeviceProp prop;
+    cap[dev] = (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) ? 0.25 * (double)prop.totalGlobalMem : 2e9;
+  }
+  return cap[dev];
+}
+
 Plan make_plan(int64_t n, int mode, int kind) {
   Plan pl;
-  // Symmetric half-pair kernel for the force paths from n = 16384 on, when
-  // the per-partner-block partials (nbk * 3n doubles) stay below 2 GB.  Block
+  // Symmetric half-pair kernel for the force paths from n = 16384 on, while
+  // the per-partner-block partials (nbk * 3n doubles) fit the cap above.  Block
   // sizes: the fastest measured on GB300 (split: 512 ions, whose two-ion-per-
   // lane P-tiles need G >= 16).
   if (kind == 0 && (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || mode == MODE_SPLIT)) {
@@ -527,7 +539,7 @@ Plan make_plan(int64_t n, int mode, int kind) {
       G = tb / 32;
     }
     const int64_t nbk = (n + 32 * G - 1) / (32 * G);
-    if (use && (double)nbk * 3.0 * (double)n * 8.0 <= 2e9) {
+    if (use && (double)nbk * 3.0 * (double)n * 8.0 <= sym_partial_cap()) {
       pl.sym = 1;
       pl.G = G;
       pl.n_jc = (int)nbk;
