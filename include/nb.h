@@ -218,9 +218,12 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
  * or 256), `R` ions per thread (1, 2, 4; force kernel only) and about
  * `blocks_per_sm` (i-tile, j-chunk) blocks per SM.  For kind 3 (the ensemble
  * kernel): `block` threads per block (multiple of 32, <= 512).  For kind 4
- * (the symmetric half-pair force kernel of NB_FP64 / NB_DF64): `block` ions
+ * (the symmetric half-pair force kernel of the four force precisions): `block` ions
  * per block pair unit (256, 512, 1024) and R = 1 to use it or 0 to disable
- * it for that n range (by default it is used from n = 16384).  The latest
+ * it for that n range (by default it is used from n = 16384).  For kind 5
+ * (the symmetric VJP kernel; `precision` NB_FP64): `block` ions per block
+ * pair unit (128 or 256) and R = 1 / 0 to use / disable it (by default it is
+ * used from n = 4096).  The latest
  * matching entry wins; block == 0 removes every override.  Results stay
  * deterministic for a fixed shape; different shapes may differ in the last
  * bits (summation order), except kind 3, which is shape-independent.     */

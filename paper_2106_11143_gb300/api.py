@@ -298,7 +298,7 @@ def plan_batched(offsets, n_bins):
     return order[:n_inst], start, mx.value, mean.value
 
 
-KINDS = {"force": 0, "potential": 1, "vjp": 2, "ensemble": 3, "symmetric": 4}
+KINDS = {"force": 0, "potential": 1, "vjp": 2, "ensemble": 3, "symmetric": 4, "symmetric_vjp": 5}
 
 
 def set_tuning(kind, precision, n_lo, n_hi, block, R=1, blocks_per_sm=16):

@@ -473,6 +473,9 @@ cudaError_t launch_split_positions(int64_t n, const double *x, const double *y,
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
                             const double *z, const double *q, const PosF32 &pf, double soft2,
                             double *part, cudaStream_t st);
+cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const double *y,
+                           const double *z, const double *q, const double *lx, const double *ly,
+                           const double *lz, double soft2, double *part, cudaStream_t st);
 
 // Epilogue kernels (nb_integrate.cu).
 struct StateView {

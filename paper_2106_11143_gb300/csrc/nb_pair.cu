@@ -449,6 +449,7 @@ cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const do
                             const double *z, const double *q, const double *lx,
                             const double *ly, const double *lz, double soft2, double *part,
                             cudaStream_t st) {
+  if (pl.sym) return launch_vjp_sym(n, pl.n_jc, pl.G, x, y, z, q, lx, ly, lz, soft2, part, st);
   const dim3 grid(pl.n_it, pl.n_jc);
   const size_t smem = 2 * sizeof(D4) * pl.block;
   if (q)
@@ -544,6 +545,25 @@ Plan make_plan(int64_t n, int mode, int kind) {
       pl.G = G;
       pl.n_jc = (int)nbk;
       pl.block = 256;
+      return pl;
+    }
+  }
+  // Symmetric VJP kernel from n = 4096 (128-ion blocks below n = 16384, 256
+  // above), under the same cap; tuning kind 5 overrides (R = 0 disables).
+  if (kind == 2) {
+    int G = n >= 16384 ? 8 : 4;
+    bool use = n >= 4096;
+    int tb = 0, tr = 0, tbps = 0;
+    if (tuning_lookup(5, mode, n, &tb, &tr, &tbps)) {
+      use = tr != 0;
+      G = tb / 32;
+    }
+    const int64_t nbk = (n + 32 * G - 1) / (32 * G);
+    if (use && (double)nbk * 3.0 * (double)n * 8.0 <= sym_partial_cap()) {
+      pl.sym = 1;
+      pl.G = G;
+      pl.n_jc = (int)nbk;
+      pl.block = 128;
       return pl;
     }
   }

@@ -1,0 +1,210 @@
+// nb_vjp_sym.cu -- symmetric (half-pair) kernel for the pair-force VJP.
+//
+// For a pair (i, j) with d = r_i - r_j and dl = lam_i - lam_j, the VJP term
+//   T = dl r^-3 - 3 (d . dl) r^-5 d
+// changes sign under i <-> j (both d and dl do), so one evaluation serves both
+// ions: g_i += w_j T and g_j -= w_i T.  The work is organised as in the force
+// kernel (nb_sym.cu): block pairs (P, Q), P <= Q, of BI = 32 G ions; each
+// warp takes Q-tiles and visits the P-tiles in the staggered order
+// pt = (qs + k) mod G, one per barrier-separated step, so the warps hold
+// distinct P-tiles and update their shared-memory accumulators without
+// atomics.  A lane holds one P-ion (position, weight and lam in registers);
+// the Q-tile (64 B per ion) sits twice in shared memory, so the entry
+// (lane + r) mod 32 of rotation r is a fixed offset from the lane's base; only
+// the Q accumulators rotate, by warp shuffle.  Diagonal items (P == Q) are
+// one-sided.  Output: one partial per partner block, part[(X*3 + c)*n + i],
+// summed in block order by the VJP epilogue: bitwise reproducible.
+//
+// Four warps per block and 128-ion blocks at n < 16384 give enough items to
+// fill the GPU at the adjoint's sizes (528 items at n = 4096).
+#include <mutex>
+
+#include "nb_common.cuh"
+
+namespace nb {
+
+constexpr int VJP_THREADS = 128;
+constexpr int VJP_W = VJP_THREADS / 32;
+constexpr double VJP_FAR = 1e18;
+
+struct __align__(16) VD8 {
+  double x, y, z, w, lx, ly, lz, pad;
+};
+
+__device__ __forceinline__ double vshfl_next(double v, int lane) {
+  return __shfl_sync(0xffffffffu, v, (lane + 1) & 31);
+}
+
+// One pair evaluation: P-ion p against Q-ion q; a (P side) += w_q T,
+// b (Q side) -= w_p T.
+template <bool W>
+__device__ __forceinline__ void vjp_eval(const VD8 &p, const VD8 &q, double soft2, double a[3],
+                                         double b[3]) {
+  const double dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+  const double ex = p.lx - q.lx, ey = p.ly - q.ly, ez = p.lz - q.lz;
+  double s3, s5x3;
+  rinv35_fp64(dx, dy, dz, soft2, s3, s5x3);
+  const double w3 = fma(dx, ex, fma(dy, ey, dz * ez)) * s5x3;
+  const double sa = W ? s3 * q.w : s3, wa = W ? w3 * q.w : w3;
+  const double sb = W ? s3 * p.w : s3, wb = W ? w3 * p.w : w3;
+  a[0] = fma(-dx, wa, fma(ex, sa, a[0]));
+  a[1] = fma(-dy, wa, fma(ey, sa, a[1]));
+  a[2] = fma(-dz, wa, fma(ez, sa, a[2]));
+  b[0] = fma(dx, wb, fma(-ex, sb, b[0]));
+  b[1] = fma(dy, wb, fma(-ey, sb, b[1]));
+  b[2] = fma(dz, wb, fma(-ez, sb, b[2]));
+}
+
+// Staged entry i of a block (g = global index); ions past n are weight-0,
+// lam-0 dummies far away.  dup: the Q-side layout, each 32-ion tile stored
+// twice back to back.
+template <bool QARR>
+__device__ __forceinline__ void vjp_stage(VD8 *dst, int i, int64_t g, int64_t n, const double *x,
+                                          const double *y, const double *z, const double *q,
+                                          const double *lx, const double *ly, const double *lz,
+                                          bool dup) {
+  VD8 e;
+  if (g < n) {
+    e.x = x[g];
+    e.y = y[g];
+    e.z = z[g];
+    e.w = QARR ? q[g] : 1.0;
+    e.lx = lx[g];
+    e.ly = ly[g];
+    e.lz = lz[g];
+  } else {
+    e.x = e.y = e.z = VJP_FAR;
+    e.w = 0.0;
+    e.lx = e.ly = e.lz = 0.0;
+  }
+  e.pad = 0.0;
+  if (dup) {
+    const int k = (i >> 5) * 64 + (i & 31);
+    dst[k] = e;
+    dst[k + 32] = e;
+  } else {
+    dst[i] = e;
+  }
+}
+
+template <bool QARR>
+__global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, int G,
+                                                         const double *__restrict__ x,
+                                                         const double *__restrict__ y,
+                                                         const double *__restrict__ z,
+                                                         const double *__restrict__ q,
+                                                         const double *__restrict__ lx,
+                                                         const double *__restrict__ ly,
+                                                         const double *__restrict__ lz, double soft2,
+                                                         double *__restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int BI = 32 * G;
+  VD8 *posP = reinterpret_cast<VD8 *>(smem_raw);
+  VD8 *posQ = posP + BI;                                      // 2 BI entries (dup)
+  double *accP = reinterpret_cast<double *>(posQ + 2 * BI);  // [3][BI]
+  int t = blockIdx.x, P = 0;
+  while (t >= nbk - P) {  // item -> (P, Q), P <= Q, row by row
+    t -= nbk - P;
+    ++P;
+  }
+  const int Q = P + t;
+  const int64_t p0 = (int64_t)P * BI, q0 = (int64_t)Q * BI;
+  const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < BI; i += VJP_THREADS) {
+    vjp_stage<QARR>(posP, i, p0 + i, n, x, y, z, q, lx, ly, lz, false);
+    if (P != Q) vjp_stage<QARR>(posQ, i, q0 + i, n, x, y, z, q, lx, ly, lz, true);
+    accP[i] = 0.0;
+    accP[BI + i] = 0.0;
+    accP[2 * BI + i] = 0.0;
+  }
+  __syncthreads();
+
+  if (P == Q) {  // the block's own pairs, one-sided (the self pair gives T = 0)
+    for (int i = tid; i < np; i += VJP_THREADS) {
+      const VD8 pi = posP[i];
+      double a[3] = {0.0, 0.0, 0.0}, dummy[3];
+      for (int j = 0; j < np; ++j) vjp_eval<QARR>(pi, posP[j], soft2, a, dummy);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + p0 + i] = a[c];
+    }
+    return;
+  }
+
+  const bool weighted = QARR || np < BI || nq < BI;
+  for (int qs = warp; qs < G; qs += VJP_W) {
+    const VD8 *qd = posQ + qs * 64 + lane;
+    double aq[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < G; ++k) {
+      const int pt = (qs + k) % G;
+      __syncthreads();  // all warps are at step k: their P-tiles are distinct
+      const int ip = pt * 32 + lane;
+      const VD8 pp = posP[ip];
+      double a[3] = {0.0, 0.0, 0.0}, b[3] = {0.0, 0.0, 0.0};
+      if (weighted) {
+#pragma unroll 2
+        for (int r = 0; r < 32; ++r) {
+          vjp_eval<true>(pp, qd[r], soft2, a, b);
+          b[0] = vshfl_next(b[0], lane);
+          b[1] = vshfl_next(b[1], lane);
+          b[2] = vshfl_next(b[2], lane);
+        }
+      } else {
+#pragma unroll 2
+        for (int r = 0; r < 32; ++r) {
+          vjp_eval<false>(pp, qd[r], soft2, a, b);
+          b[0] = vshfl_next(b[0], lane);
+          b[1] = vshfl_next(b[1], lane);
+          b[2] = vshfl_next(b[2], lane);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        accP[c * BI + ip] += a[c];
+        aq[c] += b[c];
+      }
+    }
+    const int iq = qs * 32 + lane;
+    if (iq < nq)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + q0 + iq] = aq[c];
+  }
+  __syncthreads();
+  for (int i = tid; i < np; i += VJP_THREADS)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) part[((int64_t)Q * 3 + c) * n + p0 + i] = accP[c * BI + i];
+}
+
+static size_t vjp_smem_bytes(int G) { return (size_t)32 * G * (3 * sizeof(VD8) + 3 * sizeof(double)); }
+
+cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const double *y,
+                           const double *z, const double *q, const double *lx, const double *ly,
+                           const double *lz, double soft2, double *part, cudaStream_t st) {
+  if (G != 4 && G != 8) return cudaErrorInvalidValue;
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!done[dev]) {
+      const int lim = (int)vjp_smem_bytes(8);
+      e = cudaFuncSetAttribute(k_vjp_sym<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_vjp_sym<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e != cudaSuccess) return e;
+      done[dev] = true;
+    }
+  }
+  const int items = nbk * (nbk + 1) / 2;
+  const size_t smem = vjp_smem_bytes(G);
+  if (q)
+    k_vjp_sym<true><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, part);
+  else
+    k_vjp_sym<false><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, part);
+  return cudaGetLastError();
+}
+
+}  // namespace nb

@@ -134,6 +134,31 @@ def test_vjp(nb, orc):
         assert np.max(np.abs(g - ref)) <= 1e-11 * scale
 
 
+def test_vjp_symmetric_kernel(nb, orc):
+    """The half-pair VJP kernel (on from n = 4096), forced on at small and
+    ragged sizes with both block sizes, with charges and softening, against the
+    oracle; and against the one-sided VJP kernel at n = 4100."""
+    rng = np.random.default_rng(6)
+    try:
+        for k, (n, block) in enumerate([(2, 128), (129, 128), (1000, 128), (1500, 256), (4100, 128)]):
+            nb.set_tuning("symmetric_vjp", "fp64", 1, 1 << 40, block, R=1)
+            pos, _ = W.random_cloud(n, seed=400 + k)
+            q = W.E_CHARGE * rng.choice([-1.0, 1.0, 2.0], size=n) if k % 2 else None
+            lam = rng.standard_normal((3, n))
+            phys = W.phys(omega=(6e6, 5e6, 1.2e6), soft2=(0.1e-6) ** 2 if k == 2 else 0.0)
+            g = nb.forces_vjp(nb.Params.from_phys(phys), nb.System(pos, q=q), lam, total=True).cpu().numpy()
+            ref = np.stack(orc.forces_vjp(oparams(orc, phys), 0.0, *pos, *lam, q=q, include_trap=True))
+            assert np.max(np.abs(g - ref)) <= 1e-11 * np.max(np.abs(ref)), (n, block)
+            g2 = nb.forces_vjp(nb.Params.from_phys(phys), nb.System(pos, q=q), lam, total=True).cpu().numpy()
+            assert np.array_equal(g, g2)
+        nb.set_tuning("symmetric_vjp", "fp64", 1, 1 << 40, 128, R=0)
+        one = nb.forces_vjp(nb.Params.from_phys(phys), nb.System(pos, q=q), lam, total=True).cpu().numpy()
+    finally:
+        nb.set_tuning("force", "fp64", 0, 0, 0)
+    assert not np.array_equal(one, g)  # genuinely the other kernel
+    assert np.max(np.abs(one - g)) <= 1e-11 * np.max(np.abs(g))
+
+
 def _oracle_traj(orc, phys, pos, vel, nsteps, reverse=False, q=None, eps=0.0):
     p = oparams(orc, phys)
     pos = np.asarray(pos) * (1.0 + eps)

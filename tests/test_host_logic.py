@@ -59,5 +59,10 @@ def test_tuning_validation(api):
         api.set_tuning("potential", "fp64", 0, 100, 64, R=2)
     with pytest.raises(api.NBError):
         api.set_tuning("ensemble", "fp64", 0, 100, 1024)
+    with pytest.raises(api.NBError):
+        api.set_tuning("symmetric_vjp", "fp64", 0, 100, 512)
+    with pytest.raises(api.NBError):
+        api.set_tuning("symmetric_vjp", "fp64", 0, 100, 128, R=2)
+    api.set_tuning("symmetric_vjp", "fp64", 0, 100, 256, R=0)
     api.set_tuning("force", "fp64", 0, 100, 64, R=2, blocks_per_sm=8)
     api.set_tuning("force", "fp64", 0, 0, 0)  # clear
