@@ -225,6 +225,26 @@ def test_trajectory_parity(nb, orc, which, precision):
     assert dv <= max(10 * dv_self, 1e-14 * V) + k * dt * 1e-12 * amax
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_trajectory_full_size_rf(nb, orc, precision):
+    """The RF workload at its full N = 16384, where nb_step runs the symmetric
+    kernel (as the bench does from n = 16384): 20 steps of the time-dependent
+    trap with friction against the oracle, same tolerance as above."""
+    w = W.cloud_rf_16384()
+    phys, nsteps = w["phys"], 20
+    ref = _oracle_traj(orc, phys, w["pos"], w["vel"], nsteps)
+    sysm = _gpu_traj(nb, phys, w["pos"], w["vel"], nsteps, precision=precision, chunks=2)
+    dp_self, dv_self = _self_divergence(orc, phys, w["pos"], w["vel"], nsteps, ref)
+    dp, dv = _traj_errs(sysm, ref)
+    L = np.max(np.abs(w["pos"]))
+    V = math.sqrt(W.K_B * 10e-3 / W.MASS_40U)
+    print("rf N=16384 %s: gpu dp=%.3g dv=%.3g | oracle self dp=%.3g dv=%.3g" % (precision, dp, dv, dp_self, dv_self))
+    amax = max(np.max(np.abs(ref[k])) for k in ("ax", "ay", "az"))
+    k, dt = nsteps, phys["dt"]
+    assert dp <= max(10 * dp_self, 1e-14 * L) + k * k * dt * dt * 1e-12 * amax
+    assert dv <= max(10 * dv_self, 1e-14 * V) + k * dt * 1e-12 * amax
+
+
 def _traj_errs_np(a, b):
     ap = np.stack([a["x"], a["y"], a["z"]]); bp = np.stack([b["x"], b["y"], b["z"]])
     av = np.stack([a["vx"], a["vy"], a["vz"]]); bv = np.stack([b["vx"], b["vy"], b["vz"]])
