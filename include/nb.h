@@ -217,7 +217,9 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
  * `precision` and n in [n_lo, n_hi]: `block` threads per block (32, 64, 128
  * or 256), `R` ions per thread (1, 2, 4; force kernel only) and about
  * `blocks_per_sm` (i-tile, j-chunk) blocks per SM.  For kind 3 (the ensemble
- * kernel): `block` threads per block (multiple of 32, <= 512).  For kind 4
+ * kernel): `block` threads per block (multiple of 32, <= 512), and R = 0 to
+ * keep its one-sided force phase (by default fp64 ensembles whose instances
+ * all have at most 4096 ions use the half-pair phase).  For kind 4
  * (the symmetric half-pair force kernel of the four force precisions): `block` ions
  * per block pair unit (256, 512, 1024) and R = 1 to use it or 0 to disable
  * it for that n range (by default it is used from n = 16384).  For kind 5

@@ -419,10 +419,12 @@ nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t
   cudaStream_t st = (cudaStream_t)stream;
   Arena *a = nullptr;
   NB_TRY(get_arena(st, 256, &a));
-  int threads = 256, R = 1, bps = 1;  // 256 threads: fastest in the autotuner on GB300
+  // fastest on GB300: 512 threads for the half-pair fp64 phase, 256 for df64
+  int threads = params->precision == NB_DF64 ? 256 : 512, R = 1, bps = 1;
   tuning_lookup(3, params->precision, packed->n, &threads, &R, &bps);
   const int n_bins = std::min(n_inst, device_sm_count());
-  NB_CUDA_TRY(launch_batched(to_phys(params), to_view(packed), n_inst, offsets, n_bins, threads,
+  // a tuning entry with R = 0 keeps the one-sided force phase
+  NB_CUDA_TRY(launch_batched(to_phys(params), to_view(packed), n_inst, offsets, n_bins, threads, R != 0,
                              packed->step, nsteps, a->err, st));
   count_launches(1);
   packed->step += nsteps;

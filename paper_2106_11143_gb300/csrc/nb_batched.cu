@@ -18,8 +18,10 @@
 // kernel by value (__grid_constant__), so a launch needs no host-to-device
 // copy and can be captured in a CUDA graph.
 //
-// The arithmetic of an ion depends only on its instance (the j order is
-// 0..n-1, accumulation sequential per ion), not on the schedule or the block
+// fp64 instances of at most 4096 ions use a half-pair force phase
+// (bsym_forces below); larger instances and df64 use the one-sided phase.
+// Either way the arithmetic of an ion depends only on its instance (a fixed
+// pair order and accumulation order per ion), not on the schedule or the block
 // size, so results are bitwise reproducible.
 #include <algorithm>
 #include <mutex>
@@ -100,6 +102,106 @@ __device__ __forceinline__ void bphilox(uint32_t c[4], uint32_t k0, uint32_t k1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Half-pair (Newton's third law) force phase for fp64 instances of at most
+// BATCH_SYM_N ions.  The instance is padded to whole 32-ion tiles with
+// weight-0 dummies far away; the per-ion sums go to FP64 accumulators in
+// shared memory.  A diagonal phase evaluates each tile against itself
+// (one-sided); then Tp - 1 rounds of a round-robin schedule (circle method on
+// Tp = T rounded up to even tiles, a bye for odd T) pair every two tiles once,
+// each tile appearing once per round, so the warps of a round touch disjoint
+// accumulators; a barrier separates the rounds.  Within a tile pair a lane
+// holds one ion of tile a, reads tile b at the rotated index (lane + r) mod 32
+// and rotates tile b's accumulators by shuffle.  The order of every sum is
+// fixed by the schedule, not by the block size.
+constexpr int BATCH_SYM_N = 4096;
+
+__device__ __forceinline__ double bshfl_next(double v, int lane) {
+  return __shfl_sync(0xffffffffu, v, (lane + 1) & 31);
+}
+
+template <bool W>
+__device__ __forceinline__ void bsym_eval(const BD4 &p, const BD4 &q, double soft2, double a[3],
+                                          double b[3]) {
+  const double dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+  const double s = rinv3_fp64(dx, dy, dz, soft2);
+  const double sp = W ? s * q.w : s, sq = W ? s * p.w : s;
+  a[0] = fma(dx, sp, a[0]);
+  a[1] = fma(dy, sp, a[1]);
+  a[2] = fma(dz, sp, a[2]);
+  b[0] = fma(-dx, sq, b[0]);
+  b[1] = fma(-dy, sq, b[1]);
+  b[2] = fma(-dz, sq, b[2]);
+}
+
+// Tiles (a, b) of round rho, pair k, for Tp tiles (circle method).
+__device__ __forceinline__ void round_pair(int rho, int k, int Tp, int &a, int &b) {
+  if (k == 0) {
+    a = rho;
+    b = Tp - 1;
+  } else {
+    a = (rho + k) % (Tp - 1);
+    b = (rho - k + Tp - 1) % (Tp - 1);
+  }
+}
+
+// The force phase: acc[c * npad + i] = sum_j w_j (r_i - r_j) / |r_i - r_j|^3
+// for the instance's np32 staged entries (n real ions, weights in w).
+template <bool QARR>
+__device__ void bsym_forces(const BD4 *sp, double *acc, int npad, int n, int np32, double soft2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  const int T = np32 >> 5;
+  const bool ragged = (n & 31) != 0;
+  // diagonal tiles, one-sided (the self pair gives 0)
+  for (int t = warp; t < T; t += NW) {
+    const int i = t * 32 + lane;
+    const BD4 pi = sp[i];
+    double a[3] = {0.0, 0.0, 0.0}, dummy[3];
+    if (QARR || (ragged && t == T - 1)) {
+      for (int j = 0; j < 32; ++j) bsym_eval<true>(pi, sp[t * 32 + j], soft2, a, dummy);
+    } else {
+      for (int j = 0; j < 32; ++j) bsym_eval<false>(pi, sp[t * 32 + j], soft2, a, dummy);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c * npad + i] = a[c];
+  }
+  __syncthreads();
+  const int Tp = T + (T & 1);
+  for (int rho = 0; rho < Tp - 1; ++rho) {
+    for (int k = warp; k < Tp / 2; k += NW) {
+      int ta, tb;
+      round_pair(rho, k, Tp, ta, tb);
+      if (ta >= T || tb >= T) continue;  // the bye of an odd tile count
+      const BD4 pp = sp[ta * 32 + lane];
+      const BD4 *qt = sp + tb * 32;
+      double a[3] = {0.0, 0.0, 0.0}, b[3] = {0.0, 0.0, 0.0};
+      if (QARR || (ragged && (ta == T - 1 || tb == T - 1))) {
+#pragma unroll 2
+        for (int r = 0; r < 32; ++r) {
+          bsym_eval<true>(pp, qt[(lane + r) & 31], soft2, a, b);
+          b[0] = bshfl_next(b[0], lane);
+          b[1] = bshfl_next(b[1], lane);
+          b[2] = bshfl_next(b[2], lane);
+        }
+      } else {
+#pragma unroll 2
+        for (int r = 0; r < 32; ++r) {
+          bsym_eval<false>(pp, qt[(lane + r) & 31], soft2, a, b);
+          b[0] = bshfl_next(b[0], lane);
+          b[1] = bshfl_next(b[1], lane);
+          b[2] = bshfl_next(b[2], lane);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[c * npad + ta * 32 + lane] += a[c];
+        acc[c * npad + tb * 32 + lane] += b[c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ void bnormals3(unsigned long long seed, unsigned instance, int64_t step,
                                           int64_t ion, double out[3]) {
   uint32_t c[4] = {(uint32_t)ion, (uint32_t)((uint64_t)step & 0xffffffffu),
@@ -117,12 +219,13 @@ __device__ __forceinline__ void bnormals3(unsigned long long seed, unsigned inst
   out[2] = m1 * c3;
 }
 
-template <bool QARR, bool DF>
-__global__ void __launch_bounds__(512) k_batched(Phys p, StateView s,
+template <bool QARR, bool DF, bool SYM>
+__global__ void __launch_bounds__(512, 1) k_batched(Phys p, StateView s,
                                                   const __grid_constant__ BatchSched sch,
-                                                  int64_t step0, int64_t nsteps, unsigned *err) {
+                                                  int64_t step0, int64_t nsteps, int npad, unsigned *err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BD4 *sp = reinterpret_cast<BD4 *>(smem_raw);
+  double *acc = reinterpret_cast<double *>(sp + npad);  // SYM: [3][npad]
   const int T = blockDim.x;
   const int tid = threadIdx.x;
   const double dt = p.dt, hdt2 = 0.5 * dt * dt;
@@ -139,10 +242,13 @@ __global__ void __launch_bounds__(512) k_batched(Phys p, StateView s,
     const int n = sch.off[inst + 1] - sch.off[inst];
     const unsigned inst_id = p.instance + (unsigned)inst;
     __syncthreads();  // the previous instance is done with shared memory
+    const int np32 = (n + 31) & ~31;
+    if (SYM)
+      for (int i = n + tid; i < np32; i += T) sp[i] = BD4{1e18, 1e18, 1e18, 0.0};  // weight-0 dummies
     for (int i = tid; i < n; i += T) {
       BD4 r;
       r.x = s.x[i0 + i]; r.y = s.y[i0 + i]; r.z = s.z[i0 + i];
-      r.w = QARR ? s.q[i0 + i] : 0.0;
+      r.w = QARR ? s.q[i0 + i] : 1.0;
       if (DF && QARR) {  // q as an FP32 (hi, lo) pair for the double-float pair term
         float qh, ql;
         split_f64(s.q[i0 + i], qh, ql);
@@ -164,11 +270,18 @@ __global__ void __launch_bounds__(512) k_batched(Phys p, StateView s,
       }
       __syncthreads();
       // forces at r+ and the kick
+      if (SYM) bsym_forces<QARR>(sp, acc, npad, n, np32, p.soft2);
       for (int ib = 0; ib < n; ib += T) {
         const int i = ib + tid;
         const BD4 ri = sp[min(i, n - 1)];
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        if (DF) {
+        if (SYM) {
+          if (i < n) {
+            a0 = acc[i];
+            a1 = acc[npad + i];
+            a2 = acc[2 * npad + i];
+          }
+        } else if (DF) {
           float ah[3] = {0.0f, 0.0f, 0.0f}, al[3] = {0.0f, 0.0f, 0.0f};
           for (int j0 = 0; j0 < n; j0 += 256) {  // double-float sums flushed every 256 partners
             const int j1 = min(n, j0 + 256);
@@ -249,7 +362,7 @@ int batched_plan(int n_inst, const int64_t *offsets, int n_bins, unsigned short 
 }
 
 cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const int64_t *offsets,
-                           int n_bins, int threads, int64_t step0, int64_t nsteps, unsigned *err,
+                           int n_bins, int threads, bool allow_sym, int64_t step0, int64_t nsteps, unsigned *err,
                            cudaStream_t st) {
   BatchSched sch;
   sch.n_inst = n_inst;
@@ -258,9 +371,15 @@ cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const 
   for (int k = 0; k <= n_inst; ++k) sch.off[k] = (int)offsets[k];
   for (int k = 0; k < n_inst; ++k) maxn = std::max(maxn, (int)(offsets[k + 1] - offsets[k]));
   batched_plan(n_inst, offsets, n_bins, sch.order, sch.bin_start, nullptr, nullptr);
+  // fp64 instances of at most BATCH_SYM_N ions use the half-pair force phase,
+  // which adds the [3][npad] FP64 accumulators to the positions in shared memory.
+  const bool df = p.precision == MODE_DF64;
+  const bool sym = allow_sym && !df && maxn <= BATCH_SYM_N;
+  const int npad = (std::max(maxn, 1) + 31) & ~31;
+  const size_t need = sym ? (size_t)npad * (sizeof(BD4) + 3 * sizeof(double)) : (size_t)std::max(maxn, 1) * sizeof(BD4);
   // At least 120 KB of shared memory per CTA, so no SM holds two bins: each
   // bin then owns one SM, which is what the LPT packing assumes.
-  const size_t smem = std::max((size_t)std::max(maxn, 1) * sizeof(BD4), (size_t)120 * 1024);
+  const size_t smem = std::max(need, (size_t)120 * 1024);
   static std::mutex mu;
   static bool attr_done[64] = {false};
   int dev = 0;
@@ -270,27 +389,28 @@ cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const 
     std::lock_guard<std::mutex> lk(mu);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_done[dev]) {
-      const int lim = 200 * 1024;
-      e = cudaFuncSetAttribute(k_batched<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_batched<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_batched<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_batched<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      const int lim = 227 * 1024;
+      const void *fns[6] = {(const void *)k_batched<true, false, false>, (const void *)k_batched<false, false, false>,
+                            (const void *)k_batched<true, true, false>,  (const void *)k_batched<false, true, false>,
+                            (const void *)k_batched<true, false, true>,  (const void *)k_batched<false, false, true>};
+      for (int f = 0; f < 6 && e == cudaSuccess; ++f)
+        e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e != cudaSuccess) return e;
       attr_done[dev] = true;
     }
   }
-  const bool df = p.precision == MODE_DF64;
-  if (s.q && df)
-    k_batched<true, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
+  if (sym && s.q)
+    k_batched<true, false, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+  else if (sym)
+    k_batched<false, false, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+  else if (s.q && df)
+    k_batched<true, true, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
   else if (s.q)
-    k_batched<true, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
+    k_batched<true, false, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
   else if (df)
-    k_batched<false, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
+    k_batched<false, true, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
   else
-    k_batched<false, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, err);
+    k_batched<false, false, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
   return cudaGetLastError();
 }
 

@@ -177,3 +177,36 @@ def test_full_ensemble_sampled(nb, orc, precision):
         fp, fv = contract_floor(ref, nsteps, phys["dt"])
         assert dv <= 10 * sv + fv
         assert dp <= 10 * sp + fp
+
+
+@pytest.mark.parametrize("charges", [False, True])
+def test_batched_symmetric_phase_matches_one_sided(nb, charges):
+    """The half-pair force phase (fp64 instances of at most 4096 ions: a
+    round-robin schedule of 32-ion tile pairs, odd tile counts with a bye, a
+    4096-ion instance at the shared-memory limit) against the one-sided phase
+    (tuning R = 0), one step and ten steps."""
+    sizes = [1, 31, 33, 65, 200, 4096]
+    off, pos, vel, phys = small_ensemble(sizes, seed=12)
+    pos = pos + 1e-7 * np.random.default_rng(3).standard_normal(pos.shape)  # off the axis
+    q = W.E_CHARGE * np.random.default_rng(4).choice([1.0, 2.0], size=pos.shape[1]) if charges else None
+    par = nb.Params.from_phys(phys)
+
+    def run(nsteps, one_sided):
+        if one_sided:
+            nb.set_tuning("ensemble", "fp64", 0, 1 << 40, 256, R=0)
+        try:
+            sysm = nb.System(pos, vel, q=q)
+            nb.init_batched(par, sysm, off)
+            nb.step_batched(par, sysm, off, nsteps)
+            nb.sync_status()
+        finally:
+            nb.set_tuning("ensemble", "fp64", 0, 0, 0)
+        return sysm
+
+    a1, b1 = run(1, False), run(1, True)
+    acc_a, acc_b = a1.acc().cpu().numpy(), b1.acc().cpu().numpy()
+    assert not np.array_equal(acc_a, acc_b)  # genuinely the other phase
+    assert np.max(np.abs(acc_a - acc_b)) <= 1e-12 * np.max(np.abs(acc_b))
+    a10, b10 = run(10, False), run(10, True)
+    scale = np.max(np.abs(pos))
+    assert np.max(np.abs(a10.pos().cpu().numpy() - b10.pos().cpu().numpy())) <= 1e-12 * scale
