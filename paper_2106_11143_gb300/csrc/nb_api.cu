@@ -419,8 +419,7 @@ nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t
   cudaStream_t st = (cudaStream_t)stream;
   Arena *a = nullptr;
   NB_TRY(get_arena(st, 256, &a));
-  // fastest on GB300: 512 threads for the half-pair fp64 phase, 256 for df64
-  int threads = params->precision == NB_DF64 ? 256 : 512, R = 1, bps = 1;
+  int threads = 512, R = 1, bps = 1;  // fastest on GB300 with the half-pair phase
   tuning_lookup(3, params->precision, packed->n, &threads, &R, &bps);
   const int n_bins = std::min(n_inst, device_sm_count());
   // a tuning entry with R = 0 keeps the one-sided force phase

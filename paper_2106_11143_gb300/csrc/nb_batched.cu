@@ -18,8 +18,8 @@
 // kernel by value (__grid_constant__), so a launch needs no host-to-device
 // copy and can be captured in a CUDA graph.
 //
-// fp64 instances of at most 4096 ions use a half-pair force phase
-// (bsym_forces below); larger instances and df64 use the one-sided phase.
+// Instances of at most 4096 ions use a half-pair force phase (bsym_forces
+// below); larger instances use the one-sided phase.
 // Either way the arithmetic of an ion depends only on its instance (a fixed
 // pair order and accumulation order per ion), not on the schedule or the block
 // size, so results are bitwise reproducible.
@@ -103,7 +103,7 @@ __device__ __forceinline__ void bphilox(uint32_t c[4], uint32_t k0, uint32_t k1)
 }
 
 // ---------------------------------------------------------------------------
-// Half-pair (Newton's third law) force phase for fp64 instances of at most
+// Half-pair (Newton's third law) force phase for instances of at most
 // BATCH_SYM_N ions.  The instance is padded to whole 32-ion tiles with
 // weight-0 dummies far away; the per-ion sums go to FP64 accumulators in
 // shared memory.  A diagonal phase evaluates each tile against itself
@@ -134,6 +134,47 @@ __device__ __forceinline__ void bsym_eval(const BD4 &p, const BD4 &q, double sof
   b[2] = fma(-dz, sq, b[2]);
 }
 
+// The double-float pair term for both ions (df64): P side (ah, al) += w_q d s,
+// Q side (bh, bl) -= w_p d s, with the weights as FP32 (hi, lo) pairs in w.
+__device__ __forceinline__ void df_scale(float sh, float sl, double w, float &oh, float &ol) {
+  const float2 q = *reinterpret_cast<const float2 *>(&w);
+  oh = sh * q.x;
+  ol = fmaf(sh, q.y, fmaf(sl, q.x, fmaf(sh, q.x, -oh)));
+}
+
+template <bool W>
+__device__ __forceinline__ void bsym_eval_df64(const BD4 &p, const BD4 &q, float s2h, float s2l,
+                                               float ah[3], float al[3], float bh[3], float bl[3]) {
+  float dh[3], dl[3];
+  split_f64(p.x - q.x, dh[0], dl[0]);
+  split_f64(p.y - q.y, dh[1], dl[1]);
+  split_f64(p.z - q.z, dh[2], dl[2]);
+  float sh, sl;
+  df_rinv3(dh, dl, s2h, s2l, sh, sl);
+  float sah = sh, sal = sl, sbh = sh, sbl = sl;
+  if (W) {
+    df_scale(sh, sl, q.w, sah, sal);
+    df_scale(sh, sl, p.w, sbh, sbl);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float ph = dh[k] * sah;
+    const float pl = fmaf(dh[k], sal, fmaf(dl[k], sah, fmaf(dh[k], sah, -ph)));
+    float u, t;
+    two_sum_f(ah[k], ph, u, t);
+    ah[k] = u;
+    al[k] += t + pl;
+    float qh = ph, ql = pl;
+    if (W) {
+      qh = dh[k] * sbh;
+      ql = fmaf(dh[k], sbl, fmaf(dl[k], sbh, fmaf(dh[k], sbh, -qh)));
+    }
+    two_sum_f(bh[k], -qh, u, t);
+    bh[k] = u;
+    bl[k] += t - ql;
+  }
+}
+
 // Tiles (a, b) of round rho, pair k, for Tp tiles (circle method).
 __device__ __forceinline__ void round_pair(int rho, int k, int Tp, int &a, int &b) {
   if (k == 0) {
@@ -146,9 +187,42 @@ __device__ __forceinline__ void round_pair(int rho, int k, int Tp, int &a, int &
 }
 
 // The force phase: acc[c * npad + i] = sum_j w_j (r_i - r_j) / |r_i - r_j|^3
-// for the instance's np32 staged entries (n real ions, weights in w).
-template <bool QARR>
-__device__ void bsym_forces(const BD4 *sp, double *acc, int npad, int n, int np32, double soft2) {
+// for the instance's np32 staged entries (n real ions, weights in w: an FP64
+// value for fp64, an FP32 (hi, lo) pair for df64).
+template <bool W, bool DF>
+__device__ __forceinline__ void bsym_tile_pair(const BD4 &pp, const BD4 *qt, int lane, double soft2,
+                                               float s2h, float s2l, double a[3], double b[3]) {
+  if (DF) {
+    float ah[3] = {0, 0, 0}, al[3] = {0, 0, 0}, bh[3] = {0, 0, 0}, bl[3] = {0, 0, 0};
+#pragma unroll 2
+    for (int r = 0; r < 32; ++r) {
+      bsym_eval_df64<W>(pp, qt[(lane + r) & 31], s2h, s2l, ah, al, bh, bl);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        bh[c] = __shfl_sync(0xffffffffu, bh[c], (lane + 1) & 31);
+        bl[c] = __shfl_sync(0xffffffffu, bl[c], (lane + 1) & 31);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a[c] = f32_to_f64(ah[c]) + f32_to_f64(al[c]);
+      b[c] = f32_to_f64(bh[c]) + f32_to_f64(bl[c]);
+    }
+  } else {
+    a[0] = a[1] = a[2] = b[0] = b[1] = b[2] = 0.0;
+#pragma unroll 2
+    for (int r = 0; r < 32; ++r) {
+      bsym_eval<W>(pp, qt[(lane + r) & 31], soft2, a, b);
+      b[0] = bshfl_next(b[0], lane);
+      b[1] = bshfl_next(b[1], lane);
+      b[2] = bshfl_next(b[2], lane);
+    }
+  }
+}
+
+template <bool QARR, bool DF>
+__device__ void bsym_forces(const BD4 *sp, double *acc, int npad, int n, int np32, double soft2,
+                            float s2h, float s2l) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
   const int T = np32 >> 5;
   const bool ragged = (n & 31) != 0;
@@ -156,11 +230,26 @@ __device__ void bsym_forces(const BD4 *sp, double *acc, int npad, int n, int np3
   for (int t = warp; t < T; t += NW) {
     const int i = t * 32 + lane;
     const BD4 pi = sp[i];
-    double a[3] = {0.0, 0.0, 0.0}, dummy[3];
-    if (QARR || (ragged && t == T - 1)) {
-      for (int j = 0; j < 32; ++j) bsym_eval<true>(pi, sp[t * 32 + j], soft2, a, dummy);
+    double a[3] = {0.0, 0.0, 0.0};
+    const bool w = QARR || (ragged && t == T - 1);
+    if (DF) {
+      float ah[3] = {0, 0, 0}, al[3] = {0, 0, 0}, bh[3], bl[3];
+      for (int j = 0; j < 32; ++j) {
+        bh[0] = bh[1] = bh[2] = bl[0] = bl[1] = bl[2] = 0.0f;  // the partner side is not used
+        if (w)
+          bsym_eval_df64<true>(pi, sp[t * 32 + j], s2h, s2l, ah, al, bh, bl);
+        else
+          bsym_eval_df64<false>(pi, sp[t * 32 + j], s2h, s2l, ah, al, bh, bl);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a[c] = f32_to_f64(ah[c]) + f32_to_f64(al[c]);
     } else {
-      for (int j = 0; j < 32; ++j) bsym_eval<false>(pi, sp[t * 32 + j], soft2, a, dummy);
+      double dummy[3];
+      if (w) {
+        for (int j = 0; j < 32; ++j) bsym_eval<true>(pi, sp[t * 32 + j], soft2, a, dummy);
+      } else {
+        for (int j = 0; j < 32; ++j) bsym_eval<false>(pi, sp[t * 32 + j], soft2, a, dummy);
+      }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[c * npad + i] = a[c];
@@ -174,24 +263,11 @@ __device__ void bsym_forces(const BD4 *sp, double *acc, int npad, int n, int np3
       if (ta >= T || tb >= T) continue;  // the bye of an odd tile count
       const BD4 pp = sp[ta * 32 + lane];
       const BD4 *qt = sp + tb * 32;
-      double a[3] = {0.0, 0.0, 0.0}, b[3] = {0.0, 0.0, 0.0};
-      if (QARR || (ragged && (ta == T - 1 || tb == T - 1))) {
-#pragma unroll 2
-        for (int r = 0; r < 32; ++r) {
-          bsym_eval<true>(pp, qt[(lane + r) & 31], soft2, a, b);
-          b[0] = bshfl_next(b[0], lane);
-          b[1] = bshfl_next(b[1], lane);
-          b[2] = bshfl_next(b[2], lane);
-        }
-      } else {
-#pragma unroll 2
-        for (int r = 0; r < 32; ++r) {
-          bsym_eval<false>(pp, qt[(lane + r) & 31], soft2, a, b);
-          b[0] = bshfl_next(b[0], lane);
-          b[1] = bshfl_next(b[1], lane);
-          b[2] = bshfl_next(b[2], lane);
-        }
-      }
+      double a[3], b[3];
+      if (QARR || (ragged && (ta == T - 1 || tb == T - 1)))
+        bsym_tile_pair<true, DF>(pp, qt, lane, soft2, s2h, s2l, a, b);
+      else
+        bsym_tile_pair<false, DF>(pp, qt, lane, soft2, s2h, s2l, a, b);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         acc[c * npad + ta * 32 + lane] += a[c];
@@ -253,6 +329,8 @@ __global__ void __launch_bounds__(512, 1) k_batched(Phys p, StateView s,
         float qh, ql;
         split_f64(s.q[i0 + i], qh, ql);
         *reinterpret_cast<float2 *>(&r.w) = make_float2(qh, ql);
+      } else if (DF) {
+        *reinterpret_cast<float2 *>(&r.w) = make_float2(1.0f, 0.0f);
       }
       sp[i] = r;
     }
@@ -270,7 +348,7 @@ __global__ void __launch_bounds__(512, 1) k_batched(Phys p, StateView s,
       }
       __syncthreads();
       // forces at r+ and the kick
-      if (SYM) bsym_forces<QARR>(sp, acc, npad, n, np32, p.soft2);
+      if (SYM) bsym_forces<QARR, DF>(sp, acc, npad, n, np32, p.soft2, s2h, s2l);
       for (int ib = 0; ib < n; ib += T) {
         const int i = ib + tid;
         const BD4 ri = sp[min(i, n - 1)];
@@ -371,10 +449,10 @@ cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const 
   for (int k = 0; k <= n_inst; ++k) sch.off[k] = (int)offsets[k];
   for (int k = 0; k < n_inst; ++k) maxn = std::max(maxn, (int)(offsets[k + 1] - offsets[k]));
   batched_plan(n_inst, offsets, n_bins, sch.order, sch.bin_start, nullptr, nullptr);
-  // fp64 instances of at most BATCH_SYM_N ions use the half-pair force phase,
+  // Instances of at most BATCH_SYM_N ions use the half-pair force phase,
   // which adds the [3][npad] FP64 accumulators to the positions in shared memory.
   const bool df = p.precision == MODE_DF64;
-  const bool sym = allow_sym && !df && maxn <= BATCH_SYM_N;
+  const bool sym = allow_sym && maxn <= BATCH_SYM_N;
   const int npad = (std::max(maxn, 1) + 31) & ~31;
   const size_t need = sym ? (size_t)npad * (sizeof(BD4) + 3 * sizeof(double)) : (size_t)std::max(maxn, 1) * sizeof(BD4);
   // At least 120 KB of shared memory per CTA, so no SM holds two bins: each
@@ -390,16 +468,21 @@ cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const 
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_done[dev]) {
       const int lim = 227 * 1024;
-      const void *fns[6] = {(const void *)k_batched<true, false, false>, (const void *)k_batched<false, false, false>,
+      const void *fns[8] = {(const void *)k_batched<true, false, false>, (const void *)k_batched<false, false, false>,
                             (const void *)k_batched<true, true, false>,  (const void *)k_batched<false, true, false>,
-                            (const void *)k_batched<true, false, true>,  (const void *)k_batched<false, false, true>};
-      for (int f = 0; f < 6 && e == cudaSuccess; ++f)
+                            (const void *)k_batched<true, false, true>,  (const void *)k_batched<false, false, true>,
+                            (const void *)k_batched<true, true, true>,   (const void *)k_batched<false, true, true>};
+      for (int f = 0; f < 8 && e == cudaSuccess; ++f)
         e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e != cudaSuccess) return e;
       attr_done[dev] = true;
     }
   }
-  if (sym && s.q)
+  if (sym && s.q && df)
+    k_batched<true, true, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+  else if (sym && df)
+    k_batched<false, true, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+  else if (sym && s.q)
     k_batched<true, false, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
   else if (sym)
     k_batched<false, false, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);

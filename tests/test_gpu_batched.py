@@ -179,9 +179,10 @@ def test_full_ensemble_sampled(nb, orc, precision):
         assert dp <= 10 * sp + fp
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
 @pytest.mark.parametrize("charges", [False, True])
-def test_batched_symmetric_phase_matches_one_sided(nb, charges):
-    """The half-pair force phase (fp64 instances of at most 4096 ions: a
+def test_batched_symmetric_phase_matches_one_sided(nb, charges, precision):
+    """The half-pair force phase (instances of at most 4096 ions: a
     round-robin schedule of 32-ion tile pairs, odd tile counts with a bye, a
     4096-ion instance at the shared-memory limit) against the one-sided phase
     (tuning R = 0), one step and ten steps."""
@@ -189,11 +190,11 @@ def test_batched_symmetric_phase_matches_one_sided(nb, charges):
     off, pos, vel, phys = small_ensemble(sizes, seed=12)
     pos = pos + 1e-7 * np.random.default_rng(3).standard_normal(pos.shape)  # off the axis
     q = W.E_CHARGE * np.random.default_rng(4).choice([1.0, 2.0], size=pos.shape[1]) if charges else None
-    par = nb.Params.from_phys(phys)
+    par = nb.Params.from_phys(phys, precision=precision)
 
     def run(nsteps, one_sided):
         if one_sided:
-            nb.set_tuning("ensemble", "fp64", 0, 1 << 40, 256, R=0)
+            nb.set_tuning("ensemble", precision, 0, 1 << 40, 256, R=0)
         try:
             sysm = nb.System(pos, vel, q=q)
             nb.init_batched(par, sysm, off)
