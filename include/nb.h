@@ -221,8 +221,8 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
  * keep its one-sided force phase (by default fp64 ensembles whose instances
  * all have at most 4096 ions use the half-pair phase).  For kind 4
  * (the symmetric half-pair force kernel of the four force precisions): `block` ions
- * per block pair unit (256, 512, 1024) and R = 1 to use it or 0 to disable
- * it for that n range (by default it is used from n = 16384).  For kind 5
+ * per block pair unit (128, 256, 512, 1024) and R = 1 to use it or 0 to disable
+ * it for that n range (by default it is used from n = 4096).  For kind 5
  * (the symmetric VJP kernel; `precision` NB_FP64): `block` ions per block
  * pair unit (128 or 256) and R = 1 / 0 to use / disable it (by default it is
  * used from n = 4096).  The latest

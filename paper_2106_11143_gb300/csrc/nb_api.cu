@@ -453,8 +453,8 @@ nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n
   if (precision < NB_FP64 || precision > NB_FP64_RSQ_NR2) return fail(NB_EINVAL, "bad precision");
   if (n_lo < 0 || n_hi < n_lo) return fail(NB_EINVAL, "bad n range");
   if (kind == 4) {
-    if (block != 256 && block != 512 && block != 1024)
-      return fail(NB_EINVAL, "symmetric block must be 256, 512 or 1024 ions");
+    if (block != 128 && block != 256 && block != 512 && block != 1024)
+      return fail(NB_EINVAL, "symmetric block must be 128, 256, 512 or 1024 ions");
     if (R != 0 && R != 1) return fail(NB_EINVAL, "R must be 1 (use) or 0 (disable)");
   } else if (kind == 5) {
     if (block != 128 && block != 256) return fail(NB_EINVAL, "symmetric VJP block must be 128 or 256 ions");

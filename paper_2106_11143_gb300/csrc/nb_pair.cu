@@ -527,13 +527,19 @@ static double sym_partial_cap() {
 
 Plan make_plan(int64_t n, int mode, int kind) {
   Plan pl;
-  // Symmetric half-pair kernel for the force paths from n = 16384 on, while
-  // the per-partner-block partials (nbk * 3n doubles) fit the cap above.  Block
-  // sizes: the fastest measured on GB300 (split: 512 ions, whose two-ion-per-
-  // lane P-tiles need G >= 16).
+  // Symmetric half-pair kernel for the force paths from n = 4096 on, while
+  // the per-partner-block partials (nbk * 3n doubles) fit the cap above.
+  // Block sizes, the fastest measured on GB300 counting the epilogue's reads
+  // of the partials: 128-ion blocks (4 warps) up to n = 32768 (split: 10000),
+  // then 256, and 512 from n = 60000; split uses 512-ion blocks with two
+  // P-ions per lane from n = 10000.
   if (kind == 0 && (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || mode == MODE_SPLIT)) {
-    int G = (n >= 60000 || mode == MODE_SPLIT) ? 16 : 8;
-    bool use = n >= 16384;
+    int G;
+    if (mode == MODE_SPLIT)
+      G = n >= 10000 ? 16 : 4;
+    else
+      G = n >= 60000 ? 16 : (n >= 32768 ? 8 : 4);
+    bool use = n >= 4096;
     int tb = 0, tr = 0, tbps = 0;
     if (tuning_lookup(4, mode, n, &tb, &tr, &tbps)) {
       use = tr != 0;

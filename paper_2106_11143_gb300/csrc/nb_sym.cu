@@ -35,8 +35,11 @@
 
 namespace nb {
 
+// 256 threads (8 warps) per item; 128 (4 warps) for 128-ion blocks (G = 4),
+// which give enough items to fill the GPU from n = 4096.  The staggered
+// schedule needs at least as many P-tiles as warps.
 constexpr int SYM_THREADS = 256;
-constexpr int SYM_W = SYM_THREADS / 32;
+constexpr int SYM_THREADS_SMALL = 128;
 constexpr double SYM_FAR = 1e18;
 
 struct __align__(16) SD4 {
@@ -226,7 +229,7 @@ __device__ __forceinline__ void sym_step_split2(const float4 &h1, const float4 &
 // the G/2 P-tiles outnumber the warps): warp w takes the Q-tiles qs = w,
 // w + 8, ...; at step k it holds P-tile (qs + k) mod G/2, distinct across
 // warps because all warps advance in lockstep through the barriers.
-template <bool W>
+template <bool W, int NW>
 __device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, const SD4 *posQ, double *accP,
                                                    int G, int BI, double soft2, int64_t n, int P,
                                                    int64_t q0, int nq, double *part) {
@@ -234,7 +237,7 @@ __device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, const SD4 *p
   const int GP = G >> 1;
   const float4 *fP = reinterpret_cast<const float4 *>(posP);
   const float4 *fQ = reinterpret_cast<const float4 *>(posQ);
-  for (int qs = warp; qs < G; qs += SYM_W) {
+  for (int qs = warp; qs < G; qs += NW) {
     double aq[3] = {0.0, 0.0, 0.0};
     const float4 *qhi = fQ + qs * 64 + lane, *qlo = fQ + 2 * BI + qs * 64 + lane;
     for (int k = 0; k < GP; ++k) {
@@ -258,12 +261,12 @@ __device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, const SD4 *p
   }
 }
 
-template <int MODE, bool W>
+template <int MODE, bool W, int NW>
 __device__ __forceinline__ void sym_offdiag(const SD4 *posP, const SD4 *posQ, double *accP, int G,
                                             int BI, double soft2, float s2h, float s2l, int64_t n,
                                             int P, int64_t q0, int nq, double *part) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int qs = warp; qs < G; qs += SYM_W) {
+  for (int qs = warp; qs < G; qs += NW) {
     const SD4 qh = posQ[qs * 32 + lane];
     double aq[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < G; ++k) {
@@ -350,8 +353,8 @@ __device__ __forceinline__ void sym_stage(SD4 *dst, int i, int BI, int64_t g, in
   dst[i] = e;
 }
 
-template <int MODE, bool QARR, bool P2>
-__global__ void __launch_bounds__(SYM_THREADS, MODE == MODE_FP64 ? 2 : 0) k_pair_sym(int64_t n, int nbk, int G,
+template <int MODE, bool QARR, bool P2, int NT>
+__global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ y,
                                                          const double *__restrict__ z,
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(SYM_THREADS, MODE == MODE_FP64 ? 2 : 0) k_pair
   const int64_t p0 = (int64_t)P * BI, q0 = (int64_t)Q * BI;
   const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
   const int tid = threadIdx.x;
-  for (int i = tid; i < BI; i += SYM_THREADS) {
+  for (int i = tid; i < BI; i += NT) {
     sym_stage<MODE, QARR>(posP, i, BI, p0 + i, n, x, y, z, q, pf, false);
     if (P != Q) sym_stage<MODE, QARR>(posQ, i, BI, q0 + i, n, x, y, z, q, pf, true);
     accP[i] = 0.0;
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__(SYM_THREADS, MODE == MODE_FP64 ? 2 : 0) k_pair
   __syncthreads();
 
   if (P == Q) {  // the block's own pairs, one-sided
-    for (int i = tid; i < np; i += SYM_THREADS) {
+    for (int i = tid; i < np; i += NT) {
       const SD4 pi = posP[i];
       double a[3] = {0.0, 0.0, 0.0};
       if (MODE == MODE_MIXED || MODE == MODE_SPLIT) {
@@ -475,16 +478,16 @@ __global__ void __launch_bounds__(SYM_THREADS, MODE == MODE_FP64 ? 2 : 0) k_pair
   const bool weighted = QARR || np < BI || nq < BI;
   if (P2) {
     if (weighted)
-      sym_offdiag_split2<true>(posP, posQ, accP, G, BI, soft2, n, P, q0, nq, part);
+      sym_offdiag_split2<true, NT / 32>(posP, posQ, accP, G, BI, soft2, n, P, q0, nq, part);
     else
-      sym_offdiag_split2<false>(posP, posQ, accP, G, BI, soft2, n, P, q0, nq, part);
+      sym_offdiag_split2<false, NT / 32>(posP, posQ, accP, G, BI, soft2, n, P, q0, nq, part);
   } else if (weighted) {
-    sym_offdiag<MODE, true>(posP, posQ, accP, G, BI, soft2, s2h, s2l, n, P, q0, nq, part);
+    sym_offdiag<MODE, true, NT / 32>(posP, posQ, accP, G, BI, soft2, s2h, s2l, n, P, q0, nq, part);
   } else {
-    sym_offdiag<MODE, false>(posP, posQ, accP, G, BI, soft2, s2h, s2l, n, P, q0, nq, part);
+    sym_offdiag<MODE, false, NT / 32>(posP, posQ, accP, G, BI, soft2, s2h, s2l, n, P, q0, nq, part);
   }
   __syncthreads();
-  for (int i = tid; i < np; i += SYM_THREADS)
+  for (int i = tid; i < np; i += NT)
 #pragma unroll
     for (int c = 0; c < 3; ++c) part[((int64_t)Q * 3 + c) * n + p0 + i] = accP[c * BI + i];
 }
@@ -493,7 +496,7 @@ size_t sym_smem_bytes(int G, int mode) {
   return (size_t)32 * G * ((mode == MODE_SPLIT ? 3 : 2) * sizeof(SD4) + 3 * sizeof(double));
 }
 
-template <int MODE, bool P2>
+template <int MODE, bool P2, int NT>
 static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, const double *y,
                                 const double *z, const double *q, const PosF32 &pf, double soft2,
                                 double *part, cudaStream_t st) {
@@ -507,9 +510,9 @@ static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, cons
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!done[dev]) {
       const int lim = (int)sym_smem_bytes(32, MODE);
-      e = cudaFuncSetAttribute(k_pair_sym<MODE, true, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      e = cudaFuncSetAttribute(k_pair_sym<MODE, true, P2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pair_sym<MODE, false, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_pair_sym<MODE, false, P2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  lim);
       if (e != cudaSuccess) return e;
       done[dev] = true;
@@ -518,23 +521,32 @@ static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, cons
   const int items = nbk * (nbk + 1) / 2;
   const size_t smem = sym_smem_bytes(G, MODE);
   if (q)
-    k_pair_sym<MODE, true, P2><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
+    k_pair_sym<MODE, true, P2, NT><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
   else
-    k_pair_sym<MODE, false, P2><<<items, SYM_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
+    k_pair_sym<MODE, false, P2, NT><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
                             const double *z, const double *q, const PosF32 &pf, double soft2,
                             double *part, cudaStream_t st) {
-  if (G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
+  if (G != 4 && G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
+  constexpr int S = SYM_THREADS_SMALL, L = SYM_THREADS;
+  const bool small = G == 4;  // 4 warps for 128-ion blocks
   switch (mode) {
-    case MODE_FP64: return launch_sym_m<MODE_FP64, false>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
-    case MODE_DF64: return launch_sym_m<MODE_DF64, false>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
-    case MODE_MIXED: return launch_sym_m<MODE_MIXED, false>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
-    case MODE_SPLIT:  // 64-ion P-tiles once the G/2 P-tiles outnumber the warps
-      return G >= 2 * SYM_W ? launch_sym_m<MODE_SPLIT, true>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
-                            : launch_sym_m<MODE_SPLIT, false>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_FP64:
+      return small ? launch_sym_m<MODE_FP64, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
+                   : launch_sym_m<MODE_FP64, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_DF64:
+      return small ? launch_sym_m<MODE_DF64, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
+                   : launch_sym_m<MODE_DF64, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_MIXED:
+      return small ? launch_sym_m<MODE_MIXED, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
+                   : launch_sym_m<MODE_MIXED, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+    case MODE_SPLIT:  // 64-ion P-tiles once the G/2 P-tiles outnumber the 8 warps
+      if (small) return launch_sym_m<MODE_SPLIT, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+      return G >= 16 ? launch_sym_m<MODE_SPLIT, true, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
+                     : launch_sym_m<MODE_SPLIT, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -61,7 +61,7 @@ def speed(sizes=(1000, 10000, 100000), methods=METHODS, reps=3):
         sysm = api.System(pos, vel)
         row = {}
         runs = [(m, m, False) for m in methods]
-        runs += [(m + "_sym", m, True) for m in SYMMETRIC if m in methods and n >= 16384]
+        runs += [(m + "_sym", m, True) for m in SYMMETRIC if m in methods and n >= 4096]
         for name, m, sym in runs:
             par = api.Params.from_phys(W.phys(), precision=m)
             try:

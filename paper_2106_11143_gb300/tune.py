@@ -1,7 +1,9 @@
 """Autotuner for the launch shapes of the pair kernels and the ensemble kernel.
 
 For each (kernel, precision, n bucket) it times candidate shapes -- threads
-per block, ions per thread (R) and target (i-tile, j-chunk) blocks per SM --
+per block, ions per thread (R) and target (i-tile, j-chunk) blocks per SM for
+the one-sided force kernel; ions per block pair, or the one-sided kernel
+instead, for the symmetric force kernel --
 with the library's own CUDA-event timing of the pair-kernel launches
 (nb_timing_*), keeps the fastest, and installs it with nb_set_tuning.  The
 ensemble kernel is tuned over threads per block on a Kibble-Zurek-shaped
@@ -26,8 +28,9 @@ import torch
 from . import api
 from . import workloads as W
 
-# n buckets: (lo, hi, representative n)
-BUCKETS = [(1, 3000, 1024), (3001, 24000, 16384), (24001, 1 << 31, 100000)]
+# n buckets of the one-sided force kernel, the default below n = 4096:
+# (lo, hi, representative n)
+BUCKETS = [(1, 1500, 1024), (1501, 4095, 3000)]
 FORCE_SHAPES = [(b, r, bps) for b in (64, 128, 256) for r in (1, 2, 4) for bps in (4, 8, 16, 32)]
 SMALL_SHAPES = [(b, 1, bps) for b in (32, 64, 128) for bps in (8, 16, 32, 64)]
 
@@ -45,10 +48,11 @@ def _time_forces(par, sysm, reps):
 
 
 def tune_pair(precision, quick=False, log=print):
-    """Best (block, R, blocks_per_sm) per n bucket for the force kernel."""
+    """Best (block, R, blocks_per_sm) per n bucket for the one-sided force
+    kernel (the symmetric kernel is switched off while timing)."""
     out = []
     for lo, hi, n in BUCKETS:
-        if quick and n < 100000:
+        if quick and n < 3000:
             continue
         pos, vel = W.random_cloud(n, seed=1, semi_axes=(200e-6, 200e-6, 1000e-6))
         sysm = api.System(pos, vel)
@@ -59,8 +63,9 @@ def tune_pair(precision, quick=False, log=print):
         reps = 3 if (precision == "fp64" and n >= 100000) else 10
         best = None
         for (b, r, bps) in shapes:
-            if precision != "mixed_split" and r > 1 and n < 16384:
+            if precision != "mixed_split" and r > 1:
                 continue
+            api.set_tuning("symmetric", precision, lo, hi, 256, R=0)
             api.set_tuning("force", precision, lo, hi, b, r, bps)
             _time_forces(par, sysm, 1)  # warm-up with this shape
             t = _time_forces(par, sysm, reps)
@@ -71,6 +76,49 @@ def tune_pair(precision, quick=False, log=print):
         log("force %-11s n=%-7d best block=%d R=%d blocks/SM=%d  %.4f ms" % (precision, n, b, r, bps, t))
         out.append(dict(kind="force", precision=precision, n_lo=lo, n_hi=hi, block=b, R=r,
                         blocks_per_sm=bps, ms=t))
+    return out
+
+
+SYM_BUCKETS = [(4096, 10000, 8192), (10001, 40000, 16384), (40001, 1 << 31, 100000)]
+SYM_BLOCKS = (128, 256, 512, 1024)
+
+
+def _time_step(par, sysm, reps):
+    """Device time of one velocity-Verlet step (pair kernel and epilogue), ms."""
+    api.step(par, sysm, 1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    api.step(par, sysm, reps)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune_symmetric(precision, quick=False, log=print):
+    """Best ions per block pair of the symmetric force kernel, or the one-sided
+    kernel (R = 0), per n bucket, timed as whole steps so that the epilogue's
+    reads of the per-partner-block partials count."""
+    out = []
+    for lo, hi, n in SYM_BUCKETS:
+        if quick and n < 100000:
+            continue
+        pos, vel = W.random_cloud(n, seed=1, semi_axes=(200e-6, 200e-6, 1000e-6))
+        sysm = api.System(pos, vel)
+        par = api.Params.from_phys(W.phys(), precision=precision)
+        api.forces(par, sysm, total=True)
+        reps = 2 if (n >= 100000 and precision == "fp64") else 10
+        best = None
+        for block, use in [(b, 1) for b in SYM_BLOCKS] + [(256, 0)]:
+            api.set_tuning("symmetric", precision, lo, hi, block, R=use)
+            t = _time_step(par, sysm, reps)
+            if best is None or t < best[0]:
+                best = (t, block, use)
+        api.set_tuning("symmetric", precision, 0, 0, 0)
+        t, block, use = best
+        log("symmetric %-11s n=%-7d best %s  %.4f ms/step" % (precision, n, ("block=%d" % block) if use else "one-sided", t))
+        out.append(dict(kind="symmetric", precision=precision, n_lo=lo, n_hi=hi, block=block, R=use,
+                        blocks_per_sm=1, ms=t))
     return out
 
 
@@ -118,12 +166,13 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default="tune_cache.json")
     ap.add_argument("--quick", action="store_true")
-    ap.add_argument("--precisions", default="fp64,mixed,mixed_split")
+    ap.add_argument("--precisions", default="fp64,df64,mixed,mixed_split")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     entries = []
     for prec in a.precisions.split(","):
         entries += tune_pair(prec, quick=a.quick)
+        entries += tune_symmetric(prec, quick=a.quick)
     entries += tune_ensemble(quick=a.quick)
     json.dump({"device": torch.cuda.get_device_name(), "entries": entries}, open(a.out, "w"), indent=1)
     print("wrote", a.out)
