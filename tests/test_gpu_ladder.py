@@ -74,3 +74,12 @@ def test_ladder_speed_runs_every_method_one_sided(nb):
     assert row["sqrtdiv"]["speedup_vs_sqrtdiv_pct"] == 0.0
     # the half-pair kernel does about half the pair arithmetic
     assert row["fp64_sym"]["ms"] < 0.8 * row["fp64"]["ms"]
+
+
+def test_step_rate_sweep_runs(nb):
+    """The step-rate sweep (eager and CUDA-graph replays) on two small sizes."""
+    from paper_2106_11143_gb300 import sweep
+    rows = sweep.sweep(sizes=(10, 1000), precisions=["fp64", "mixed_split"])
+    assert len(rows) == 4
+    for r in rows:
+        assert r["ms_per_step"] > 0 and r["graph_ms_per_step"] > 0
