@@ -595,12 +595,17 @@ Plan make_plan(int64_t n, int mode, int kind) {
   // about 16 blocks per SM for large n; small n keeps at least 8 warps per SM
   const int64_t target = (int64_t)device_sm_count() * bps;
   int64_t njc = (target + pl.n_it - 1) / pl.n_it;
+  // j-chunks of at least one block of partners; for n < 256 (force kernel)
+  // down to 8 partners, so that enough warps share the pair work: a warp's
+  // FP64 instructions run one after another on a narrow per-SM FP64 unit.
+  // (At n = 1000 chunks that short were slower: too many tiny blocks.)
   const int64_t min_tiles = n >= 8192 ? 4 : 1;
-  const int64_t max_jc = std::max<int64_t>(1, n / (min_tiles * (int64_t)pl.block));
+  const int64_t min_chunk = (kind == 0 && n < 256) ? 8 : (int64_t)pl.block;
+  const int64_t max_jc = std::max<int64_t>(1, n / (min_tiles * min_chunk));
   njc = std::min<int64_t>(std::max<int64_t>(njc, 1), max_jc);
   int64_t chunk = (n + njc - 1) / njc;
-  chunk = ((chunk + pl.block - 1) / pl.block) * pl.block;
-  pl.jchunk = std::max<int64_t>(chunk, pl.block);
+  if (chunk >= pl.block) chunk = ((chunk + pl.block - 1) / pl.block) * pl.block;
+  pl.jchunk = std::max<int64_t>(chunk, min_chunk);
   pl.n_jc = round_up(n, pl.jchunk);
   return pl;
 }
