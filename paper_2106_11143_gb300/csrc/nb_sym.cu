@@ -545,6 +545,8 @@ cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x
                    : launch_sym_m<MODE_MIXED, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
     case MODE_SPLIT:  // 64-ion P-tiles once the G/2 P-tiles outnumber the 8 warps
       if (small) return launch_sym_m<MODE_SPLIT, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+      if (G == 32)  // 1024-ion blocks: 16 warps, so that the 16 P-tiles of 64 ions go round
+        return launch_sym_m<MODE_SPLIT, true, 512>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
       return G >= 16 ? launch_sym_m<MODE_SPLIT, true, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
                      : launch_sym_m<MODE_SPLIT, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
     default: return cudaErrorInvalidValue;
