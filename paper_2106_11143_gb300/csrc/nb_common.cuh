@@ -277,26 +277,50 @@ __device__ __forceinline__ double rinv1_fp64(double dx, double dy, double dz, do
   return em ? a : 0.0;
 }
 
-// r^-3 and r^-5 together for the pair VJP, as rinv3_fp64 does r^-3: the
-// double-float r^-5 = y^5 (1 + 5/2 e + 35/8 e^2) shares the seed, residual and
-// y^2 of r^-3.  Returns r^-3 in s3 and 3 r^-5 in s5x3 (the factor of the VJP's
-// second term, applied exactly in double-float before the widening), 0 for a
-// zero displacement without softening.
-__device__ __forceinline__ void rinv35_fp64(double dx, double dy, double dz, double soft2, double &s3,
-                                            double &s5x3) {
+// Double-float helpers for vjp_term_fp64: exact-product multiply and
+// TwoSum-based add of (hi, lo) pairs (relative error about 2^-44).
+__device__ __forceinline__ void dfmul(float ah, float al, float bh, float bl, float &h, float &l) {
+  h = ah * bh;
+  l = fmaf(ah, bl, fmaf(al, bh, fmaf(ah, bh, -h)));
+}
+__device__ __forceinline__ void dfadd(float ah, float al, float bh, float bl, float &h, float &l) {
+  float e;
+  two_sum_f(ah, bh, h, e);
+  l = e + (al + bl);
+}
+
+// The pair-force VJP term for one pair, T = dl r^-3 - 3 (d . dl) r^-5 d, with
+// d the FP64 displacement and dl the FP64 difference of the cotangents.  All
+// of it runs in double-float on the FP32 pipe: d is split with the scale
+// 2^-sc of rinv3_fp64 (its largest component, or sqrt(soft2), in [1, 2)), dl
+// with its own scale 2^-se; r^-3, 3 r^-5, the dot product and T are formed in
+// those scaled units, and each component of T is widened to FP64 with the
+// scale 2^(se - 3 sc) put back (one FP64 add per component).  Relative error
+// about 2^-44 of the larger of the two terms.  T = 0 when dl = 0 or when d = 0
+// without softening.
+__device__ __forceinline__ void vjp_term_fp64(double dx, double dy, double dz, double lx, double ly,
+                                              double lz, double soft2, double T[3]) {
   const int ex = (__double2hiint(dx) >> 20) & 0x7ff;
   const int ey = (__double2hiint(dy) >> 20) & 0x7ff;
   const int ez = (__double2hiint(dz) >> 20) & 0x7ff;
   const int e2 = (__double2hiint(soft2) >> 20) & 0x7ff;
-  const int es = e2 ? ((e2 - 1023) >> 1) + 1023 : 0;
-  const int em = max(max(ex, ey), max(ez, es));
+  const int es2 = e2 ? ((e2 - 1023) >> 1) + 1023 : 0;
+  const int em = max(max(ex, ey), max(ez, es2));
   const int sc = em - 1023;
-  float dh[3], dl[3], s2h = 0.0f, s2l = 0.0f;
+  const int fx = (__double2hiint(lx) >> 20) & 0x7ff;
+  const int fy = (__double2hiint(ly) >> 20) & 0x7ff;
+  const int fz = (__double2hiint(lz) >> 20) & 0x7ff;
+  const int fm = max(max(fx, fy), fz);
+  const int se = fm - 1023;
+  float dh[3], dl[3], eh[3], el[3], s2h = 0.0f, s2l = 0.0f;
   split_f64_scaled(dx, sc, dh[0], dl[0]);
   split_f64_scaled(dy, sc, dh[1], dl[1]);
   split_f64_scaled(dz, sc, dh[2], dl[2]);
+  split_f64_scaled(lx, se, eh[0], el[0]);
+  split_f64_scaled(ly, se, eh[1], el[1]);
+  split_f64_scaled(lz, se, eh[2], el[2]);
   if (e2) split_f64_scaled(soft2, 2 * sc, s2h, s2l);
-  // double-float r^2 = h + l from exact products (as in df_rinv3)
+  // double-float r^2, seed, compensated residual (as in df_rinv3)
   const float p0 = dh[0] * dh[0], p1 = dh[1] * dh[1], p2 = dh[2] * dh[2];
   const float q0 = fmaf(dh[0], dh[0], -p0), q1 = fmaf(dh[1], dh[1], -p1), q2 = fmaf(dh[2], dh[2], -p2);
   float h, t1, t2;
@@ -320,22 +344,36 @@ __device__ __forceinline__ void rinv35_fp64(double dx, double dy, double dz, dou
   r = fmaf(-l, y2, r);
   const float c3 = r * fmaf(r, 1.875f, 1.5f);
   const float c5 = r * fmaf(r, 4.375f, 2.5f);
-  // y^3 and y^5 as double-floats
   const float y3h = y2 * y;
   float y3e = fmaf(y2, y, -y3h);
   y3e = fmaf(y2e, y, y3e);
   const float y5h = y3h * y2;
   float y5e = fmaf(y3h, y2, -y5h);
   y5e = fmaf(y3h, y2e, fmaf(y3e, y2, y5e));
-  const float s3l = fmaf(y3h, c3, y3e);
-  const float s5l = fmaf(y5h, c5, y5e);
-  // 3 s5 exactly as a double-float: 3 y5h = m + me (TwoProd)
-  const float m = 3.0f * y5h;
-  const float me = fmaf(3.0f, y5h, -m) + 3.0f * s5l;
-  const double a3 = f32_to_f64_scaled(y3h, -3 * sc) + f32_to_f64_scaled(s3l, -3 * sc);
-  const double a5 = f32_to_f64_scaled(m, -5 * sc) + f32_to_f64_scaled(me, -5 * sc);
-  s3 = em ? a3 : 0.0;
-  s5x3 = em ? a5 : 0.0;
+  const float s3h = y3h, s3l = fmaf(y3h, c3, y3e);
+  const float s5h = y5h, s5l = fmaf(y5h, c5, y5e);
+  // dot = d . dl (scaled units)
+  float dth, dtl, ph, pl;
+  dfmul(dh[0], dl[0], eh[0], el[0], dth, dtl);
+  dfmul(dh[1], dl[1], eh[1], el[1], ph, pl);
+  dfadd(dth, dtl, ph, pl, dth, dtl);
+  dfmul(dh[2], dl[2], eh[2], el[2], ph, pl);
+  dfadd(dth, dtl, ph, pl, dth, dtl);
+  // w = 3 r^-5 dot
+  float wh, wl;
+  dfmul(dth, dtl, s5h, s5l, wh, wl);
+  const float w3h = 3.0f * wh;
+  const float w3l = fmaf(3.0f, wh, -w3h) + 3.0f * wl;
+  const int out = se - 3 * sc;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float uh, ul, vh, vl, th, tl;
+    dfmul(eh[k], el[k], s3h, s3l, uh, ul);
+    dfmul(dh[k], dl[k], w3h, w3l, vh, vl);
+    dfadd(uh, ul, -vh, -vl, th, tl);
+    const double t = f32_to_f64_scaled(th, out) + f32_to_f64_scaled(tl, out);
+    T[k] = (em && fm) ? t : 0.0;
+  }
 }
 
 // FP32 bulk shared by the two mixed modes: given the FP32 displacement,

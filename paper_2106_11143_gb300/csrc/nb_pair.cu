@@ -308,8 +308,8 @@ __global__ void __launch_bounds__(256) k_pair_phi(int64_t n, int64_t jchunk,
 // ---------------------------------------------------------------------------
 // VJP kernel (FP64): part[(jc*3+c)*n + i] =
 //   sum_{j in chunk} w_j [ dl^c / s^3 - 3 d^c (d . dl) / s^5 ],  dl = lam_i - lam_j.
-// FP64 for the differences, the dot product and the accumulation; s^-3 and
-// 3 s^-5 come from the FP32 pipe (rinv35_fp64).
+// FP64 for the differences and the accumulation; the term itself is formed
+// in double-float on the FP32 pipe and widened (vjp_term_fp64).
 template <bool QARR>
 __global__ void __launch_bounds__(256) k_pair_vjp(int64_t n, int64_t jchunk,
                                                   const double *__restrict__ x,
@@ -343,22 +343,17 @@ __global__ void __launch_bounds__(256) k_pair_vjp(int64_t n, int64_t jchunk,
     for (int k = 0; k < cnt; ++k) {
       const D4 pj = s4[2 * k];
       const D4 lj = s4[2 * k + 1];
-      const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-      double s3, s5x3;
-      rinv35_fp64(dx, dy, dz, soft2, s3, s5x3);
+      double T[3];
+      vjp_term_fp64(xi - pj.x, yi - pj.y, zi - pj.z, mi - lj.x, ni - lj.y, oi - lj.z, soft2, T);
       if (QARR) {
-        s3 *= pj.w;
-        s5x3 *= pj.w;
+        gx = fma(pj.w, T[0], gx);
+        gy = fma(pj.w, T[1], gy);
+        gz = fma(pj.w, T[2], gz);
+      } else {
+        gx += T[0];
+        gy += T[1];
+        gz += T[2];
       }
-      const double ex = mi - lj.x, ey = ni - lj.y, ez = oi - lj.z;
-      const double dot = fma(dx, ex, fma(dy, ey, dz * ez));
-      const double w3 = dot * s5x3;
-      gx = fma(ex, s3, gx);
-      gy = fma(ey, s3, gy);
-      gz = fma(ez, s3, gz);
-      gx = fma(-dx, w3, gx);
-      gy = fma(-dy, w3, gy);
-      gz = fma(-dz, w3, gz);
     }
   }
   if (i < n) {

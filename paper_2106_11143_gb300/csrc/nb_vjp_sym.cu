@@ -40,19 +40,18 @@ __device__ __forceinline__ double vshfl_next(double v, int lane) {
 template <bool W>
 __device__ __forceinline__ void vjp_eval(const VD8 &p, const VD8 &q, double soft2, double a[3],
                                          double b[3]) {
-  const double dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-  const double ex = p.lx - q.lx, ey = p.ly - q.ly, ez = p.lz - q.lz;
-  double s3, s5x3;
-  rinv35_fp64(dx, dy, dz, soft2, s3, s5x3);
-  const double w3 = fma(dx, ex, fma(dy, ey, dz * ez)) * s5x3;
-  const double sa = W ? s3 * q.w : s3, wa = W ? w3 * q.w : w3;
-  const double sb = W ? s3 * p.w : s3, wb = W ? w3 * p.w : w3;
-  a[0] = fma(-dx, wa, fma(ex, sa, a[0]));
-  a[1] = fma(-dy, wa, fma(ey, sa, a[1]));
-  a[2] = fma(-dz, wa, fma(ez, sa, a[2]));
-  b[0] = fma(dx, wb, fma(-ex, sb, b[0]));
-  b[1] = fma(dy, wb, fma(-ey, sb, b[1]));
-  b[2] = fma(dz, wb, fma(-ez, sb, b[2]));
+  double T[3];
+  vjp_term_fp64(p.x - q.x, p.y - q.y, p.z - q.z, p.lx - q.lx, p.ly - q.ly, p.lz - q.lz, soft2, T);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (W) {
+      a[c] = fma(q.w, T[c], a[c]);
+      b[c] = fma(-p.w, T[c], b[c]);
+    } else {
+      a[c] += T[c];
+      b[c] -= T[c];
+    }
+  }
 }
 
 // Staged entry i of a block (g = global index); ions past n are weight-0,
