@@ -211,3 +211,24 @@ def test_batched_symmetric_phase_matches_one_sided(nb, charges, precision):
     a10, b10 = run(10, False), run(10, True)
     scale = np.max(np.abs(pos))
     assert np.max(np.abs(a10.pos().cpu().numpy() - b10.pos().cpu().numpy())) <= 1e-12 * scale
+
+
+def test_batched_largest_instance(nb):
+    """An instance at the size limit (6144 ions: the one-sided force phase with
+    196 KB of positions in shared memory) beside small ones, against the
+    standalone system."""
+    sizes = [6144, 40, 5000]
+    off, pos, vel, phys = small_ensemble(sizes, seed=14)
+    pos = pos + 1e-7 * np.random.default_rng(5).standard_normal(pos.shape)
+    nsteps = 5
+    ens = run_gpu(nb, phys, off, pos, vel, nsteps)
+    for k in range(len(sizes)):
+        i0, i1 = off[k], off[k + 1]
+        single = nb.System(pos[:, i0:i1], vel[:, i0:i1])
+        par = nb.Params.from_phys(phys, instance=k)
+        nb.forces(par, single, total=True)
+        nb.step(par, single, nsteps)
+        nb.sync_status()
+        scale = np.max(np.abs(pos[:, i0:i1]))
+        d = np.max(np.abs(ens.pos()[:, i0:i1].cpu().numpy() - single.pos().cpu().numpy()))
+        assert d <= 1e-12 * scale, (k, d)

@@ -303,6 +303,27 @@ def test_full_size_sampled(nb, orc, precision):
     assert np.all(np.abs(g.sum(axis=1)) <= (1e-12 if precision in ("fp64", "df64") else 1e-6) * tot)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed_split"])
+def test_large_n_sampled(nb, orc, precision):
+    """N = 262151 (ragged): the symmetric kernel with about 4 GB of
+    per-partner-block partials (the scratch cap is a quarter of the device
+    memory); sampled ions against the oracle."""
+    n = 262151
+    pos, _ = W.random_cloud(n, seed=8, semi_axes=(300e-6, 300e-6, 1500e-6))
+    phys = W.phys()
+    g = gpu_forces(nb, phys, pos, precision=precision)
+    rng = np.random.default_rng(2)
+    idx = np.unique(np.concatenate([np.arange(0, 8), np.arange(n - 8, n), rng.integers(0, n, 32)]))
+    p = oparams(orc, phys)
+    errs = []
+    for i in idx:
+        ax, ay, az, _, absf = orc.coulomb(p, *pos, i0=int(i), i1=int(i) + 1, want_absf=True)
+        d = math.sqrt((g[0, i] - ax[0]) ** 2 + (g[1, i] - ay[0]) ** 2 + (g[2, i] - az[0]) ** 2)
+        errs.append(d / absf[0])
+    print("N=%d %s: max conditioned error %.3g" % (n, precision, max(errs)))
+    assert max(errs) <= TOL[precision]
+
+
 def test_argument_errors(nb):
     par = nb.Params.from_phys(W.phys())
     sysm = nb.System(np.zeros((3, 4)) + np.arange(4.0) * 1e-6)
