@@ -48,10 +48,16 @@ typedef enum {
 } nb_status;
 
 /* Arithmetic of the pair interaction (the O(N^2) inner loop).
- *  NB_FP64       -- FP64 throughout.  1/sqrt(r^2) is seeded by the FP32
- *                   hardware reciprocal square root (MUFU) and refined in
- *                   FP64 (Sec. IV: approximate 1/sqrt refined by
- *                   Newton-Raphson), result within a few ulp of FP64.
+ *  NB_FP64       -- FP64 displacement and FP64 accumulation of the forces.
+ *                   In between, r^2, 1/sqrt(r^2) and r^-3 run on the FP32
+ *                   pipe: the displacement is split into exponent-scaled
+ *                   FP32 (hi, lo) pairs, r^2 is a double-float, the FP32
+ *                   hardware reciprocal square root (MUFU) is refined by a
+ *                   Newton residual formed in compensated FP32 (Sec. IV:
+ *                   approximate 1/sqrt refined by Newton-Raphson), and one
+ *                   FP64 add widens r^-3.  Relative error of r^-3 <= 1.1e-13
+ *                   (measured) for any FP64 displacement whose r^-3 is a
+ *                   normal double.
  *  NB_MIXED      -- pair displacements in FP64, cast to FP32; r^2, rsqrt,
  *                   r^-3 and the products in FP32; per-tile FP32 partial
  *                   sums added into FP64 accumulators with compensation.
@@ -156,8 +162,10 @@ nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi,
  * (step of the new state), via Box-Muller.
  * On entry sys->a must hold the total acceleration at the current state (call
  * nb_forces with NB_ACC_TOTAL once after setting positions/velocities).
- * Updates x, v, a in place and advances sys->step by nsteps.  One force
- * launch and one epilogue launch per step; no host synchronisation.      */
+ * Updates x, v, a in place and advances sys->step by nsteps.  Per step one
+ * pair-force launch and one epilogue launch (which also performs the next
+ * drift), plus the FP32 position split for NB_MIXED_SPLIT; one drift launch
+ * per call; no host synchronisation.                                      */
 nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps,
                   void *stream);
 
@@ -168,8 +176,9 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps,
  *             (m/2) sum omega_k^2 x_k^2; RF: (m/2) sum (c (x^2 - y^2) +
  *             omega_z^2 z^2), c = (q Omega^2/2) cos(Omega t + phase)),
  *   Coulomb = (k_C/2) sum_i q_i sum_{j != i} q_j / sqrt(r_ij^2 + soft2).
- * FP64 pair arithmetic regardless of params->precision.  Synchronises the
- * stream before returning.                                               */
+ * FP64 differences and sums regardless of params->precision; the pair term
+ * 1/sqrt(r^2 + soft2) is formed as in NB_FP64 (FP32-pipe double-float,
+ * widened to FP64).  Synchronises the stream before returning.            */
 nb_status nb_energy(const nb_params *params, const nb_system *sys,
                     double out[4], void *stream);
 
@@ -178,7 +187,10 @@ nb_status nb_energy(const nb_params *params, const nb_system *sys,
  *   d = r_i - r_j, dl = lam_i - lam_j, s^2 = |d|^2 + soft2,
  * plus, with NB_ACC_TOTAL, the trap's diagonal term at the current time.
  * The Jacobian is symmetric, so this is also the Jacobian-vector product.
- * lam* and g* are device SoA arrays of n doubles.  FP64.                  */
+ * lam* and g* are device SoA arrays of n doubles.  FP64 differences and
+ * accumulation; each pair's term (with its r^-3, r^-5 and d . dl) is formed
+ * in exponent-scaled double-float on the FP32 pipe and widened to FP64
+ * (relative error about 2^-44 of the term).                              */
 nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys,
                         const double *lx, const double *ly, const double *lz,
                         double *gx, double *gy, double *gz, int flags,
@@ -218,8 +230,8 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
  * or 256), `R` ions per thread (1, 2, 4; force kernel only) and about
  * `blocks_per_sm` (i-tile, j-chunk) blocks per SM.  For kind 3 (the ensemble
  * kernel): `block` threads per block (multiple of 32, <= 512), and R = 0 to
- * keep its one-sided force phase (by default fp64 ensembles whose instances
- * all have at most 4096 ions use the half-pair phase).  For kind 4
+ * keep its one-sided force phase (by default ensembles whose instances all
+ * have at most 4096 ions use the half-pair phase).  For kind 4
  * (the symmetric half-pair force kernel of the four force precisions): `block` ions
  * per block pair unit (128, 256, 512, 1024) and R = 1 to use it or 0 to disable
  * it for that n range (by default it is used from n = 4096).  For kind 5
