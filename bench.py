@@ -63,6 +63,8 @@ def parse():
                     help="large: the N=1e5 headline; kz: the 512-instance ensemble (extra line)")
     ap.add_argument("--profile-forces", action="store_true",
                     help="profiling case: two nb_forces calls per precision at --n, no timing")
+    ap.add_argument("--profile-vjp", action="store_true",
+                    help="profiling case: two nb_forces_vjp calls at --n, no timing")
     return ap.parse_args()
 
 
@@ -436,9 +438,28 @@ def profile_forces(args):
     print("profile case done: n=%d" % w["n"])
 
 
+def profile_vjp(args):
+    """Small case for ncu: two nb_forces_vjp calls (the adjoint's pair kernel)
+    at --n on the large-cloud distribution with seeded cotangents."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2106_11143_gb300 as nb
+    from paper_2106_11143_gb300 import workloads as W
+    w = W.cloud_large(n=args.n)
+    sysm = nb.System(w["pos"], w["vel"])
+    lam = np.random.default_rng(1).standard_normal((3, w["n"]))
+    par = nb.Params.from_phys(w["phys"])
+    for _ in range(2):
+        nb.forces_vjp(par, sysm, lam)
+    nb.sync_status()
+    print("profile case done: n=%d" % w["n"])
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.profile_forces:
+    if a.profile_vjp:
+        profile_vjp(a)
+    elif a.profile_forces:
         profile_forces(a)
     elif a.workload == "kz" and a.impl == "ours":
         main_kz(a)
