@@ -210,6 +210,33 @@ class System:
         v.step = self.step
         return v
 
+    def state_dict(self):
+        """The full Verlet state as CPU tensors (positions, velocities, the
+        acceleration of the current state, q, m, step), for torch.save.  A
+        system rebuilt from it continues bitwise as the original would: the
+        acceleration is part of the state, and the step counter sets the time
+        and the Langevin noise stream."""
+        d = {k: getattr(self, k).detach().cpu().clone() for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")}
+        d["q"] = None if self.q is None else self.q.detach().cpu().clone()
+        d["m"] = None if self.m is None else self.m.detach().cpu().clone()
+        d["step"] = int(self.step)
+        return d
+
+    @classmethod
+    def from_state(cls, d, device="cuda"):
+        """A System holding the state saved by state_dict (copied to `device`)."""
+        s = cls.__new__(cls)
+        s.n = int(d["x"].numel())
+        for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
+            t = d[k]
+            if t.dtype != torch.float64 or t.numel() != s.n:
+                raise ValueError("state entry %s must be float64 of length %d" % (k, s.n))
+            setattr(s, k, t.to(device).clone())
+        s.q = None if d.get("q") is None else d["q"].to(device, torch.float64).clone()
+        s.m = None if d.get("m") is None else d["m"].to(device, torch.float64).clone()
+        s.step = int(d["step"])
+        return s
+
     def pos(self):
         return torch.stack([self.x, self.y, self.z])
 

@@ -279,6 +279,30 @@ def test_step_determinism_and_resume(nb):
         assert torch.equal(getattr(a, t), getattr(c, t))
 
 
+def test_checkpoint_resume_bitwise(nb, tmp_path):
+    """A run checkpointed to a file after 15 steps (System.state_dict) and
+    resumed in a fresh System continues bit for bit as the uninterrupted run:
+    RF trap (time from the step counter), friction and Langevin noise (the
+    Philox counter includes the step)."""
+    w = W.cloud_rf_16384(n=2000)
+    phys = dict(w["phys"], noise_T=0.5e-3)
+    par = nb.Params.from_phys(phys)
+    a = nb.System(w["pos"], w["vel"])
+    nb.forces(par, a, total=True)
+    nb.step(par, a, 30)
+    b = nb.System(w["pos"], w["vel"])
+    nb.forces(par, b, total=True)
+    nb.step(par, b, 15)
+    nb.sync_status()
+    torch.save(b.state_dict(), tmp_path / "ckpt.pt")
+    c = nb.System.from_state(torch.load(tmp_path / "ckpt.pt"))
+    assert c.step == 15
+    nb.step(par, c, 15)
+    nb.sync_status()
+    for t in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
+        assert torch.equal(getattr(a, t), getattr(c, t)), t
+
+
 @pytest.mark.parametrize("precision", ALL)
 def test_full_size_sampled(nb, orc, precision):
     """N = 1e5 (the large-cloud workload, launch configuration of the bench):

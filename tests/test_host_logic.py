@@ -66,3 +66,19 @@ def test_tuning_validation(api):
     api.set_tuning("symmetric_vjp", "fp64", 0, 100, 256, R=0)
     api.set_tuning("force", "fp64", 0, 100, 64, R=2, blocks_per_sm=8)
     api.set_tuning("force", "fp64", 0, 0, 0)  # clear
+
+
+def test_system_state_round_trip(api, tmp_path):
+    """state_dict / from_state keep every array bit for bit, through a file."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(3)
+    s = api.System(rng.standard_normal((3, 17)), rng.standard_normal((3, 17)),
+                   q=rng.standard_normal(17), device="cpu", step=41, m=rng.uniform(1, 2, 17))
+    s.ax.copy_(torch.from_numpy(rng.standard_normal(17)))
+    path = tmp_path / "state.pt"
+    torch.save(s.state_dict(), path)
+    r = api.System.from_state(torch.load(path), device="cpu")
+    assert r.n == 17 and r.step == 41
+    for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az", "q", "m"):
+        assert torch.equal(getattr(r, k), getattr(s, k)), k
