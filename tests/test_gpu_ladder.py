@@ -83,3 +83,13 @@ def test_step_rate_sweep_runs(nb):
     assert len(rows) == 4
     for r in rows:
         assert r["ms_per_step"] > 0 and r["graph_ms_per_step"] > 0
+
+
+def test_workload_runs_module(nb):
+    """The end-to-end workload runner on its small pieces."""
+    from paper_2106_11143_gb300 import runs
+    from paper_2106_11143_gb300 import workloads as W
+    r = runs.cloud_run(W.cloud_harmonic_1024(), "fp64", 10)
+    assert r["steps"] == 10 and r["device_ms"] > 0 and np.isfinite(r["final_energy_J"][3])
+    k = runs.kz(nsteps=4, chunk=2)
+    assert k["steps"] == 4 and k["instances"] == 512
