@@ -19,6 +19,12 @@
  *    demand, reused by later calls on the same stream, and freed by
  *    nb_release().  Calls on the same stream are ordered; calls on
  *    different streams use different scratch.
+ *  - Host threads: the entry points may be called from several host
+ *    threads (the scratch registry and the tuning table are locked inside
+ *    the library), but calls that share a stream must come from one thread
+ *    at a time: any call may regrow that stream's scratch, after
+ *    synchronising the stream, while another thread is still enqueuing work
+ *    that uses the old buffer.  nb_release() must not overlap any other call.
  *  - Every call validates its arguments on the host first and returns
  *    NB_EINVAL without enqueuing any work if they are wrong.  Numerical
  *    failures on the device (a non-finite acceleration or velocity) are
