@@ -444,3 +444,37 @@ def test_step_cuda_graph_capture(nb, precision, n):
     nb.sync_status()
     for t in ("x", "vz", "ay"):
         assert torch.equal(getattr(eager, t), getattr(sysm, t)), t
+
+
+def test_concurrent_host_threads_own_streams(nb):
+    """Two host threads, each stepping its own system on its own stream (the
+    library's scratch registry is shared and locked), give bitwise the
+    results of running them one after the other."""
+    import threading
+    ws = [W.cloud_harmonic_1024(n=5000), W.cloud_rf_16384(n=20000)]
+    par = [nb.Params.from_phys(ws[0]["phys"]), nb.Params.from_phys(ws[1]["phys"], precision="mixed_split")]
+
+    def run(k, stream, out):
+        with torch.cuda.stream(stream):
+            s = nb.System(ws[k]["pos"], ws[k]["vel"])
+            nb.forces(par[k], s, total=True, stream=stream)
+            for _ in range(4):
+                nb.step(par[k], s, 5, stream=stream)
+            stream.synchronize()
+            out[k] = s
+
+    serial = {}
+    for k in range(2):
+        run(k, torch.cuda.Stream(), serial)
+    conc = {}
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    th = [threading.Thread(target=run, args=(k, streams[k], conc)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    for k in range(2):
+        nb.sync_status(streams[k])
+        for t in ("x", "vy", "az"):
+            assert torch.equal(getattr(serial[k], t), getattr(conc[k], t)), (k, t)
