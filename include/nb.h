@@ -70,7 +70,11 @@ typedef enum {
  *  NB_MIXED_SPLIT -- as NB_MIXED, but each position is carried as an FP32
  *                   (hi, lo) pair built from the FP64 value once per call,
  *                   and the displacement is (hi_i - hi_j) + (lo_i - lo_j)
- *                   in FP32.  Same accuracy class as NB_MIXED.
+ *                   in FP32.  Same accuracy class as NB_MIXED while the
+ *                   coordinates are not much larger than the separations:
+ *                   the (hi, lo) pair keeps about 48 bits, so the displacement
+ *                   error is about 2^-48 |r| (relative 2^-48 |r| / |r_i - r_j|,
+ *                   1e-6 at |r| / |r_i - r_j| ~ 3e8).
  *  NB_DF64       -- FP64-class accuracy from FP32 arithmetic: FP64
  *                   displacement split into an FP32 (hi, lo) pair; r^2,
  *                   r^-3 and the force products as double-floats (FP32

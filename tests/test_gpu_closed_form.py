@@ -94,3 +94,34 @@ def test_permutation_permutes_forces(nb, orc, precision):
         S = np.array([orc.coulomb(p, *pos, i0=int(i), i1=int(i) + 1, want_absf=True)[4][0] for i in idx])
         d = np.sqrt(np.sum((a[:, idx] - back[:, idx]) ** 2, axis=0))
         assert np.all(d <= 2 * GATE[precision] * S), (n, np.max(d / S))
+
+
+@pytest.mark.parametrize("precision", ALL)
+def test_translation_invariance(nb, orc, precision):
+    """Shifting every position by the same vector (1 cm and 10 cm off the
+    origin) leaves the forces unchanged, through both the one-sided and the
+    symmetric kernel.  Positions sit on a 2^-40 m grid and the shifts are
+    grid multiples, so shifted positions and all their differences are exact
+    in FP64: the modes that form the displacement in FP64 (fp64, df64, mixed)
+    see bitwise the same displacements and must give bitwise the same forces;
+    the split mode, which works from FP32 (hi, lo) positions, stays within its
+    gate."""
+    g = 2.0 ** -40
+    for n in (3000, 20000):
+        pos, _ = W.random_cloud(n, seed=600 + n)
+        pos = np.round(pos / g) * g
+        a = coulomb_acc(nb, pos, precision)
+        if precision == "mixed_split":
+            idx = np.random.default_rng(n).integers(0, n, 16)
+            p = orc.make_params(**W.phys())
+            S = np.array([orc.coulomb(p, *pos, i0=int(i), i1=int(i) + 1, want_absf=True)[4][0] for i in idx])
+        for shift in (1e-2, 1e-1):
+            sh = np.round(np.array([[shift], [-0.5 * shift], [0.3 * shift]]) / g) * g
+            moved = pos + sh
+            assert np.array_equal(moved - sh, pos)  # exact
+            b = coulomb_acc(nb, moved, precision)
+            if precision == "mixed_split":
+                d = np.sqrt(np.sum((a[:, idx] - b[:, idx]) ** 2, axis=0))
+                assert np.all(d <= GATE[precision] * S), (n, shift, np.max(d / S))
+            else:
+                assert np.array_equal(a, b), (n, shift)
