@@ -37,7 +37,9 @@ struct __align__(16) BD4 {
 
 constexpr int BATCH_MAX_INST = 1024;
 constexpr int BATCH_MAX_BINS = 1024;
-constexpr int BATCH_MAX_N = 6144;  // ions per instance: 32 B each in shared memory (192 KB)
+static_assert(BATCH_MAX_INST == BATCH_LIMIT_INST, "schedule arrays sized for the validated instance limit");
+// ions per instance (BATCH_LIMIT_N, checked on the host): 32 B each in shared memory
+static_assert(BATCH_LIMIT_N * sizeof(BD4) <= 227 * 1024, "an instance's positions fit one block's shared memory");
 
 struct BatchSched {
   int n_inst;
