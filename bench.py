@@ -18,7 +18,6 @@ all-pairs problem per GPU here; no collective on the data path).
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess

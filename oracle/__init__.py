@@ -15,7 +15,6 @@ Every function follows a passage of the paper (see nb_oracle.c):
   philox4x32_10, normals3 -- counter-based RNG from its published definition
 """
 import ctypes as C
-import os
 
 import numpy as np
 

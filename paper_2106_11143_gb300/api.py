@@ -7,7 +7,7 @@ no CPU fallback -- if libnb.so is missing, every call raises.
 """
 import ctypes as C
 import os
-from dataclasses import dataclass, field, fields
+from dataclasses import dataclass, fields
 
 import numpy as np
 import torch

@@ -27,7 +27,6 @@ pancake(): the N = 128 radial-plane (2D) crystal of Sec. V, compared the same
 """
 import argparse
 import json
-import math
 
 import numpy as np
 import torch

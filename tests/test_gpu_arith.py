@@ -107,7 +107,6 @@ def test_rinv3_softening_and_zero(nb):
 
 
 def test_probe_rejects_bad_arguments(nb):
-    import ctypes as C
     L = nb.lib()
     assert L.nb_rinv3_probe(99, 4, None, None, None, 0.0, None, None) == 1
     assert L.nb_rinv3_probe(0, -1, None, None, None, 0.0, None, None) == 1

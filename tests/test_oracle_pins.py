@@ -7,7 +7,6 @@ import math
 import os
 
 import numpy as np
-import pytest
 
 from paper_2106_11143_gb300 import workloads as W
 
