@@ -59,3 +59,15 @@ def test_invalid_arguments_rejected_on_host(libnb):
     libnb.nb_step.restype = ctypes.c_int
     assert libnb.nb_forces(None, None, None, 0, None) == 1
     assert libnb.nb_step(None, None, 1, None) == 1
+    # the arithmetic probes validate before touching the device
+    libnb.nb_rinv3_probe.restype = ctypes.c_int
+    libnb.nb_rinv3_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+    libnb.nb_rsqrt_seed_probe.restype = ctypes.c_int
+    libnb.nb_rsqrt_seed_probe.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert libnb.nb_rinv3_probe(99, 4, None, None, None, 0.0, None, None) == 1   # unknown precision
+    assert libnb.nb_rinv3_probe(0, -1, None, None, None, 0.0, None, None) == 1   # n < 0
+    assert libnb.nb_rinv3_probe(0, 4, None, None, None, 0.0, None, None) == 1    # NULL arrays
+    assert libnb.nb_rinv3_probe(0, 4, 8, 8, 8, -1.0, 8, None) == 1               # soft2 < 0
+    assert libnb.nb_rinv3_probe(0, 0, None, None, None, 0.0, None, None) == 0    # n == 0: nothing to do
+    assert libnb.nb_rsqrt_seed_probe(-1, None, None, None) == 1
