@@ -175,7 +175,22 @@ nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi,
  * Updates x, v, a in place and advances sys->step by nsteps.  Per step one
  * pair-force launch and one epilogue launch (which also performs the next
  * drift), plus the FP32 position split for NB_MIXED_SPLIT; one drift launch
- * per call; no host synchronisation.                                      */
+ * per call; no host synchronisation.
+ * Small systems: up to n = 48 ions (NB_FP64, NB_DF64, NB_MIXED,
+ * NB_MIXED_SPLIT), 32 (NB_FP64_RSQ*) or 16 (NB_FP64_SQRTDIV) -- nb_set_tuning kind 7
+ * changes the bounds, up to 512 ions and 227 KB of shared memory -- the call
+ * runs in one thread block: one launch per min(16384, max(64, 2^28/n^2))
+ * steps, positions in shared memory, the one-sided plan's pair items and
+ * chunk sums, and the same kick and drift, so the results are bitwise those
+ * of the multi-kernel steps.
+ * Step windows: for larger n up to 4096 and nsteps >= 32 (nb_set_tuning kind 6
+ * changes both), the middle steps of the call run as replays of one CUDA
+ * graph of 8 steps, captured on a private stream at the first such call and
+ * kept while every kernel argument is unchanged; the epilogues then read the
+ * step index from two counters in the stream's scratch.  The replays run
+ * the same kernels on the same data in the same order on `stream`, so the
+ * results are bitwise those of plain launches.  They are not used while `stream` is
+ * itself being captured or while nb_timing_enable has event pairs left. */
 nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps,
                   void *stream);
 
@@ -247,7 +262,12 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
  * it for that n range (by default it is used from n = 4096).  For kind 5
  * (the symmetric VJP kernel; `precision` NB_FP64): `block` ions per block
  * pair unit (128 or 256) and R = 1 / 0 to use / disable it (by default it is
- * used from n = 4096).  The latest
+ * used from n = 4096).  For kind 6 (step windows of nb_step): R = 1 to
+ * use them or 0 not to, for calls of at least `block` steps (by default
+ * they are used for n <= 4096 and nsteps >= 32).  For kind 7 (single-block
+ * steps of small systems in nb_step): R = 1 to use them or 0 not to, for n
+ * in [n_lo, n_hi] (`block` >= 1, not used; the kernel's own limits still
+ * apply).  The latest
  * matching entry wins; block == 0 removes every override.  Results stay
  * deterministic for a fixed shape; different shapes may differ in the last
  * bits (summation order), except kind 3, which is shape-independent.     */

@@ -325,7 +325,8 @@ def plan_batched(offsets, n_bins):
     return order[:n_inst], start, mx.value, mean.value
 
 
-KINDS = {"force": 0, "potential": 1, "vjp": 2, "ensemble": 3, "symmetric": 4, "symmetric_vjp": 5}
+KINDS = {"force": 0, "potential": 1, "vjp": 2, "ensemble": 3, "symmetric": 4, "symmetric_vjp": 5,
+         "step_windows": 6, "small_steps": 7}
 
 
 def set_tuning(kind, precision, n_lo, n_hi, block, R=1, blocks_per_sm=16):

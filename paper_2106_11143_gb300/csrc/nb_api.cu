@@ -44,12 +44,25 @@ nb_status fail(nb_status s, const char *fmt, ...) {
                   __FILE__, __LINE__);                                                 \
   } while (0)
 
+// A captured two-step window of nb_step, replayed for the middle steps of a
+// long call at small n, and the bytes of every kernel argument it was
+// captured with (it is valid while they are unchanged).
+struct StepGraph {
+  std::vector<unsigned char> key;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;  // kernel launches per replay
+};
+
 // Scratch owned by the library for one (device, stream).
 struct Arena {
   char *buf = nullptr;
   size_t cap = 0;
-  unsigned *err = nullptr;  // device error word
+  unsigned *err = nullptr;  // 256 B: device error word at 0, step counters at 64 and 72
+  cudaStream_t cap_st = nullptr;  // private stream the step window is captured on
+  StepGraph sg;
 };
+
+int64_t *step_counters(Arena *a) { return reinterpret_cast<int64_t *>(reinterpret_cast<char *>(a->err) + 64); }
 
 std::mutex g_mu;
 std::map<std::pair<int, cudaStream_t>, Arena> g_arenas;
@@ -219,13 +232,20 @@ nb_status pair_forces(const Plan &pl, int mode, int64_t n, const double *x, cons
 // ---------------------------------------------------------------------------
 // Instrumentation state.
 std::atomic<uint64_t> g_launches{0};
+thread_local uint64_t *g_count_sink = nullptr;  // set while a step window is captured
 std::mutex g_tmu;
 std::vector<cudaEvent_t> g_ev;  // pairs: start, stop
 int64_t g_ev_cap = 0, g_ev_used = 0;
 
 }  // namespace
 
-void count_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+void count_launches(uint64_t k) {
+  if (g_count_sink) {  // captured into a graph, counted when it is replayed
+    *g_count_sink += k;
+    return;
+  }
+  g_launches.fetch_add(k, std::memory_order_relaxed);
+}
 
 void record_error(const char *msg) { g_last_error = msg; }
 
@@ -241,6 +261,162 @@ void timing_end(cudaStream_t st) {
     ++g_ev_used;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Step windows: at small n a step is a few short kernels and the per-launch
+// cost bounds the step rate, so nb_step captures STEP_WINDOW steps once into a
+// CUDA graph and replays it for the middle steps of a call.
+namespace {
+
+constexpr int64_t STEP_WINDOW = 8;        // steps per replay (even: the position buffers alternate)
+constexpr int64_t STEP_GRAPH_N = 4096;    // default: windows for n up to this
+constexpr int64_t STEP_GRAPH_STEPS = 32;  // default: and calls of at least this many steps
+
+bool timing_active() {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  return g_ev_used < g_ev_cap;
+}
+
+// Whether this nb_step call replays windows.  Tuning kind 6 overrides the
+// default (R = 1 use, 0 not; block = the least nsteps).  Never while the
+// caller's stream is itself being captured or kernel timing is on.
+bool use_step_graph(int mode, int64_t n, int64_t nsteps, cudaStream_t st) {
+  int tb = 0, tr = 0, tbps = 0;
+  bool on = n <= STEP_GRAPH_N;
+  int64_t least = STEP_GRAPH_STEPS;
+  if (tuning_lookup(6, mode, n, &tb, &tr, &tbps)) {
+    on = tr == 1;
+    least = tb;
+  }
+  if (!on || nsteps < std::max<int64_t>(least, STEP_WINDOW + 2) || timing_active()) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs == cudaStreamCaptureStatusNone;
+}
+
+// Single-block steps (nb_small.cu) for small systems: one launch runs many
+// steps, but all pair terms of a step run on one SM, so the path wins only
+// below a size that grows with the pair term's throughput.  Defaults: the
+// largest n, per precision, at which it was faster than the multi-kernel
+// steps on GB300.  Tuning kind 7 overrides them (R = 1 use, 0 not) within
+// the kernel's limits.  Not while kernel timing is on (it times pair
+// kernels).
+// Steps per launch: at most 16384, and about 2^28 pair terms per launch at
+// larger n, so that one launch stays well under a second.
+int64_t small_steps_per_launch(int64_t n) {
+  return std::max<int64_t>(64, std::min<int64_t>(16384, ((int64_t)1 << 28) / (n * n)));
+}
+
+int64_t small_default_n(int mode) {
+  switch (mode) {
+    case MODE_SQRTDIV: return 16;  // an FP64 square root and division per pair
+    case MODE_RSQ:
+    case MODE_RSQ_NR1:
+    case MODE_RSQ_NR2: return 32;
+    default: return 48;
+  }
+}
+
+bool use_small_steps(const Plan &pl, int mode, int64_t n) {
+  if (pl.sym || n > SMALL_MAX_N || small_smem_bytes(pl, mode, n) > (size_t)SMALL_SMEM_MAX || timing_active())
+    return false;
+  int tb = 0, tr = 0, tbps = 0;
+  if (tuning_lookup(7, mode, n, &tb, &tr, &tbps)) return tr == 1;
+  return n <= small_default_n(mode);
+}
+
+// The bytes of every argument the kernels of a window take: a cached window
+// is replayed only while they are unchanged.
+struct KeyBytes {
+  std::vector<unsigned char> b;
+  template <class T>
+  void put(const T &v) {
+    const unsigned char *p = reinterpret_cast<const unsigned char *>(&v);
+    b.insert(b.end(), p, p + sizeof(T));
+  }
+};
+
+static_assert(sizeof(Phys) == 160 && sizeof(StateView) == 96 && sizeof(Plan) == 32,
+              "a new field of Phys, StateView or Plan must join window_key");
+
+std::vector<unsigned char> window_key(const Plan &pl, int mode, const Phys &p, const StateView &v,
+                                      double *const *A, double *const *B, const double *part,
+                                      const float *split, const Arena *a) {
+  KeyBytes k;
+  k.put(mode);
+  k.put(tuning_generation());
+  k.put(pl.block); k.put(pl.R); k.put(pl.jchunk); k.put(pl.n_it); k.put(pl.n_jc); k.put(pl.sym); k.put(pl.G);
+  k.put(p.k_coulomb); k.put(p.mass); k.put(p.charge); k.put(p.soft2); k.put(p.trap); k.put(p.precision);
+  for (int c = 0; c < 3; ++c) {
+    k.put(p.omega[c]);
+    k.put(p.omega_rate[c]);
+  }
+  k.put(p.q_mathieu); k.put(p.omega_rf); k.put(p.rf_phase); k.put(p.gamma); k.put(p.dt); k.put(p.t0);
+  k.put(p.noise_T); k.put(p.seed); k.put(p.instance);
+  k.put(v.n); k.put(v.x); k.put(v.y); k.put(v.z); k.put(v.vx); k.put(v.vy); k.put(v.vz);
+  k.put(v.ax); k.put(v.ay); k.put(v.az); k.put(v.q); k.put(v.m);
+  for (int c = 0; c < 3; ++c) {
+    k.put(A[c]);
+    k.put(B[c]);
+  }
+  k.put(part); k.put(split); k.put(a->err);
+  return k.b;
+}
+
+// Captures one window on the arena's private stream: STEP_WINDOW steps of
+// pair forces and epilogue, the position buffers alternating A -> B -> A.
+// The epilogues take the step index from the two counters c0, c1: the first
+// reads c0 (the index of the step before the window) and stores
+// c0 + STEP_WINDOW in c1; the others read c1 with offsets, and the last
+// copies c1 to c0, so each replay continues where the previous one ended.
+nb_status capture_window(Arena *a, const Plan &pl, int mode, const Phys &p, const StateView &v,
+                         double *const *A, double *const *B, double *part, float *split,
+                         double soft2) {
+  if (!a->cap_st) NB_CUDA_TRY(cudaStreamCreateWithFlags(&a->cap_st, cudaStreamNonBlocking));
+  cudaStream_t cs = a->cap_st;
+  int64_t *c = step_counters(a);
+  NB_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  uint64_t kernels = 0;
+  g_count_sink = &kernels;
+  nb_status rc = NB_OK;
+  cudaError_t e = cudaSuccess;
+  for (int64_t k = 1; k <= STEP_WINDOW && rc == NB_OK && e == cudaSuccess; ++k) {
+    double *const *P = (k % 2) ? A : B;
+    double *const *Nx = (k % 2) ? B : A;
+    rc = pair_forces(pl, mode, v.n, P[0], P[1], P[2], v.q, soft2, part, split, cs);
+    if (rc != NB_OK) break;
+    const int64_t *cin = k == 1 ? c : c + 1;
+    const int64_t soff = k == 1 ? 1 : k - STEP_WINDOW;
+    int64_t *cout = k == 1 ? c + 1 : (k == STEP_WINDOW ? c : nullptr);
+    const int64_t cout_off = k == 1 ? STEP_WINDOW : 0;
+    e = launch_epi_step(p, v, P[0], P[1], P[2], part, pl.n_jc, soff, Nx[0], Nx[1], Nx[2], a->err, cs,
+                        cin, cout, cout_off);
+    count_launches(1);
+  }
+  g_count_sink = nullptr;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+  if (rc != NB_OK || e != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (rc != NB_OK) return rc;
+    return fail(NB_ECUDA, "capturing the step window failed: %s",
+                cudaGetErrorString(e != cudaSuccess ? e : ee));
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return fail(NB_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ie));
+  if (a->sg.exec) cudaGraphExecDestroy(a->sg.exec);  // a pending launch of it still completes
+  a->sg.exec = exec;
+  a->sg.kernels = kernels;
+  return NB_OK;
+}
+
+}  // namespace
 
 }  // namespace nb
 
@@ -296,6 +472,19 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void 
   const int mode = params->precision;
   const Plan pl = make_plan(n, mode, 0);
   Arena *a = nullptr;
+  if (use_small_steps(pl, mode, n)) {
+    NB_TRY(get_arena(st, 256, &a));
+    const Phys p = to_phys(params);
+    const StateView v = to_view(sys);
+    for (int64_t done = 0; done < nsteps;) {
+      const int64_t k = std::min(nsteps - done, small_steps_per_launch(n));
+      NB_CUDA_TRY(launch_small_steps(pl, mode, p, v, sys->step + done, k, a->err, st));
+      count_launches(1);
+      done += k;
+    }
+    sys->step += nsteps;
+    return NB_OK;
+  }
   NB_TRY(get_arena(st, force_bytes(pl, mode, n, true, false, pl), &a));
   Carver cv;
   cv.base = a->buf;
@@ -309,21 +498,39 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void 
   auto buf = [&](int64_t s) -> double ** { return ((nsteps - 1 - s) % 2 == 0) ? obuf : ubuf; };
   const Phys p = to_phys(params);
   const StateView v = to_view(sys);
+  // Steps 0 .. nsteps-2 write the next drift, the last one the final state.
+  // With step windows, the middle steps after `pre` eager ones are `reps`
+  // replays of one captured window.
+  const bool windows = use_step_graph(mode, n, nsteps, st);
+  const int64_t pre = windows ? 1 + (nsteps - 2) % STEP_WINDOW : nsteps - 1;
+  const int64_t reps = windows ? (nsteps - 1 - pre) / STEP_WINDOW : 0;
+  int64_t *ctr = step_counters(a);
   double **b0 = buf(0);
   NB_CUDA_TRY(launch_drift(p, v, b0[0], b0[1], b0[2], st));
   count_launches(1);
-  for (int64_t s = 0; s < nsteps; ++s) {
-    double **P = buf(s);
+  for (int64_t s = 0; s < pre; ++s) {
+    double **P = buf(s), **Nx = buf(s + 1);
     NB_TRY(pair_forces(pl, mode, n, P[0], P[1], P[2], sys->q, params->soft2, part, split, st));
     const int64_t snew = sys->step + s + 1;
-    if (s + 1 < nsteps) {
-      double **Nx = buf(s + 1);
-      NB_CUDA_TRY(launch_epi_step(p, v, P[0], P[1], P[2], part, pl.n_jc, snew, Nx[0], Nx[1], Nx[2], a->err, st));
-    } else {
-      NB_CUDA_TRY(launch_epi_step(p, v, P[0], P[1], P[2], part, pl.n_jc, snew, nullptr, nullptr, nullptr, a->err, st));
-    }
+    int64_t *cout = (windows && s + 1 == pre) ? ctr : nullptr;  // the windows' starting index
+    NB_CUDA_TRY(launch_epi_step(p, v, P[0], P[1], P[2], part, pl.n_jc, snew, Nx[0], Nx[1], Nx[2], a->err, st,
+                                nullptr, cout, snew));
     count_launches(1);
   }
+  if (reps > 0) {
+    std::vector<unsigned char> key = window_key(pl, mode, p, v, buf(pre), buf(pre + 1), part, split, a);
+    if (!a->sg.exec || a->sg.key != key) {
+      NB_TRY(capture_window(a, pl, mode, p, v, buf(pre), buf(pre + 1), part, split, params->soft2));
+      a->sg.key.swap(key);
+    }
+    for (int64_t r = 0; r < reps; ++r) NB_CUDA_TRY(cudaGraphLaunch(a->sg.exec, st));
+    count_launches(a->sg.kernels * (uint64_t)reps);
+  }
+  double **P = buf(nsteps - 1);
+  NB_TRY(pair_forces(pl, mode, n, P[0], P[1], P[2], sys->q, params->soft2, part, split, st));
+  NB_CUDA_TRY(launch_epi_step(p, v, P[0], P[1], P[2], part, pl.n_jc, sys->step + nsteps, nullptr, nullptr, nullptr,
+                              a->err, st));
+  count_launches(1);
   sys->step += nsteps;
   return NB_OK;
 }
@@ -449,7 +656,7 @@ nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n
     tuning_clear();
     return NB_OK;
   }
-  if (kind < 0 || kind > 5) return fail(NB_EINVAL, "kind must be 0..5");
+  if (kind < 0 || kind > 7) return fail(NB_EINVAL, "kind must be 0..7");
   if (precision < NB_FP64 || precision > NB_FP64_RSQ_NR2) return fail(NB_EINVAL, "bad precision");
   if (n_lo < 0 || n_hi < n_lo) return fail(NB_EINVAL, "bad n range");
   if (kind == 4) {
@@ -458,6 +665,12 @@ nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n
     if (R != 0 && R != 1) return fail(NB_EINVAL, "R must be 1 (use) or 0 (disable)");
   } else if (kind == 5) {
     if (block != 128 && block != 256) return fail(NB_EINVAL, "symmetric VJP block must be 128 or 256 ions");
+    if (R != 0 && R != 1) return fail(NB_EINVAL, "R must be 1 (use) or 0 (disable)");
+  } else if (kind == 7) {
+    if (block < 1) return fail(NB_EINVAL, "block must be >= 1 (it is not used)");
+    if (R != 0 && R != 1) return fail(NB_EINVAL, "R must be 1 (use) or 0 (disable)");
+  } else if (kind == 6) {
+    if (block < 1) return fail(NB_EINVAL, "block (the least nsteps) must be >= 1");
     if (R != 0 && R != 1) return fail(NB_EINVAL, "R must be 1 (use) or 0 (disable)");
   } else if (kind == 3) {
     if (block < 32 || block > 512 || block % 32) return fail(NB_EINVAL, "block must be 32..512, a multiple of 32");
@@ -674,6 +887,8 @@ nb_status nb_release(void) {
   for (auto &kv : g_arenas) {
     if (cudaSetDevice(kv.first.first) != cudaSuccess) { rc = NB_ECUDA; continue; }
     cudaDeviceSynchronize();
+    if (kv.second.sg.exec && cudaGraphExecDestroy(kv.second.sg.exec) != cudaSuccess) rc = NB_ECUDA;
+    if (kv.second.cap_st && cudaStreamDestroy(kv.second.cap_st) != cudaSuccess) rc = NB_ECUDA;
     if (kv.second.buf && cudaFree(kv.second.buf) != cudaSuccess) rc = NB_ECUDA;
     if (kv.second.err && cudaFree(kv.second.err) != cudaSuccess) rc = NB_ECUDA;
   }

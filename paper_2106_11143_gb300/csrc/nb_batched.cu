@@ -27,7 +27,7 @@
 #include <mutex>
 #include <vector>
 
-#include "nb_common.cuh"
+#include "nb_verlet.cuh"
 
 namespace nb {
 
@@ -88,19 +88,6 @@ __device__ __forceinline__ void bpair_df64(double xi, double yi, double zi, cons
     two_sum_f(ah[k], ph, s, t);
     ah[k] = s;
     al[k] += t + pl;
-  }
-}
-
-// Philox4x32-10 and Box-Muller as in the single-system epilogue.
-__device__ __forceinline__ void bphilox(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
-    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
 }
 
@@ -280,23 +267,6 @@ __device__ void bsym_forces(const BD4 *sp, double *acc, int npad, int n, int np3
   }
 }
 
-__device__ __forceinline__ void bnormals3(unsigned long long seed, unsigned instance, int64_t step,
-                                          int64_t ion, double out[3]) {
-  uint32_t c[4] = {(uint32_t)ion, (uint32_t)((uint64_t)step & 0xffffffffu),
-                   (uint32_t)((uint64_t)step >> 32), instance};
-  bphilox(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
-  const double s = 2.3283064365386963e-10;
-  const double u0 = ((double)c[0] + 0.5) * s, u1 = ((double)c[1] + 0.5) * s;
-  const double u2 = ((double)c[2] + 0.5) * s, u3 = ((double)c[3] + 0.5) * s;
-  const double m0 = sqrt(-2.0 * log(u0)), m1 = sqrt(-2.0 * log(u2));
-  double s1, c1, s3, c3;
-  sincospi(2.0 * u1, &s1, &c1);
-  sincospi(2.0 * u3, &s3, &c3);
-  out[0] = m0 * c1;
-  out[1] = m0 * s1;
-  out[2] = m1 * c3;
-}
-
 template <bool QARR, bool DF, bool SYM>
 __global__ void __launch_bounds__(512, 1) k_batched(Phys p, StateView s,
                                                   const __grid_constant__ BatchSched sch,
@@ -307,7 +277,7 @@ __global__ void __launch_bounds__(512, 1) k_batched(Phys p, StateView s,
   const int T = blockDim.x;
   const int tid = threadIdx.x;
   const double dt = p.dt, hdt2 = 0.5 * dt * dt;
-  const double cfr = p.gamma * dt / (2.0 * p.mass), g = p.gamma / p.mass;
+  const double inv = 1.0 / (1.0 + p.gamma * dt / (2.0 * p.mass)), g = p.gamma / p.mass;
   const double sig = p.noise_T > 0.0 ? sqrt(2.0 * p.gamma * KB * p.noise_T * dt) / p.mass : 0.0;
   const double pref_u = p.k_coulomb * p.charge * p.charge / p.mass;
   float s2h = 0.0f, s2l = 0.0f;
@@ -381,14 +351,14 @@ __global__ void __launch_bounds__(512, 1) k_batched(Phys p, StateView s,
           double tr[3];
           trap_accel(p, t, ri.x, ri.y, ri.z, tr[0], tr[1], tr[2]);
           double xi[3] = {0.0, 0.0, 0.0};
-          if (sig > 0.0) bnormals3(p.seed, inst_id, snew, i, xi);
+          if (sig > 0.0) normals3(p.seed, inst_id, snew, i, xi);
           const double acc[3] = {a0, a1, a2};
           double *vs[3] = {s.vx, s.vy, s.vz};
           double *as[3] = {s.ax, s.ay, s.az};
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
             const double u = pref * acc[k] + tr[k];
-            double v = (vs[k][gi] + 0.5 * dt * (as[k][gi] + u)) / (1.0 + cfr);
+            double v = (vs[k][gi] + 0.5 * dt * (as[k][gi] + u)) * inv;
             v += sig * xi[k];
             const double a = u - g * v;
             vs[k][gi] = v;

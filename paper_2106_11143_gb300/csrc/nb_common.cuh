@@ -485,7 +485,7 @@ Plan make_plan(int64_t n, int mode, int kind);  // kind: 0 force, 1 phi, 2 vjp
 int device_sm_count();
 
 // Launch accounting and optional event timing of pair kernels (nb_api.cu).
-void count_launches(int k);
+void count_launches(uint64_t k);
 void record_error(const char *msg);  // message returned by nb_last_error()
 void timing_begin(cudaStream_t st);
 void timing_end(cudaStream_t st);
@@ -546,7 +546,8 @@ cudaError_t launch_drift(const Phys &p, const StateView &s, double *px, double *
 cudaError_t launch_epi_step(const Phys &p, const StateView &s, const double *cx,
                             const double *cy, const double *cz, const double *part, int n_jc,
                             int64_t snew, double *nx, double *ny, double *nz, unsigned *err,
-                            cudaStream_t st);
+                            cudaStream_t st, const int64_t *cin = nullptr,
+                            int64_t *cout = nullptr, int64_t cout_off = 0);
 // Ensemble kernel (nb_batched.cu).
 int batched_plan(int n_inst, const int64_t *offsets, int n_bins, unsigned short *order,
                  unsigned short *bin_start, double *max_load, double *mean_load);
@@ -555,10 +556,21 @@ cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const 
                            unsigned *err, cudaStream_t st);
 constexpr int BATCH_LIMIT_INST = 1024;
 constexpr int BATCH_LIMIT_N = 6144;
+// Single-block step kernel for small systems (nb_small.cu): one thread per
+// ion in the kick, so at most SMALL_THREADS ions; positions and the chunk
+// partials of the one-sided plan `pl` in at most SMALL_SMEM_MAX bytes of
+// shared memory (small_smem_bytes).
+constexpr int SMALL_THREADS = 512;
+constexpr int SMALL_MAX_N = SMALL_THREADS;
+constexpr int SMALL_SMEM_MAX = 227 * 1024;
+size_t small_smem_bytes(const Plan &pl, int mode, int64_t n);
+cudaError_t launch_small_steps(const Plan &pl, int mode, const Phys &p, const StateView &s,
+                               int64_t step0, int64_t nsteps, unsigned *err, cudaStream_t st);
 
 // Launch-shape overrides set by nb_set_tuning (nb_pair.cu); kind 3 is the
 // ensemble kernel (block = threads per CTA).
 bool tuning_lookup(int kind, int mode, int64_t n, int *block, int *R, int *blocks_per_sm);
+uint64_t tuning_generation();  // changes whenever the override table does
 void tuning_set(int kind, int mode, int64_t n_lo, int64_t n_hi, int block, int R, int blocks_per_sm);
 void tuning_clear();
 

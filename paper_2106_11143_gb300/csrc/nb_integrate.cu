@@ -1,7 +1,7 @@
 // nb_integrate.cu -- O(N) kernels of libnb.so: the epilogues that turn the
 // pair partial sums into accelerations (Eq. 1), the velocity-Verlet kick and
 // drift (Sec. II), the Langevin kick, and the energy reduction.
-#include "nb_common.cuh"
+#include "nb_verlet.cuh"
 
 namespace nb {
 
@@ -15,81 +15,12 @@ __device__ __forceinline__ double chunk_sum(const double *__restrict__ part, int
   return s;
 }
 
-// The three components of chunk_sum at once, each summed in the same
-// ascending-chunk order (bitwise equal to three chunk_sum calls); eight chunks'
-// loads are issued before their adds, so that a thread keeps 24 loads in
-// flight over the symmetric plan's hundreds of slots.
+// The three components of ion i's chunk partials, part[(jc*3 + c)*n + i],
+// summed by slot_sum3 with streaming loads (the partials are read once).
 __device__ __forceinline__ void chunk_sum3(const double *__restrict__ part, int n_jc, int64_t n,
                                            int64_t i, double out[3]) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  const int64_t stride = 3 * n;
   const double *p = part + i;
-  int jc = 0;
-  for (; jc + 8 <= n_jc; jc += 8, p += 8 * stride) {
-    double v[8][3];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      v[u][0] = __ldcs(p + u * stride);
-      v[u][1] = __ldcs(p + u * stride + n);
-      v[u][2] = __ldcs(p + u * stride + 2 * n);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      s0 += v[u][0];
-      s1 += v[u][1];
-      s2 += v[u][2];
-    }
-  }
-  for (; jc < n_jc; ++jc, p += stride) {
-    s0 += p[0];
-    s1 += p[n];
-    s2 += p[2 * n];
-  }
-  out[0] = s0;
-  out[1] = s1;
-  out[2] = s2;
-}
-
-// Coulomb prefactor k_C q_i w / m_i, where the pair sums carry w_j = q_j when
-// per-ion charges are given and w_j = 1 otherwise.
-__device__ __forceinline__ double coulomb_pref(const Phys &p, const StateView &s, int64_t i) {
-  const double m = ion_mass(p, s, i);
-  return s.q ? p.k_coulomb * s.q[i] / m : p.k_coulomb * p.charge * p.charge / m;
-}
-
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) from its definition:
-// ten rounds of two 32x32 -> 64-bit products with the multipliers
-// 0xD2511F53 and 0xCD9E8D57, key bumped by 0x9E3779B9 / 0xBB67AE85.
-__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
-    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-}
-
-// Three N(0,1) draws for (seed, instance, step, ion): Box-Muller on the four
-// Philox words mapped to (0,1) as (k + 1/2) 2^-32.
-__device__ __forceinline__ void normals3(unsigned long long seed, unsigned instance,
-                                         int64_t step, int64_t ion, double out[3]) {
-  uint32_t c[4] = {(uint32_t)ion, (uint32_t)((uint64_t)step & 0xffffffffu),
-                   (uint32_t)((uint64_t)step >> 32), instance};
-  philox(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
-  const double s = 2.3283064365386963e-10;
-  const double u0 = ((double)c[0] + 0.5) * s, u1 = ((double)c[1] + 0.5) * s;
-  const double u2 = ((double)c[2] + 0.5) * s, u3 = ((double)c[3] + 0.5) * s;
-  const double m0 = sqrt(-2.0 * log(u0)), m1 = sqrt(-2.0 * log(u2));
-  double s1, c1, s3, c3;
-  sincospi(2.0 * u1, &s1, &c1);
-  sincospi(2.0 * u3, &s3, &c3);
-  out[0] = m0 * c1;
-  out[1] = m0 * s1;
-  out[2] = m1 * c3;
+  slot_sum3(n_jc, [&](int jc, int c) { return __ldcs(p + ((int64_t)jc * 3 + c) * n); }, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -163,10 +94,10 @@ cudaError_t launch_epi_vjp(const Phys &p, const StateView &s, const double *part
 __global__ void k_drift(Phys p, StateView s, double *px, double *py, double *pz) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
-  const double dt = p.dt, h = 0.5 * dt * dt;
-  px[i] = s.x[i] + s.vx[i] * dt + h * s.ax[i];
-  py[i] = s.y[i] + s.vy[i] * dt + h * s.ay[i];
-  pz[i] = s.z[i] + s.vz[i] * dt + h * s.az[i];
+  const double dt = p.dt;
+  px[i] = verlet_drift(s.x[i], s.vx[i], s.ax[i], dt);
+  py[i] = verlet_drift(s.y[i], s.vy[i], s.ay[i], dt);
+  pz[i] = verlet_drift(s.z[i], s.vz[i], s.az[i], dt);
 }
 
 cudaError_t launch_drift(const Phys &p, const StateView &s, double *px, double *py, double *pz,
@@ -183,60 +114,102 @@ cudaError_t launch_drift(const Phys &p, const StateView &s, double *px, double *
 //   a+ = a+_cons - (gamma/m) v+
 // then either the next drift r++ = r+ + v+ dt + a+ dt^2/2 into (nx, ny, nz),
 // or (last step) r+ copied to the state positions.
+// The step index is snew = base + soff with base = *cin (a device counter) or
+// 0 when cin is null; with cout non-null, thread 0 stores base + cout_off
+// there.  The counter form lets one captured graph of steps be replayed with
+// a step index that advances from replay to replay (cin and cout are never
+// the same word, so no thread reads what another writes).
 __global__ void k_epi_step(Phys p, StateView s, const double *__restrict__ cx,
                            const double *__restrict__ cy, const double *__restrict__ cz,
-                           const double *__restrict__ part, int n_jc, int64_t snew, double *nx,
+                           const double *__restrict__ part, int n_jc, int64_t soff,
+                           const int64_t *cin, int64_t *cout, int64_t cout_off, double *nx,
                            double *ny, double *nz, unsigned *err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
-  const double dt = p.dt;
-  const double t = p.t0 + (double)snew * dt;
-  const double pref = coulomb_pref(p, s, i);
+  const int64_t base = cin ? *cin : 0;
+  const int64_t snew = base + soff;
+  if (cout && i == 0) *cout = base + cout_off;
   const double r[3] = {cx[i], cy[i], cz[i]};
-  double tr[3];
-  trap_accel(p, t, r[0], r[1], r[2], tr[0], tr[1], tr[2]);
-  const double ts = trap_scale(p, s, i);
-  tr[0] *= ts;
-  tr[1] *= ts;
-  tr[2] *= ts;
-  const double mi = ion_mass(p, s, i);
-  const double c = p.gamma * dt / (2.0 * mi);
-  const double g = p.gamma / mi;
-  double xi[3] = {0.0, 0.0, 0.0};
-  double sig = 0.0;
-  if (p.noise_T > 0.0) {
-    sig = sqrt(2.0 * p.gamma * KB * p.noise_T * dt) / mi;
-    normals3(p.seed, p.instance, snew, i, xi);
-  }
-  double *vs[3] = {s.vx, s.vy, s.vz};
-  double *as[3] = {s.ax, s.ay, s.az};
-  double *ns[3] = {nx, ny, nz};
-  double *xs[3] = {s.x, s.y, s.z};
   double cs[3];
   chunk_sum3(part, n_jc, s.n, i, cs);
-  bool bad = false;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double ucons = pref * cs[k] + tr[k];
-    double v = (vs[k][i] + 0.5 * dt * (as[k][i] + ucons)) / (1.0 + c);
-    v += sig * xi[k];
-    const double a = ucons - g * v;
-    vs[k][i] = v;
-    as[k][i] = a;
-    if (nx)
-      ns[k][i] = r[k] + v * dt + 0.5 * dt * dt * a;
-    else
-      xs[k][i] = r[k];
-    bad |= not_finite(v) || not_finite(a);
+  double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
+  double a[3] = {s.ax[i], s.ay[i], s.az[i]};
+  const bool bad = verlet_kick(p, s, i, snew, r, cs, v, a);
+  s.vx[i] = v[0]; s.vy[i] = v[1]; s.vz[i] = v[2];
+  s.ax[i] = a[0]; s.ay[i] = a[1]; s.az[i] = a[2];
+  if (nx) {
+    nx[i] = verlet_drift(r[0], v[0], a[0], p.dt);
+    ny[i] = verlet_drift(r[1], v[1], a[1], p.dt);
+    nz[i] = verlet_drift(r[2], v[2], a[2], p.dt);
+  } else {
+    s.x[i] = r[0]; s.y[i] = r[1]; s.z[i] = r[2];
   }
   if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
+// The same epilogue with eight lanes per ion, for small n, where one thread
+// per ion leaves the chunk sum a long chain of dependent loads and adds on a
+// few SMs.  Lane u of an ion's group forms slot_sum3's running sum u (chunks
+// u, u+8, ...), three shuffle levels add the eight in slot_sum3's pairing, so
+// the sum is bitwise the same, and lane 0 completes the ion.
+__global__ void k_epi_step8(Phys p, StateView s, const double *__restrict__ cx,
+                            const double *__restrict__ cy, const double *__restrict__ cz,
+                            const double *__restrict__ part, int n_jc, int64_t soff,
+                            const int64_t *cin, int64_t *cout, int64_t cout_off, double *nx,
+                            double *ny, double *nz, unsigned *err) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int u = threadIdx.x & 7;
+  const int64_t i = g < s.n ? g : s.n - 1;  // every lane takes part in the shuffles
+  double cs[3] = {0.0, 0.0, 0.0};
+  const double *pi = part + i;
+  for (int jc = u; jc < n_jc; jc += 8) {
+    const double *q = pi + (int64_t)jc * 3 * s.n;
+    cs[0] += __ldcs(q);
+    cs[1] += __ldcs(q + s.n);
+    cs[2] += __ldcs(q + 2 * s.n);
+  }
+#pragma unroll
+  for (int d = 1; d < 8; d <<= 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double o = __shfl_down_sync(0xffffffffu, cs[c], d, 8);
+      if ((u & (2 * d - 1)) == 0) cs[c] = cs[c] + o;
+    }
+  }
+  if (u != 0 || g >= s.n) return;
+  const int64_t base = cin ? *cin : 0;
+  const int64_t snew = base + soff;
+  if (cout && i == 0) *cout = base + cout_off;
+  const double r[3] = {cx[i], cy[i], cz[i]};
+  double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
+  double a[3] = {s.ax[i], s.ay[i], s.az[i]};
+  const bool bad = verlet_kick(p, s, i, snew, r, cs, v, a);
+  s.vx[i] = v[0]; s.vy[i] = v[1]; s.vz[i] = v[2];
+  s.ax[i] = a[0]; s.ay[i] = a[1]; s.az[i] = a[2];
+  if (nx) {
+    nx[i] = verlet_drift(r[0], v[0], a[0], p.dt);
+    ny[i] = verlet_drift(r[1], v[1], a[1], p.dt);
+    nz[i] = verlet_drift(r[2], v[2], a[2], p.dt);
+  } else {
+    s.x[i] = r[0]; s.y[i] = r[1]; s.z[i] = r[2];
+  }
+  if (bad) atomicOr(err, ERR_NONFINITE);
+}
+
+// Ion counts up to which the epilogue runs with eight lanes per ion.
+constexpr int64_t EPI8_MAX_N = 2048;
+
 cudaError_t launch_epi_step(const Phys &p, const StateView &s, const double *cx, const double *cy,
                             const double *cz, const double *part, int n_jc, int64_t snew,
-                            double *nx, double *ny, double *nz, unsigned *err, cudaStream_t st) {
+                            double *nx, double *ny, double *nz, unsigned *err, cudaStream_t st,
+                            const int64_t *cin, int64_t *cout, int64_t cout_off) {
   const int T = 256;
-  k_epi_step<<<blocks_for(s.n, T), T, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, nx, ny, nz, err);
+  if (s.n <= EPI8_MAX_N)
+    k_epi_step8<<<blocks_for(8 * s.n, T), T, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout, cout_off,
+                                                      nx, ny, nz, err);
+  else
+    k_epi_step<<<blocks_for(s.n, T), T, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout, cout_off,
+                                                 nx, ny, nz, err);
   return cudaGetLastError();
 }
 

@@ -23,102 +23,9 @@
 #include <mutex>
 #include <vector>
 
-#include "nb_common.cuh"
+#include "nb_pairterm.cuh"
 
 namespace nb {
-
-// One staged j-particle: position and weight (or lambda), 16-byte aligned so
-// a tile entry is read with two 128-bit shared-memory loads.
-struct __align__(16) D4 {
-  double x, y, z, w;
-};
-__device__ __forceinline__ D4 make_d4(double x, double y, double z, double w) {
-  D4 r;
-  r.x = x; r.y = y; r.z = z; r.w = w;
-  return r;
-}
-
-// ---------------------------------------------------------------------------
-// Pair terms.
-
-// FP64: acc += w_j (r_i - r_j) / (|r_i - r_j|^2 + soft2)^(3/2)
-template <bool QARR>
-__device__ __forceinline__ void pair_f64(double xi, double yi, double zi, const D4 &pj,
-                                         double soft2, double &ax, double &ay, double &az) {
-  const double dx = xi - pj.x;
-  const double dy = yi - pj.y;
-  const double dz = zi - pj.z;
-  double s = rinv3_fp64(dx, dy, dz, soft2);
-  if (QARR) s *= pj.w;
-  ax = fma(dx, s, ax);
-  ay = fma(dy, s, ay);
-  az = fma(dz, s, az);
-}
-
-// FP64 pair term with the 1/sqrt method of the ladder (Sec. IV): SQRT+DIV,
-// the bare seed, or the seed refined by y <- y (3 - r^2 y^2) / 2 once or
-// twice (the recurrence of Sec. IV); then r^-3 = y^3.
-template <int MODE, bool QARR>
-__device__ __forceinline__ void pair_ladder(double xi, double yi, double zi, const D4 &pj,
-                                            double soft2, double &ax, double &ay, double &az) {
-  const double dx = xi - pj.x;
-  const double dy = yi - pj.y;
-  const double dz = zi - pj.z;
-  const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, soft2)));
-  double s = ladder_rinv3<MODE>(r2);
-  if (QARR) s *= pj.w;
-  ax = fma(dx, s, ax);
-  ay = fma(dy, s, ay);
-  az = fma(dz, s, az);
-}
-
-// ---------------------------------------------------------------------------
-// FP64-class pair term on the FP32 pipe ("double-float", MODE_DF64).
-// The displacement is an FP64 subtraction (exact for close pairs), split into
-// FP32 (hi, lo) parts.  r^2 is summed as a double-float from exact products
-// (FMA) and TwoSums; r^-3 takes the FP32 seed of its high part and the
-// Newton residual formed in compensated FP32, with y^3 kept as a double-float; the
-// three force products are exact-product double-floats accumulated with
-// TwoSum into a per-tile double-float, flushed into FP64 once per tile.
-// Relative error per pair about 2^-44 (the residual's FP32 roundings).
-
-template <bool QARR>
-__device__ __forceinline__ void pair_df64(double xi, double yi, double zi, const D4 &pj,
-                                          float s2h, float s2l, float ah[3], float al[3]) {
-  float dh[3], dl[3];
-  split_f64(xi - pj.x, dh[0], dl[0]);
-  split_f64(yi - pj.y, dh[1], dl[1]);
-  split_f64(zi - pj.z, dh[2], dl[2]);
-  float sh, sl;
-  df_rinv3(dh, dl, s2h, s2l, sh, sl);
-  if (QARR) {  // times q_j, carried as an FP32 pair in the staged entry's w
-    const float2 q = *reinterpret_cast<const float2 *>(&pj.w);
-    const float ph = sh * q.x;
-    const float pe = fmaf(sh, q.x, -ph);
-    sl = fmaf(sh, q.y, fmaf(sl, q.x, pe));
-    sh = ph;
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float ph = dh[k] * sh;
-    const float pe = fmaf(dh[k], sh, -ph);
-    const float pl = fmaf(dh[k], sl, fmaf(dl[k], sh, pe));
-    float s, t;
-    two_sum_f(ah[k], ph, s, t);
-    ah[k] = s;
-    al[k] += t + pl;
-  }
-}
-
-// Adds a tile's FP32 partial to an FP64 accumulator with TwoSum
-// compensation (the error term is kept in c and added at the end).
-__device__ __forceinline__ void flush_tile(float &af, double &ad, double &c) {
-  double s, e;
-  two_sum(ad, f32_to_f64(af), s, e);
-  ad = s;
-  c += e;
-  af = 0.0f;
-}
 
 // ---------------------------------------------------------------------------
 // Force kernel: part[(jc*3 + c)*n + i] = sum_{j in chunk jc} w_j d_ij^c / s_ij^3.
@@ -481,15 +388,23 @@ struct TuneEntry {
 };
 static std::mutex g_tune_mu;
 static std::vector<TuneEntry> g_tune;
+static uint64_t g_tune_gen = 0;
 
 void tuning_set(int kind, int mode, int64_t n_lo, int64_t n_hi, int block, int R, int bps) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.push_back(TuneEntry{kind, mode, n_lo, n_hi, block, R, bps});
+  ++g_tune_gen;
 }
 
 void tuning_clear() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.clear();
+  ++g_tune_gen;
+}
+
+uint64_t tuning_generation() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune_gen;
 }
 
 bool tuning_lookup(int kind, int mode, int64_t n, int *block, int *R, int *bps) {
@@ -590,12 +505,15 @@ Plan make_plan(int64_t n, int mode, int kind) {
   // about 16 blocks per SM for large n; small n keeps at least 8 warps per SM
   const int64_t target = (int64_t)device_sm_count() * bps;
   int64_t njc = (target + pl.n_it - 1) / pl.n_it;
-  // j-chunks of at least one block of partners; for n < 256 (force kernel)
-  // down to 8 partners, so that enough warps share the pair work: a warp's
-  // FP64 instructions run one after another on a narrow per-SM FP64 unit.
-  // (At n = 1000 chunks that short were slower: too many tiny blocks.)
+  // j-chunks of at least one block of partners; for the force kernel below
+  // n = 8192 down to 8 partners, and below n = 128 down to n/16 partners
+  // (about 16 chunks), so that many warps share the pair work.  At small n
+  // every dependent FP64 instruction costs 64 cycles of latency, so a
+  // thread's chain of partners, not throughput, sets the kernel's time; the
+  // epilogue adds the chunks with a chain of n_jc/8 + 3.
   const int64_t min_tiles = n >= 8192 ? 4 : 1;
-  const int64_t min_chunk = (kind == 0 && n < 256) ? 8 : (int64_t)pl.block;
+  const int64_t min_chunk = (kind == 0 && n < 8192) ? std::min<int64_t>(8, std::max<int64_t>(1, n / 16))
+                                                    : (int64_t)pl.block;
   const int64_t max_jc = std::max<int64_t>(1, n / (min_tiles * min_chunk));
   njc = std::min<int64_t>(std::max<int64_t>(njc, 1), max_jc);
   int64_t chunk = (n + njc - 1) / njc;

@@ -3,11 +3,23 @@
 For each N and precision: the device time of K velocity-Verlet steps through
 nb_step (CUDA events on the launching stream), reported as ms per step, steps
 per second and G pair-interactions per second (N^2 per step).  At small N a
-step is a few short kernels, so the launch latency dominates; the same steps
-are also timed as replays of one captured CUDA graph of a single step, which
-removes the per-launch host cost.  Inputs: uniform seeded clouds in a static
-harmonic trap (a replay repeats the captured step counter, so the trap is
-static and there is no noise).
+step is a few short kernels, so launch latency dominates, and the numbers
+depend on how the steps are issued:
+
+  ms_per_step          one nb_step call of K steps, the library default:
+                       single-block steps for the smallest N (one launch
+                       for the call), else the multi-kernel steps, whose
+                       middle steps are replays of a captured 8-step window
+                       for N <= 4096
+  windows_ms_per_step  the multi-kernel steps with windows (N <= 4096)
+  plain_ms_per_step    the multi-kernel steps without windows (one launch
+                       per kernel, issued from the library's host loop)
+  per_call_ms_per_step K nb_step calls of one step from Python
+  graph_ms_per_step    K replays of one caller-captured graph of one step
+
+Inputs: uniform seeded clouds in a static harmonic trap (a caller's graph
+repeats the captured step counter, so the trap is static and there is no
+noise).
 
     python -m paper_2106_11143_gb300.sweep [--sizes 10,100,1000,10000,100000]
 """
@@ -27,16 +39,40 @@ def _steps(n):
     return 2000 if n <= 1000 else (200 if n <= 10000 else 10)
 
 
-def time_eager(par, sysm, k):
-    api.step(par, sysm, 2)
-    torch.cuda.synchronize()
+def _timed(fn, k):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    for _ in range(k):
-        api.step(par, sysm, 1)
+    fn()
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / k
+
+
+def time_call(par, sysm, k, precision, small=None, windows=None):
+    """One nb_step call of k steps, after one untimed call of the same length;
+    small / windows = True or False force the single-block steps or the step
+    windows on or off, None keeps the library's default."""
+    api.set_tuning("force", "fp64", 0, 0, 0)
+    if small is not None:
+        api.set_tuning("small_steps", precision, 0, 1 << 40, 1, R=int(small))
+    if windows is not None:
+        api.set_tuning("step_windows", precision, 0, 1 << 40, 1, R=int(windows))
+    try:
+        api.step(par, sysm, k)
+        torch.cuda.synchronize()
+        return _timed(lambda: api.step(par, sysm, k), k)
+    finally:
+        api.set_tuning("force", "fp64", 0, 0, 0)
+
+
+def time_per_call(par, sysm, k):
+    api.step(par, sysm, 2)
+    torch.cuda.synchronize()
+
+    def run():
+        for _ in range(k):
+            api.step(par, sysm, 1)
+    return _timed(run, k)
 
 
 def time_graph(par, sysm, k, pos, vel):
@@ -51,13 +87,11 @@ def time_graph(par, sysm, k, pos, vel):
         api.step(par, sysm, 1)
     g.replay()
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(k):
-        g.replay()
-    b.record()
-    torch.cuda.synchronize()
-    return a.elapsed_time(b) / k
+
+    def run():
+        for _ in range(k):
+            g.replay()
+    return _timed(run, k)
 
 
 def sweep(sizes=(10, 100, 1000, 10000, 100000), precisions=PRECISIONS, graphs=True):
@@ -72,9 +106,14 @@ def sweep(sizes=(10, 100, 1000, 10000, 100000), precisions=PRECISIONS, graphs=Tr
             par = api.Params.from_phys(phys, precision=prec)
             sysm = api.System(pos, vel)
             api.forces(par, sysm, total=True)
-            ms = time_eager(par, sysm, k)
+            ms = time_call(par, sysm, k, prec)
             row = {"n": n, "precision": prec, "steps": k, "ms_per_step": round(ms, 5),
                    "steps_per_s": round(1e3 / ms, 1), "G_pairs_per_s": round(n * n / ms / 1e6, 4)}
+            if n <= 4096:
+                row.update(windows_ms_per_step=round(time_call(par, sysm, k, prec, small=False, windows=True), 5))
+            if n <= 10000:
+                pms = time_call(par, sysm, k, prec, small=False, windows=False)
+                row.update(plain_ms_per_step=round(pms, 5), per_call_ms_per_step=round(time_per_call(par, sysm, k), 5))
             if graphs and n <= 10000:
                 gms = time_graph(par, sysm, k, pos, vel)
                 row.update(graph_ms_per_step=round(gms, 5), graph_steps_per_s=round(1e3 / gms, 1),
