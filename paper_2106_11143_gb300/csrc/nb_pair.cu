@@ -485,10 +485,12 @@ Plan make_plan(int64_t n, int mode, int kind) {
   }
   int bps;
   if (kind == 0) {
-    // force kernel: shapes found by the autotuner on GB300 (tune.py)
-    pl.block = n >= 24000 ? 256 : (n >= 3000 ? 128 : 32);
+    // force kernel: shapes measured on GB300 (tune.py and step sweeps).  Below
+    // n = 8192 a target of 8 blocks per SM: more, shorter j-chunks only add
+    // partials for the epilogue once the chunks hold about 30 partners.
+    pl.block = n >= 24000 ? 256 : (n >= 3000 ? 128 : (n >= 1500 ? 64 : 32));
     pl.R = (mode == MODE_SPLIT && n >= 24000) ? 4 : 1;
-    bps = 32;
+    bps = n < 8192 ? 8 : 32;
   } else {
     pl.block = n >= 8192 ? 128 : (n >= 2048 ? 64 : 32);
     pl.R = 1;

@@ -23,7 +23,7 @@ pancake(): the N = 128 radial-plane (2D) crystal of Sec. V, compared the same
            frequency of 2 pi 700 kHz (a single radial plane for 128 ions) and
            the stated Gamma = 1e-21 kg/s.
 
-    python -m paper_2106_11143_gb300.ladder [--steps 5000] [--pancake-steps 880000]
+    python -m paper_2106_11143_gb300.ladder [--steps 5000] [--pancake-steps 880000] [--speed-only]
 """
 import argparse
 import json
@@ -163,9 +163,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--pancake-steps", type=int, default=880000)
     ap.add_argument("--sizes", default="1000,10000,100000")
+    ap.add_argument("--speed-only", action="store_true", help="only the force-evaluation timings")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     sizes = tuple(int(s) for s in a.sizes.split(","))
+    if a.speed_only:
+        print(json.dumps({"speed": speed(sizes)}))
+        return
     print(json.dumps({"speed": speed(sizes), "chain_dbar": chain(steps=a.steps),
                       "pancake_dbar": pancake(steps=a.pancake_steps)}))
 
