@@ -259,7 +259,8 @@ def run_e2e(nb, w, precision, steps, world, flush):
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
 
-SYMMETRIC = {"fp64", "df64", "mixed", "mixed_split"}  # half-pair kernel at N >= 4096
+SYMMETRIC = {"fp64", "df64", "mixed", "mixed_split"}  # half-pair kernel from SYM_FROM[path] ions
+SYM_FROM = {"fp64": 3000, "df64": 3000, "mixed": 2500, "mixed_split": 2500}
 
 # DRAM bytes (read + write) per launch of the pair kernel, from one ncu capture
 # of this bench's command (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass;
@@ -275,11 +276,11 @@ def roofline(path, n, kernel_ms):
     peak = PEAK_TFLOPS[PATH_PEAK[path]]
     r = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
          "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get((path, n)),
-         "kernel": ("k_pair_sym<%s>" if path in SYMMETRIC and n >= 4096 else "k_pair_force<%s>") % path,
+         "kernel": ("k_pair_sym<%s>" if path in SYMMETRIC and n >= SYM_FROM[path] else "k_pair_force<%s>") % path,
          "peak_source": "%s FMA lanes x 2 flops x 152 SMs x 2070 MHz (unit counts and max clock)"
                         % ("2 FP64" if PATH_PEAK[path] == "fp64" else "128 FP32"),
          "convention": "A: 20 flops per pair interaction"}
-    if path in SYMMETRIC and n >= 4096:
+    if path in SYMMETRIC and n >= SYM_FROM[path]:
         r["note"] = ("half-pair kernel: one pair evaluation serves both ions, so convention-A flops "
                      "(20 per interaction) per second can exceed the pipe peak; per-pipe "
                      "utilisation from ncu is in profiles/")

@@ -437,19 +437,21 @@ static double sym_partial_cap() {
 
 Plan make_plan(int64_t n, int mode, int kind) {
   Plan pl;
-  // Symmetric half-pair kernel for the force paths from n = 4096 on, while
-  // the per-partner-block partials (nbk * 3n doubles) fit the cap above.
-  // Block sizes, the fastest measured on GB300 counting the epilogue's reads
-  // of the partials: 128-ion blocks (4 warps) up to n = 32768 (split: 10000),
-  // then 256, and 512 from n = 60000; split uses 512-ion blocks with two
-  // P-ions per lane from n = 10000.
+  // Symmetric half-pair kernel for the force paths, while the
+  // per-partner-block partials (nbk * 3n doubles) fit the cap above.  Block
+  // sizes, the fastest measured on GB300 counting the epilogue's reads of the
+  // partials: 128-ion blocks (4 warps) up to n = 32768, then 256, and 512
+  // from n = 60000; split: 128 below n = 4096, 256 below 8000, then 512-ion
+  // blocks with two P-ions per lane.
   if (kind == 0 && (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || mode == MODE_SPLIT)) {
     int G;
     if (mode == MODE_SPLIT)
-      G = n >= 10000 ? 16 : 4;
+      G = n >= 8000 ? 16 : (n >= 4096 ? 8 : 4);
     else
       G = n >= 60000 ? 16 : (n >= 32768 ? 8 : 4);
-    bool use = n >= 4096;
+    // from n = 3000 (fp64, df64) or 2500 (mixed, split): where it beat the
+    // one-sided kernel in step sweeps on GB300
+    bool use = n >= ((mode == MODE_FP64 || mode == MODE_DF64) ? 3000 : 2500);
     int tb = 0, tr = 0, tbps = 0;
     if (tuning_lookup(4, mode, n, &tb, &tr, &tbps)) {
       use = tr != 0;
@@ -464,11 +466,12 @@ Plan make_plan(int64_t n, int mode, int kind) {
       return pl;
     }
   }
-  // Symmetric VJP kernel from n = 4096 (128-ion blocks below n = 16384, 256
-  // above), under the same cap; tuning kind 5 overrides (R = 0 disables).
+  // Symmetric VJP kernel from n = 2500, where it beat the one-sided kernel
+  // on GB300 (128-ion blocks below n = 16384, 256 above), under the same
+  // cap; tuning kind 5 overrides (R = 0 disables).
   if (kind == 2) {
     int G = n >= 16384 ? 8 : 4;
-    bool use = n >= 4096;
+    bool use = n >= 2500;
     int tb = 0, tr = 0, tbps = 0;
     if (tuning_lookup(5, mode, n, &tb, &tr, &tbps)) {
       use = tr != 0;
