@@ -64,6 +64,9 @@ def parse():
                     help="profiling case: two nb_forces calls per precision at --n, no timing")
     ap.add_argument("--profile-vjp", action="store_true",
                     help="profiling case: two nb_forces_vjp calls at --n, no timing")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="the oracle's force evaluation per N on one core and on all host cores, "
+                         "beside the GPU force evaluation (one JSON line per N)")
     return ap.parse_args()
 
 
@@ -455,9 +458,68 @@ def profile_vjp(args):
     print("profile case done: n=%d" % w["n"])
 
 
+def cpu_sweep(sizes=(10, 100, 1000, 10000, 100000), target_s=2.0):
+    """One force evaluation per N: the FP64 oracle (as it stands) on one host
+    core and on all of them, and the GPU (nb_forces, fp64 and mixed_split;
+    CUDA events around repeated calls from Python, so small N includes the
+    call overhead).  At large N the oracle times ions [0, S) against all N,
+    S sized for about target_s seconds, and the rate is scaled to all N."""
+    import math
+    import torch
+    import oracle
+    import paper_2106_11143_gb300 as nb
+    from paper_2106_11143_gb300 import workloads as W
+    nb.lib()
+    cores = oracle.get_threads()
+    for n in sizes:
+        c = 4e-6 * (n / (4.0 / 3.0 * math.pi * 25.0)) ** (1.0 / 3.0)  # about 4 um spacing
+        pos, _ = W.random_cloud(n, seed=21, semi_axes=(c, c, 5 * c))
+        phys = W.phys(omega=(2 * math.pi * 1e6, 2 * math.pi * 1e6, 2 * math.pi * 200e3))
+        p = oracle.make_params(**phys)
+        row = {"n": n, "pairs": n * n}
+        for k in (1, cores):
+            oracle.set_threads(k)
+            s, reps, dt = min(n, 64), 1, 0.0
+            while True:  # grow the sample (ions, then repetitions) to about target_s
+                t = time.perf_counter()
+                for _ in range(reps):
+                    oracle.coulomb(p, *pos, i0=0, i1=s)
+                dt = time.perf_counter() - t
+                if dt >= target_s or (s == n and reps >= 1 << 20):
+                    break
+                grow = max(2.0, min(16.0, target_s / max(dt, 1e-6)))
+                if s < n:
+                    s = int(min(n, s * grow))
+                else:
+                    reps = int(reps * grow)
+            row["oracle_%dcore_ms" % k] = round(dt / reps * 1e3 * n / s, 6)
+            row["oracle_%dcore_sample" % k] = "%d of %d ions x %d" % (s, n, reps)
+        oracle.set_threads(cores)
+        for prec in ("fp64", "mixed_split"):
+            par = nb.Params.from_phys(phys, precision=prec)
+            sysm = nb.System(pos)
+            for _ in range(3):
+                nb.forces(par, sysm)
+            torch.cuda.synchronize()
+            reps = 2000 if n <= 10000 else 20
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                nb.forces(par, sysm)
+            b.record()
+            torch.cuda.synchronize()
+            row["gpu_%s_ms" % prec] = round(a.elapsed_time(b) / reps, 6)
+        nb.sync_status()
+        row["cores"] = cores
+        row["gpu_fp64_over_oracle_allcores"] = round(row["oracle_%dcore_ms" % cores] / row["gpu_fp64_ms"], 1)
+        print(json.dumps(row), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.profile_vjp:
+    if a.cpu_sweep:
+        cpu_sweep()
+    elif a.profile_vjp:
         profile_vjp(a)
     elif a.profile_forces:
         profile_forces(a)
