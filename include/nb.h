@@ -282,8 +282,10 @@ nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n
  * (energies as in nb_energy; the squared distance in m^2, added as plain
  * numbers), and its exact gradient with respect to x_0, v_0 and the three
  * trap frequencies by the discrete adjoint (reverse sweep) of the Verlet
- * map.  Supported: static harmonic trap, gamma = 0, noise_T = 0, FP64 pair
- * arithmetic (NB_ENOTSUP otherwise).  The forward stores the state (x, v, a)
+ * map.  Supported: static harmonic trap, gamma = 0, noise_T = 0, and the
+ * NB_FP64 or NB_DF64 force arithmetic for the forward and its recompute
+ * (NB_ENOTSUP otherwise); the Jacobian products are FP64 (nb_forces_vjp's
+ * arithmetic) in both cases.  The forward stores the state (x, v, a)
  * at steps 0, every, 2*every, ... in `ckpt`; the backward recomputes each
  * segment from its checkpoint (bitwise identical to the forward) and sweeps
  * it in reverse, so the result does not depend on `every`. */

@@ -29,8 +29,10 @@ class TrajectoryLoss(torch.autograd.Function):
         v0 = v0.detach().to(torch.float64).contiguous()
         target = target.detach().to(device=dev, dtype=torch.float64).contiguous()
         n = x0.shape[1]
+        # the force arithmetic of the forward and its recompute: df64 if asked, else fp64
+        prec = "df64" if params.precision == "df64" else "fp64"
         par = dataclasses.replace(params, omega=tuple(float(w) for w in omega.detach().cpu().tolist()),
-                                  precision="fp64")
+                                  precision=prec)
         sysm = api.System(x0, v0)
         L = api.lib()
         nck = L.nb_traj_ckpt_doubles(n, int(nsteps), int(every))

@@ -697,7 +697,8 @@ nb_status check_adjoint(const nb_params *p) {
   if (p->trap != NB_TRAP_HARMONIC || p->gamma != 0.0 || p->noise_T != 0.0 ||
       p->omega_rate[0] != 0.0 || p->omega_rate[1] != 0.0 || p->omega_rate[2] != 0.0)
     return fail(NB_ENOTSUP, "the trajectory adjoint supports the static harmonic trap without friction or noise");
-  if (p->precision != NB_FP64) return fail(NB_ENOTSUP, "the trajectory adjoint is FP64 only");
+  if (p->precision != NB_FP64 && p->precision != NB_DF64)
+    return fail(NB_ENOTSUP, "the trajectory adjoint takes NB_FP64 or NB_DF64 force arithmetic");
   if (!(p->dt > 0.0)) return fail(NB_EINVAL, "dt must be > 0");
   return NB_OK;
 }
@@ -774,7 +775,8 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
   NB_TRY(check_array(gomega, "gomega"));
   if (gscale && !aligned8(gscale)) return fail(NB_EINVAL, "gscale is not 8-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
-  const Plan pl = make_plan(n, MODE_FP64, 0);
+  const int mode = params->precision;  // the forward's force arithmetic, for the recompute
+  const Plan pl = make_plan(n, mode, 0);
   const Plan plv = make_plan(n, MODE_FP64, 2);
   const int64_t S = n_segments(nsteps, every);
   const int64_t slots = std::min(every, std::max<int64_t>(nsteps, 1)) + 2;
@@ -825,7 +827,7 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
       count_launches(1);
       for (int64_t m = 0; m < len; ++m) {
         const auto P = slot(m + 1), Nx = slot(m + 2);
-        NB_CUDA_TRY(launch_pair_force(pl, MODE_FP64, n, P[0], P[1], P[2], sys->q, nopf, params->soft2, fpart, st));
+        NB_CUDA_TRY(launch_pair_force(pl, mode, n, P[0], P[1], P[2], sys->q, nopf, params->soft2, fpart, st));
         NB_CUDA_TRY(launch_epi_step(p, sv, P[0], P[1], P[2], fpart, pl.n_jc, start + m + 1, Nx[0], Nx[1], Nx[2],
                                     a->err, st));
         count_launches(2);

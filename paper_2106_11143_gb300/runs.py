@@ -13,7 +13,8 @@ device times (CUDA events) and the quantities a user of each would look at.
                          the friction damps that over the full run.
   adjoint-cloud-N4096    trajectory loss and its gradient with respect to the
                          initial positions and the three trap frequencies
-                         (checkpoints every 100 steps)
+                         (checkpoints every 100 steps), with the forward in
+                         fp64 and in df64
 
     python -m paper_2106_11143_gb300.runs [--kz-steps 200]
 """
@@ -99,10 +100,12 @@ def kz(nsteps=200, chunk=200):
             "max_radial_um": round(float(np.max(np.hypot(x[0], x[1]))) * 1e6, 3)}
 
 
-def adjoint():
+def adjoint(precision="fp64"):
+    """The adjoint workload with the forward (and its recompute) in `precision`
+    (fp64 or df64); the Jacobian products are FP64 either way."""
     from .autograd import trajectory_loss
     w = W.adjoint_cloud()
-    par = api.Params.from_phys(w["phys"])
+    par = api.Params.from_phys(w["phys"], precision=precision)
     x0 = torch.tensor(w["pos"], device="cuda", requires_grad=True)
     v0 = torch.tensor(w["vel"], device="cuda", requires_grad=True)
     om = torch.tensor(w["phys"]["omega"], dtype=torch.float64, device="cuda", requires_grad=True)
@@ -115,7 +118,7 @@ def adjoint():
     loss.backward()
     c.record()
     torch.cuda.synchronize()
-    return {"workload": w["name"], "n": w["n"], "steps": w["steps"], "checkpoint_every": 100,
+    return {"workload": w["name"], "precision": precision, "n": w["n"], "steps": w["steps"], "checkpoint_every": 100,
             "forward_s": round(a.elapsed_time(b) / 1e3, 3), "backward_s": round(b.elapsed_time(c) / 1e3, 3),
             "loss": float(loss.item()), "grad_omega": [float(g) for g in om.grad.cpu()],
             "grad_x0_max_abs": float(x0.grad.abs().max().item())}
@@ -131,6 +134,7 @@ def main():
     rows += large_cloud()
     rows.append(kz(args.kz_steps))
     rows.append(adjoint())
+    rows.append(adjoint("df64"))
     for r in rows:
         print(json.dumps(r))
 

@@ -32,8 +32,8 @@ def small_problem(n=48, seed=21):
     return x0, v0, target, phys
 
 
-def gpu_grad(nb, x0, v0, target, phys, nsteps, every, gscale=1.0):
-    par = nb.Params.from_phys(phys)
+def gpu_grad(nb, x0, v0, target, phys, nsteps, every, gscale=1.0, precision="fp64"):
+    par = nb.Params.from_phys(phys, precision=precision)
     X0 = torch.tensor(x0, device="cuda", requires_grad=True)
     V0 = torch.tensor(v0, device="cuda", requires_grad=True)
     Wt = torch.tensor(phys["omega"], dtype=torch.float64, device="cuda", requires_grad=True)
@@ -44,10 +44,14 @@ def gpu_grad(nb, x0, v0, target, phys, nsteps, every, gscale=1.0):
     return loss.item(), X0.grad.cpu().numpy(), V0.grad.cpu().numpy(), Wt.grad.cpu().numpy()
 
 
-def test_loss_and_gradient_match_oracle(nb, orc):
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_loss_and_gradient_match_oracle(nb, orc, precision):
+    """The loss and all three gradients against the oracle's discrete adjoint,
+    within 10x the oracle's own sensitivity to a one-ulp change of x0, with
+    the forward and its recompute in FP64 or in double-float arithmetic."""
     x0, v0, target, phys = small_problem()
     nsteps, every = 150, 37
-    loss, gx, gv, gw = gpu_grad(nb, x0, v0, target, phys, nsteps, every)
+    loss, gx, gv, gw = gpu_grad(nb, x0, v0, target, phys, nsteps, every, precision=precision)
     p = orc.make_params(**phys)
     lr, gxr, gvr, gwr = orc.trajectory_grad(p, x0, v0, nsteps, target)
     lu, gxu, gvu, gwu = orc.trajectory_grad(p, x0 * (1 + 2.0 ** -52), v0, nsteps, target)
@@ -61,11 +65,16 @@ def test_loss_and_gradient_match_oracle(nb, orc):
         assert d <= 10 * self_d + 1e-11 * scale, name
 
 
-def test_gradient_independent_of_checkpoint_interval(nb):
-    x0, v0, target, phys = small_problem(n=100, seed=3)
-    ref = gpu_grad(nb, x0, v0, target, phys, 60, 60)
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+@pytest.mark.parametrize("n", [100, 3100])
+def test_gradient_independent_of_checkpoint_interval(nb, precision, n):
+    """Bitwise the same loss and gradients for every checkpoint interval: the
+    recompute reproduces the forward exactly, through the step windows and the
+    single-block path (n = 100) and the symmetric kernels (n = 3100)."""
+    x0, v0, target, phys = small_problem(n=n, seed=3)
+    ref = gpu_grad(nb, x0, v0, target, phys, 60, 60, precision=precision)
     for every in (1, 7, 25, 1000):
-        r = gpu_grad(nb, x0, v0, target, phys, 60, every)
+        r = gpu_grad(nb, x0, v0, target, phys, 60, every, precision=precision)
         assert r[0] == ref[0]
         for a, b in zip(r[1:], ref[1:]):
             assert np.array_equal(a, b), every
