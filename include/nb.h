@@ -212,10 +212,17 @@ nb_status nb_energy(const nb_params *params, const nb_system *sys,
  *   d = r_i - r_j, dl = lam_i - lam_j, s^2 = |d|^2 + soft2,
  * plus, with NB_ACC_TOTAL, the trap's diagonal term at the current time.
  * The Jacobian is symmetric, so this is also the Jacobian-vector product.
- * lam* and g* are device SoA arrays of n doubles.  FP64 differences and
- * accumulation; each pair's term (with its r^-3, r^-5 and d . dl) is formed
- * in exponent-scaled double-float on the FP32 pipe and widened to FP64
- * (relative error about 2^-44 of the term).                              */
+ * lam* and g* are device SoA arrays of n doubles.  FP64 differences d and
+ * dl.  Each pair's term (with its r^-3, r^-5 and d . dl) is formed in
+ * double-float on the FP32 pipe (relative error about 2^-44 of the term):
+ *  - params->precision == NB_DF64: in units fixed for the call (positions
+ *    and sqrt(soft2) by 2^-sc, cotangents by 2^-se, from the largest
+ *    exponents over all ions, found by a pre-pass on the stream), summed in
+ *    double-float over tiles of partners and widened to FP64 once per tile.
+ *    1/r in those units is capped at 2^25: pairs closer than 2^-25 of the
+ *    position unit take the seed terms at that distance.
+ *  - otherwise: in units of each pair's own exponents, widened to FP64 per
+ *    pair and accumulated in FP64.                                         */
 nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys,
                         const double *lx, const double *ly, const double *lz,
                         double *gx, double *gy, double *gz, int flags,
@@ -283,9 +290,9 @@ nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n
  * numbers), and its exact gradient with respect to x_0, v_0 and the three
  * trap frequencies by the discrete adjoint (reverse sweep) of the Verlet
  * map.  Supported: static harmonic trap, gamma = 0, noise_T = 0, and the
- * NB_FP64 or NB_DF64 force arithmetic for the forward and its recompute
- * (NB_ENOTSUP otherwise); the Jacobian products are FP64 (nb_forces_vjp's
- * arithmetic) in both cases.  The forward stores the state (x, v, a)
+ * NB_FP64 or NB_DF64 arithmetic for the forward, its recompute and the
+ * Jacobian products (as nb_forces and nb_forces_vjp in that precision;
+ * NB_ENOTSUP otherwise).  The forward stores the state (x, v, a)
  * at steps 0, every, 2*every, ... in `ckpt`; the backward recomputes each
  * segment from its checkpoint (bitwise identical to the forward) and sweeps
  * it in reverse, so the result does not depend on `every`. */

@@ -376,6 +376,112 @@ __device__ __forceinline__ void vjp_term_fp64(double dx, double dy, double dz, d
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float VJP (NB_DF64).  vjp_term_fp64 scales each pair by its own
+// exponents, so its double-float T of different pairs have different units
+// and are widened to FP64 one by one.  Here the units are fixed for a whole
+// call: positions (and sqrt(soft2)) scaled by 2^-sc and cotangents by 2^-se,
+// with sc and se from the largest exponents over all ions (k_vjp_scales), so
+// that |d| 2^-sc < 2 and |dl| 2^-se < 2.  Every T' = T 2^(3 sc - se) is then
+// in one unit, and a thread sums them on the FP32 pipe (df_acc) and widens
+// the sum once per tile.
+
+// 1/r in the fixed unit is capped at 2^25, so that y^5 stays below 2^125:
+// pairs closer than 2^-25 of the position unit take the uncorrected seed
+// terms at that distance.
+constexpr float VJP_YMAX = 33554432.0f;  // 2^25
+
+// sc from the largest biased exponent e of the position components (and of
+// sqrt(soft2)), se from that of the cotangent components: |x| < 2^(e - 1022),
+// so differences stay below 2^(e - 1021).
+__device__ __forceinline__ int vjp_pos_scale(int epos, double soft2) {
+  const int e2 = (__double2hiint(soft2) >> 20) & 0x7ff;
+  const int es2 = e2 ? ((e2 - 1023) >> 1) + 1023 : 0;
+  return max(epos, es2) - 1021;
+}
+__device__ __forceinline__ int vjp_lam_scale(int elam) { return elam - 1021; }
+
+// TwoSum accumulation of a double-float term into a double-float sum.
+__device__ __forceinline__ void df_acc(float &ah, float &al, float bh, float bl) {
+  float s, e;
+  two_sum_f(ah, bh, s, e);
+  ah = s;
+  al += e + bl;
+}
+
+// The VJP term T = dl r^-3 - 3 (d . dl) r^-5 d of vjp_term_fp64 in the fixed
+// units (th + tl = T 2^(3 sc - se)); 0 when d = 0 without softening.
+__device__ __forceinline__ void vjp_term_df(double dx, double dy, double dz, double lx, double ly,
+                                            double lz, double soft2, int sc, int se, float th[3],
+                                            float tl[3]) {
+  const int ex = (__double2hiint(dx) >> 20) & 0x7ff;
+  const int ey = (__double2hiint(dy) >> 20) & 0x7ff;
+  const int ez = (__double2hiint(dz) >> 20) & 0x7ff;
+  const bool e2 = soft2 != 0.0;
+  const bool live = (ex | ey | ez) != 0 || e2;
+  float dh[3], dl[3], eh[3], el[3], s2h = 0.0f, s2l = 0.0f;
+  split_f64_scaled(dx, sc, dh[0], dl[0]);
+  split_f64_scaled(dy, sc, dh[1], dl[1]);
+  split_f64_scaled(dz, sc, dh[2], dl[2]);
+  split_f64_scaled(lx, se, eh[0], el[0]);
+  split_f64_scaled(ly, se, eh[1], el[1]);
+  split_f64_scaled(lz, se, eh[2], el[2]);
+  if (e2) split_f64_scaled(soft2, 2 * sc, s2h, s2l);
+  const float p0 = dh[0] * dh[0], p1 = dh[1] * dh[1], p2 = dh[2] * dh[2];
+  const float q0 = fmaf(dh[0], dh[0], -p0), q1 = fmaf(dh[1], dh[1], -p1), q2 = fmaf(dh[2], dh[2], -p2);
+  float h, t1, t2;
+  two_sum_f(p0, p1, h, t1);
+  two_sum_f(h, p2, h, t2);
+  float l = (t1 + t2) + (q0 + q1 + q2);
+  l = fmaf(dh[0] + dh[0], dl[0], l);
+  l = fmaf(dh[1] + dh[1], dl[1], l);
+  l = fmaf(dh[2] + dh[2], dl[2], l);
+  if (e2) {
+    float t3;
+    two_sum_f(h, s2h, h, t3);
+    l += t3 + s2l;
+  }
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(h));
+  const bool capped = !(y <= VJP_YMAX);  // also for h = 0 (y = inf)
+  y = capped ? VJP_YMAX : y;
+  const float y2 = y * y;
+  const float y2e = fmaf(y, y, -y2);
+  float r = fmaf(-h, y2, 1.0f);
+  r = fmaf(-h, y2e, r);
+  r = fmaf(-l, y2, r);
+  r = capped ? 0.0f : r;
+  const float c3 = r * fmaf(r, 1.875f, 1.5f);
+  const float c5 = r * fmaf(r, 4.375f, 2.5f);
+  const float y3h = y2 * y;
+  float y3e = fmaf(y2, y, -y3h);
+  y3e = fmaf(y2e, y, y3e);
+  const float y5h = y3h * y2;
+  float y5e = fmaf(y3h, y2, -y5h);
+  y5e = fmaf(y3h, y2e, fmaf(y3e, y2, y5e));
+  const float s3h = y3h, s3l = fmaf(y3h, c3, y3e);
+  const float s5h = y5h, s5l = fmaf(y5h, c5, y5e);
+  float dth, dtl, ph, pl;
+  dfmul(dh[0], dl[0], eh[0], el[0], dth, dtl);
+  dfmul(dh[1], dl[1], eh[1], el[1], ph, pl);
+  dfadd(dth, dtl, ph, pl, dth, dtl);
+  dfmul(dh[2], dl[2], eh[2], el[2], ph, pl);
+  dfadd(dth, dtl, ph, pl, dth, dtl);
+  float wh, wl;
+  dfmul(dth, dtl, s5h, s5l, wh, wl);
+  const float w3h = 3.0f * wh;
+  const float w3l = fmaf(3.0f, wh, -w3h) + 3.0f * wl;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float uh, ul, vh, vl;
+    dfmul(eh[k], el[k], s3h, s3l, uh, ul);
+    dfmul(dh[k], dl[k], w3h, w3l, vh, vl);
+    dfadd(uh, ul, -vh, -vl, th[k], tl[k]);
+    th[k] = live ? th[k] : 0.0f;
+    tl[k] = live ? tl[k] : 0.0f;
+  }
+}
+
 // FP32 bulk shared by the two mixed modes: given the FP32 displacement,
 // acc += w_j d / s^3 with s^-3 = y^3 (1 + 3/2 e), y = MUFU.RSQ(s^2),
 // e = 1 - s^2 y^2 (one first-order correction in FP32).
@@ -502,10 +608,17 @@ cudaError_t launch_pair_force(const Plan &pl, int mode, int64_t n, const double 
 cudaError_t launch_pair_phi(const Plan &pl, int64_t n, const double *x, const double *y,
                             const double *z, const double *q, double charge, double soft2,
                             double *part, cudaStream_t st);
+// VJP pair kernels: FP64 (vjp_term_fp64) or, with df, the double-float form
+// in the fixed units of `scales` (two ints written by launch_vjp_scales).
 cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const double *y,
                             const double *z, const double *q, const double *lx,
                             const double *ly, const double *lz, double soft2, double *part,
-                            cudaStream_t st);
+                            cudaStream_t st, bool df = false, const int *scales = nullptr);
+// The largest biased exponents of the position and cotangent components
+// (scales[0], scales[1]); zeroes them first, on `st`.
+cudaError_t launch_vjp_scales(int64_t n, const double *x, const double *y, const double *z,
+                              const double *lx, const double *ly, const double *lz, int *scales,
+                              cudaStream_t st);
 cudaError_t launch_split_positions(int64_t n, const double *x, const double *y,
                                    const double *z, float *out6, cudaStream_t st);
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
@@ -513,7 +626,8 @@ cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x
                             double *part, cudaStream_t st);
 cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const double *y,
                            const double *z, const double *q, const double *lx, const double *ly,
-                           const double *lz, double soft2, double *part, cudaStream_t st);
+                           const double *lz, double soft2, double *part, cudaStream_t st, bool df,
+                           const int *scales);
 
 // Epilogue kernels (nb_integrate.cu).
 struct StateView {

@@ -17,6 +17,13 @@
 //
 // Four warps per block and 128-ion blocks at n < 16384 give enough items to
 // fill the GPU at the adjoint's sizes (528 items at n = 4096).
+//
+// DF (NB_DF64): the terms are vjp_term_df's double-floats in the call's
+// fixed units, summed on the FP32 pipe per 32-partner tile (the rotating Q
+// sums as six floats instead of three doubles) and widened into the FP64
+// accumulators once per tile, which takes the per-pair FP64 work from 15 to
+// the 6 differences.  Padding ions sit at the origin with weight 0, so their
+// terms are finite and vanish.
 #include <mutex>
 
 #include "nb_common.cuh"
@@ -54,10 +61,36 @@ __device__ __forceinline__ void vjp_eval(const VD8 &p, const VD8 &q, double soft
   }
 }
 
-// Staged entry i of a block (g = global index); ions past n are weight-0,
-// lam-0 dummies far away.  dup: the Q-side layout, each 32-ion tile stored
-// twice back to back.
-template <bool QARR>
+// The same in double-float: (ah, al) += w_q T', (bh, bl) -= w_p T', with the
+// weights carried as FP32 (hi, lo) pairs in w.
+template <bool W>
+__device__ __forceinline__ void vjp_eval_df(const VD8 &p, const VD8 &q, double soft2, int sc, int se,
+                                            float ah[3], float al[3], float bh[3], float bl[3]) {
+  float th[3], tl[3];
+  vjp_term_df(p.x - q.x, p.y - q.y, p.z - q.z, p.lx - q.lx, p.ly - q.ly, p.lz - q.lz, soft2, sc, se, th, tl);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (W) {
+      const float2 wq = *reinterpret_cast<const float2 *>(&q.w);
+      const float2 wp = *reinterpret_cast<const float2 *>(&p.w);
+      float uh, ul;
+      dfmul(th[c], tl[c], wq.x, wq.y, uh, ul);
+      df_acc(ah[c], al[c], uh, ul);
+      dfmul(th[c], tl[c], wp.x, wp.y, uh, ul);
+      df_acc(bh[c], bl[c], -uh, -ul);
+    } else {
+      df_acc(ah[c], al[c], th[c], tl[c]);
+      df_acc(bh[c], bl[c], -th[c], -tl[c]);
+    }
+  }
+}
+
+// Staged entry i of a block (g = global index).  Ions past n are weight-0,
+// lam-0 dummies: far away for the FP64 term (whose scaling is per pair), at
+// the origin for the double-float one (inside its fixed position unit).  DF
+// carries the weight as an FP32 (hi, lo) pair.  dup: the Q-side layout, each
+// 32-ion tile stored twice back to back.
+template <bool QARR, bool DF>
 __device__ __forceinline__ void vjp_stage(VD8 *dst, int i, int64_t g, int64_t n, const double *x,
                                           const double *y, const double *z, const double *q,
                                           const double *lx, const double *ly, const double *lz,
@@ -71,9 +104,14 @@ __device__ __forceinline__ void vjp_stage(VD8 *dst, int i, int64_t g, int64_t n,
     e.lx = lx[g];
     e.ly = ly[g];
     e.lz = lz[g];
+    if (DF) {
+      float wh = 1.0f, wl = 0.0f;
+      if (QARR) split_f64(q[g], wh, wl);
+      *reinterpret_cast<float2 *>(&e.w) = make_float2(wh, wl);
+    }
   } else {
-    e.x = e.y = e.z = VJP_FAR;
-    e.w = 0.0;
+    e.x = e.y = e.z = DF ? 0.0 : VJP_FAR;
+    e.w = 0.0;  // also the FP32 pair (0, 0)
     e.lx = e.ly = e.lz = 0.0;
   }
   e.pad = 0.0;
@@ -86,7 +124,7 @@ __device__ __forceinline__ void vjp_stage(VD8 *dst, int i, int64_t g, int64_t n,
   }
 }
 
-template <bool QARR>
+template <bool QARR, bool DF>
 __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ y,
@@ -95,6 +133,7 @@ __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, 
                                                          const double *__restrict__ lx,
                                                          const double *__restrict__ ly,
                                                          const double *__restrict__ lz, double soft2,
+                                                         const int *__restrict__ scales,
                                                          double *__restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int BI = 32 * G;
@@ -110,9 +149,15 @@ __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, 
   const int64_t p0 = (int64_t)P * BI, q0 = (int64_t)Q * BI;
   const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int sc = 0, se = 0, out = 0;
+  if (DF) {
+    sc = vjp_pos_scale(scales[0], soft2);
+    se = vjp_lam_scale(scales[1]);
+    out = se - 3 * sc;
+  }
   for (int i = tid; i < BI; i += VJP_THREADS) {
-    vjp_stage<QARR>(posP, i, p0 + i, n, x, y, z, q, lx, ly, lz, false);
-    if (P != Q) vjp_stage<QARR>(posQ, i, q0 + i, n, x, y, z, q, lx, ly, lz, true);
+    vjp_stage<QARR, DF>(posP, i, p0 + i, n, x, y, z, q, lx, ly, lz, false);
+    if (P != Q) vjp_stage<QARR, DF>(posQ, i, q0 + i, n, x, y, z, q, lx, ly, lz, true);
     accP[i] = 0.0;
     accP[BI + i] = 0.0;
     accP[2 * BI + i] = 0.0;
@@ -123,7 +168,17 @@ __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, 
     for (int i = tid; i < np; i += VJP_THREADS) {
       const VD8 pi = posP[i];
       double a[3] = {0.0, 0.0, 0.0}, dummy[3];
-      for (int j = 0; j < np; ++j) vjp_eval<QARR>(pi, posP[j], soft2, a, dummy);
+      if (DF) {
+        for (int j0 = 0; j0 < np; j0 += 32) {  // tiles of 32 partners, as off the diagonal
+          float ah[3] = {0.0f, 0.0f, 0.0f}, al[3] = {0.0f, 0.0f, 0.0f};
+          float bh[3] = {0.0f, 0.0f, 0.0f}, bl[3] = {0.0f, 0.0f, 0.0f};  // not used
+          for (int j = j0; j < min(np, j0 + 32); ++j) vjp_eval_df<QARR>(pi, posP[j], soft2, sc, se, ah, al, bh, bl);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) a[c] += f32_to_f64_scaled(ah[c], out) + f32_to_f64_scaled(al[c], out);
+        }
+      } else {
+        for (int j = 0; j < np; ++j) vjp_eval<QARR>(pi, posP[j], soft2, a, dummy);
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + p0 + i] = a[c];
     }
@@ -140,7 +195,36 @@ __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, 
       const int ip = pt * 32 + lane;
       const VD8 pp = posP[ip];
       double a[3] = {0.0, 0.0, 0.0}, b[3] = {0.0, 0.0, 0.0};
-      if (weighted) {
+      if (DF) {
+        float ah[3] = {0.0f, 0.0f, 0.0f}, al[3] = {0.0f, 0.0f, 0.0f};
+        float bh[3] = {0.0f, 0.0f, 0.0f}, bl[3] = {0.0f, 0.0f, 0.0f};
+        if (weighted) {
+#pragma unroll 2
+          for (int r = 0; r < 32; ++r) {
+            vjp_eval_df<true>(pp, qd[r], soft2, sc, se, ah, al, bh, bl);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              bh[c] = __shfl_sync(0xffffffffu, bh[c], (lane + 1) & 31);
+              bl[c] = __shfl_sync(0xffffffffu, bl[c], (lane + 1) & 31);
+            }
+          }
+        } else {
+#pragma unroll 2
+          for (int r = 0; r < 32; ++r) {
+            vjp_eval_df<false>(pp, qd[r], soft2, sc, se, ah, al, bh, bl);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              bh[c] = __shfl_sync(0xffffffffu, bh[c], (lane + 1) & 31);
+              bl[c] = __shfl_sync(0xffffffffu, bl[c], (lane + 1) & 31);
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          a[c] = f32_to_f64_scaled(ah[c], out) + f32_to_f64_scaled(al[c], out);
+          b[c] = f32_to_f64_scaled(bh[c], out) + f32_to_f64_scaled(bl[c], out);
+        }
+      } else if (weighted) {
 #pragma unroll 2
         for (int r = 0; r < 32; ++r) {
           vjp_eval<true>(pp, qd[r], soft2, a, b);
@@ -178,8 +262,10 @@ static size_t vjp_smem_bytes(int G) { return (size_t)32 * G * (3 * sizeof(VD8) +
 
 cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const double *y,
                            const double *z, const double *q, const double *lx, const double *ly,
-                           const double *lz, double soft2, double *part, cudaStream_t st) {
+                           const double *lz, double soft2, double *part, cudaStream_t st, bool df,
+                           const int *scales) {
   if (G != 4 && G != 8) return cudaErrorInvalidValue;
+  if (df && !scales) return cudaErrorInvalidValue;
   static std::mutex mu;
   static bool done[64] = {false};
   int dev = 0;
@@ -190,19 +276,30 @@ cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const dou
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!done[dev]) {
       const int lim = (int)vjp_smem_bytes(8);
-      e = cudaFuncSetAttribute(k_vjp_sym<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      e = cudaFuncSetAttribute(k_vjp_sym<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_vjp_sym<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        e = cudaFuncSetAttribute(k_vjp_sym<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_vjp_sym<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_vjp_sym<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e != cudaSuccess) return e;
       done[dev] = true;
     }
   }
   const int items = nbk * (nbk + 1) / 2;
   const size_t smem = vjp_smem_bytes(G);
-  if (q)
-    k_vjp_sym<true><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, part);
-  else
-    k_vjp_sym<false><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, part);
+  if (df) {
+    if (q)
+      k_vjp_sym<true, true><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part);
+    else
+      k_vjp_sym<false, true><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part);
+  } else {
+    if (q)
+      k_vjp_sym<true, false><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part);
+    else
+      k_vjp_sym<false, false><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part);
+  }
   return cudaGetLastError();
 }
 

@@ -101,8 +101,8 @@ def kz(nsteps=200, chunk=200):
 
 
 def adjoint(precision="fp64"):
-    """The adjoint workload with the forward (and its recompute) in `precision`
-    (fp64 or df64); the Jacobian products are FP64 either way."""
+    """The adjoint workload with the forward, its recompute and the Jacobian
+    products in `precision` (fp64 or df64)."""
     from .autograd import trajectory_loss
     w = W.adjoint_cloud()
     par = api.Params.from_phys(w["phys"], precision=precision)

@@ -119,7 +119,8 @@ def test_energy_with_softening_and_charges(nb, orc):
     assert np.all(np.abs(e - e_ref) <= 1e-12 * np.abs(e_ref))
 
 
-def test_vjp(nb, orc):
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_vjp(nb, orc, precision):
     rng = np.random.default_rng(5)
     n = 1500
     pos, _ = W.random_cloud(n, seed=5)
@@ -128,17 +129,20 @@ def test_vjp(nb, orc):
     phys = W.phys(omega=(6e6, 5e6, 1.2e6))
     for total in (False, True):
         sysm = nb.System(pos, q=q)
-        g = nb.forces_vjp(nb.Params.from_phys(phys), sysm, lam, total=total).cpu().numpy()
+        g = nb.forces_vjp(nb.Params.from_phys(phys, precision=precision), sysm, lam, total=total).cpu().numpy()
         ref = np.stack(orc.forces_vjp(oparams(orc, phys), 0.0, *pos, *lam, q=q, include_trap=total))
         scale = np.max(np.abs(ref))
         assert np.max(np.abs(g - ref)) <= 1e-11 * scale
 
 
-def test_vjp_symmetric_kernel(nb, orc):
-    """The half-pair VJP kernel (on from n = 4096), forced on at small and
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_vjp_symmetric_kernel(nb, orc, precision):
+    """The half-pair VJP kernel (on from n = 2500), forced on at small and
     ragged sizes with both block sizes, with charges and softening, against the
-    oracle; and against the one-sided VJP kernel at n = 4100."""
+    oracle; and against the one-sided VJP kernel at n = 4100.  df64: the
+    double-float terms summed per tile on the FP32 pipe."""
     rng = np.random.default_rng(6)
+    Pm = lambda phys: nb.Params.from_phys(phys, precision=precision)
     try:
         for k, (n, block) in enumerate([(2, 128), (129, 128), (1000, 128), (1500, 256), (4100, 128)]):
             nb.set_tuning("symmetric_vjp", "fp64", 1, 1 << 40, block, R=1)
@@ -146,17 +150,61 @@ def test_vjp_symmetric_kernel(nb, orc):
             q = W.E_CHARGE * rng.choice([-1.0, 1.0, 2.0], size=n) if k % 2 else None
             lam = rng.standard_normal((3, n))
             phys = W.phys(omega=(6e6, 5e6, 1.2e6), soft2=(0.1e-6) ** 2 if k == 2 else 0.0)
-            g = nb.forces_vjp(nb.Params.from_phys(phys), nb.System(pos, q=q), lam, total=True).cpu().numpy()
+            g = nb.forces_vjp(Pm(phys), nb.System(pos, q=q), lam, total=True).cpu().numpy()
             ref = np.stack(orc.forces_vjp(oparams(orc, phys), 0.0, *pos, *lam, q=q, include_trap=True))
             assert np.max(np.abs(g - ref)) <= 1e-11 * np.max(np.abs(ref)), (n, block)
-            g2 = nb.forces_vjp(nb.Params.from_phys(phys), nb.System(pos, q=q), lam, total=True).cpu().numpy()
+            g2 = nb.forces_vjp(Pm(phys), nb.System(pos, q=q), lam, total=True).cpu().numpy()
             assert np.array_equal(g, g2)
         nb.set_tuning("symmetric_vjp", "fp64", 1, 1 << 40, 128, R=0)
-        one = nb.forces_vjp(nb.Params.from_phys(phys), nb.System(pos, q=q), lam, total=True).cpu().numpy()
+        one = nb.forces_vjp(Pm(phys), nb.System(pos, q=q), lam, total=True).cpu().numpy()
     finally:
         nb.set_tuning("force", "fp64", 0, 0, 0)
     assert not np.array_equal(one, g)  # genuinely the other kernel
     assert np.max(np.abs(one - g)) <= 1e-11 * np.max(np.abs(g))
+
+
+def _vjp_term_bound(pos, lam, q, k_c, mass):
+    """Per ion, a bound on the sum of its VJP term magnitudes:
+    |k_C q_i / m| sum_j |q_j| 4 |lam_i - lam_j| / r_ij^3 (|T| <= 4 |dl| r^-3)."""
+    n = pos.shape[1]
+    out = np.empty(n)
+    for i0 in range(0, n, 512):
+        i1 = min(n, i0 + 512)
+        d = pos[:, i0:i1, None] - pos[:, None, :]
+        r = np.sqrt(np.sum(d * d, axis=0))
+        dl = np.sqrt(np.sum((lam[:, i0:i1, None] - lam[:, None, :]) ** 2, axis=0))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = np.where(r > 0, 4.0 * np.abs(q)[None, :] * dl / r ** 3, 0.0)
+        out[i0:i1] = np.abs(k_c * q[i0:i1] / mass) * np.sum(t, axis=1)
+    return out
+
+
+@pytest.mark.parametrize("n", [1500, 6000])
+def test_vjp_df64_fixed_units(nb, orc, n):
+    """The double-float VJP works in units fixed for the whole call (the
+    largest position and cotangent exponents).  Stress them: a cloud 1 cm off
+    the origin (a position unit far above the spacing), cotangents spread over
+    20 decades, a pair 10 nm apart, charges; the one-sided (n = 1500) and the
+    half-pair (n = 6000) kernels.  Gate per ion: the error against the oracle
+    within 1e-12 of a bound on the sum of the ion's term magnitudes, for
+    fp64 and df64 alike."""
+    rng = np.random.default_rng(n)
+    pos, _ = W.random_cloud(n, seed=n)
+    pos = pos + np.array([[1e-2], [0.0], [-3e-3]])
+    pos[:, 1] = pos[:, 0] + np.array([1e-8, 0.0, 0.0])
+    q = W.E_CHARGE * rng.choice([1.0, 2.0], size=n)
+    lam = rng.standard_normal((3, n)) * 10.0 ** rng.uniform(-10, 10, size=n)
+    phys = W.phys(omega=(6e6, 5e6, 1.2e6))
+    ref = np.stack(orc.forces_vjp(oparams(orc, phys), 0.0, *pos, *lam, q=q))
+    bound = _vjp_term_bound(pos, lam, q, W.K_COULOMB, W.MASS_40U)
+    out = {}
+    for prec in ("fp64", "df64"):
+        out[prec] = nb.forces_vjp(nb.Params.from_phys(phys, precision=prec), nb.System(pos, q=q),
+                                  lam).cpu().numpy()
+        err = np.max(np.sqrt(np.sum((out[prec] - ref) ** 2, axis=0)) / bound)
+        print("%s n=%d: max conditioned error %.3g" % (prec, n, err))
+        assert err <= 1e-12, prec
+    assert not np.array_equal(out["fp64"], out["df64"])
 
 
 def _oracle_traj(orc, phys, pos, vel, nsteps, reverse=False, q=None, eps=0.0):
