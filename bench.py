@@ -443,7 +443,8 @@ def profile_forces(args):
 
 def profile_vjp(args):
     """Small case for ncu: two nb_forces_vjp calls (the adjoint's pair kernel)
-    at --n on the large-cloud distribution with seeded cotangents."""
+    in fp64, then two in df64, at --n on the large-cloud distribution with
+    seeded cotangents."""
     import torch
     torch.cuda.set_device(0)
     import paper_2106_11143_gb300 as nb
@@ -451,9 +452,10 @@ def profile_vjp(args):
     w = W.cloud_large(n=args.n)
     sysm = nb.System(w["pos"], w["vel"])
     lam = np.random.default_rng(1).standard_normal((3, w["n"]))
-    par = nb.Params.from_phys(w["phys"])
-    for _ in range(2):
-        nb.forces_vjp(par, sysm, lam)
+    for prec in ("fp64", "df64"):
+        par = nb.Params.from_phys(w["phys"], precision=prec)
+        for _ in range(2):
+            nb.forces_vjp(par, sysm, lam)
     nb.sync_status()
     print("profile case done: n=%d" % w["n"])
 
