@@ -62,7 +62,7 @@ def build(force=False, verbose=False, extra=()):
         raise RuntimeError("nvcc failed:\n" + "\n".join("%s:\n%s" % f for f in failed))
     if force or procs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-ldl"])  # dlopen for NVTX
         os.replace(tmp, LIB)
     if verbose:
         print("built %s in %.1fs" % (LIB, time.time() - t0))

@@ -428,6 +428,7 @@ extern "C" {
 
 nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi, int flags,
                     void *stream) {
+  NvtxRange range_("nb_forces");
   NB_TRY(check_params(params));
   NB_TRY(check_system(sys, (flags & NB_ACC_TOTAL) != 0, true));
   if (flags & ~NB_ACC_TOTAL) return fail(NB_EINVAL, "unknown flags 0x%x", flags);
@@ -461,6 +462,7 @@ nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi, 
 }
 
 nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void *stream) {
+  NvtxRange range_("nb_step");
   NB_TRY(check_params(params));
   NB_TRY(check_system(sys, true, true));
   if (nsteps < 0) return fail(NB_EINVAL, "nsteps must be >= 0");
@@ -475,6 +477,7 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void 
   const Plan pl = make_plan(n, mode, 0);
   Arena *a = nullptr;
   if (use_small_steps(pl, mode, n)) {
+    NvtxRange sub_("nb_step: single-block steps");
     NB_TRY(get_arena(st, 256, &a));
     const Phys p = to_phys(params);
     const StateView v = to_view(sys);
@@ -520,6 +523,7 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void 
     count_launches(1);
   }
   if (reps > 0) {
+    NvtxRange sub_("nb_step: step windows");
     std::vector<unsigned char> key = window_key(pl, mode, p, v, buf(pre), buf(pre + 1), part, split, a);
     if (!a->sg.exec || a->sg.key != key) {
       NB_TRY(capture_window(a, pl, mode, p, v, buf(pre), buf(pre + 1), part, split, params->soft2));
@@ -538,6 +542,7 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void 
 }
 
 nb_status nb_energy(const nb_params *params, const nb_system *sys, double out[4], void *stream) {
+  NvtxRange range_("nb_energy");
   NB_TRY(check_params(params));
   NB_TRY(check_system(sys, true, false));
   if (!out) return fail(NB_EINVAL, "out is NULL");
@@ -573,6 +578,7 @@ nb_status nb_energy(const nb_params *params, const nb_system *sys, double out[4]
 nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys, const double *lx,
                         const double *ly, const double *lz, double *gx, double *gy, double *gz,
                         int flags, void *stream) {
+  NvtxRange range_("nb_forces_vjp");
   NB_TRY(check_params(params));
   NB_TRY(check_system(sys, false, false));
   if (flags & ~NB_ACC_TOTAL) return fail(NB_EINVAL, "unknown flags 0x%x", flags);
@@ -606,6 +612,7 @@ nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys, const dou
 
 nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t *offsets,
                           nb_system *packed, int64_t nsteps, void *stream) {
+  NvtxRange range_("nb_step_batched");
   NB_TRY(check_params(params));
   NB_TRY(check_system(packed, true, true));
   if (params->precision != NB_FP64 && params->precision != NB_DF64)
@@ -726,6 +733,7 @@ extern "C" int64_t nb_traj_ckpt_doubles(int64_t n, int64_t nsteps, int64_t every
 extern "C" nb_status nb_traj_forward(const nb_params *params, nb_system *sys, int64_t nsteps,
                                      int64_t every, double *ckpt, const double *target, double *loss,
                                      void *stream) {
+  NvtxRange range_("nb_traj_forward");
   NB_TRY(check_adjoint(params));
   NB_TRY(check_system(sys, true, true));
   if (sys->m) return fail(NB_ENOTSUP, "the trajectory adjoint has one species (m must be NULL)");
@@ -769,6 +777,7 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
                                       int64_t every, const double *ckpt, const double *target,
                                       const double *gscale, double *gx0, double *gv0, double *gomega,
                                       void *stream) {
+  NvtxRange range_("nb_traj_backward");
   NB_TRY(check_adjoint(params));
   if (!sys) return fail(NB_EINVAL, "system is NULL");
   if (sys->m) return fail(NB_ENOTSUP, "the trajectory adjoint has one species (m must be NULL)");

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/nb.h"
 
@@ -680,6 +681,16 @@ constexpr int SMALL_SMEM_MAX = 227 * 1024;
 size_t small_smem_bytes(const Plan &pl, int mode, int64_t n);
 cudaError_t launch_small_steps(const Plan &pl, int mode, const Phys &p, const StateView &s,
                                int64_t step0, int64_t nsteps, unsigned *err, cudaStream_t st);
+
+// An NVTX range over an ABI call, so that timeline tools (nsys, ncu --nvtx)
+// can attribute kernels to the call that launched them.  Header-only NVTX 3:
+// without an attached tool a push or pop is a branch on a null pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Launch-shape overrides set by nb_set_tuning (nb_pair.cu); kind 3 is the
 // ensemble kernel (block = threads per CTA).

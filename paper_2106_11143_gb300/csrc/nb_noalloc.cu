@@ -64,6 +64,7 @@ using namespace nb;
 
 extern "C" nb_status nb_energy_noalloc(const nb_params *params, const nb_system *sys,
                                        double out[4], void *stream) {
+  NvtxRange range_("nb_energy_noalloc");
   if (!params || !sys || !out) return NB_EINVAL;
   if (!(params->mass > 0.0) || params->soft2 < 0.0 || params->reserved != 0 ||
       (params->trap != NB_TRAP_HARMONIC && params->trap != NB_TRAP_RF))
