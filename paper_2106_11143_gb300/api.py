@@ -247,6 +247,70 @@ class System:
         return torch.stack([self.ax, self.ay, self.az])
 
 
+CKPT_MAGIC = b"NBCKPT1\n"
+_STATE = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")
+
+
+def save_checkpoint(path, system, params=None):
+    """Write the Verlet state (x, v, a, optional q and m, the step counter) and
+    optionally the parameters to `path`, framework-free: the magic line
+    NBCKPT1, the byte length of a JSON header as a little-endian uint64, the
+    header ({"format", "version", "n", "step", "arrays", "params"}), then
+    each array of `arrays` as n little-endian float64.  The step counter sets
+    t and the noise stream, so a run resumed from the file continues bit for
+    bit (see load_checkpoint)."""
+    import dataclasses
+    import json
+    import struct
+    names = list(_STATE) + [k for k in ("q", "m") if getattr(system, k) is not None]
+    header = {"format": "nb-checkpoint", "version": 1, "n": int(system.n), "step": int(system.step),
+              "arrays": names, "params": None if params is None else dataclasses.asdict(params)}
+    if header["params"] is not None:
+        for k in ("omega", "omega_rate"):
+            header["params"][k] = [float(v) for v in header["params"][k]]
+    hb = json.dumps(header, sort_keys=True).encode()
+    with open(path, "wb") as f:
+        f.write(CKPT_MAGIC)
+        f.write(struct.pack("<Q", len(hb)))
+        f.write(hb)
+        for k in names:
+            a = getattr(system, k).detach().to("cpu", torch.float64).contiguous().numpy()
+            f.write(a.astype("<f8", copy=False).tobytes())
+
+
+def load_checkpoint(path, device="cuda"):
+    """Read a file written by save_checkpoint: returns (System on `device`,
+    Params or None).  Raises ValueError on a malformed file."""
+    import json
+    import struct
+    with open(path, "rb") as f:
+        if f.read(len(CKPT_MAGIC)) != CKPT_MAGIC:
+            raise ValueError("not an nb checkpoint")
+        (hl,) = struct.unpack("<Q", f.read(8))
+        header = json.loads(f.read(hl).decode())
+        if header.get("format") != "nb-checkpoint" or header.get("version") != 1:
+            raise ValueError("unknown checkpoint format or version")
+        n = int(header["n"])
+        names = header["arrays"]
+        if not set(_STATE) <= set(names) or not set(names) <= set(_STATE) | {"q", "m"}:
+            raise ValueError("checkpoint arrays %s" % names)
+        arrays = {}
+        for k in names:
+            b = f.read(8 * n)
+            if len(b) != 8 * n:
+                raise ValueError("checkpoint truncated in array %s" % k)
+            arrays[k] = torch.from_numpy(np.frombuffer(b, dtype="<f8").astype(np.float64))
+        if f.read(1):
+            raise ValueError("trailing bytes after the checkpoint arrays")
+    d = {k: arrays[k] for k in _STATE}
+    d["q"], d["m"], d["step"] = arrays.get("q"), arrays.get("m"), header["step"]
+    system = System.from_state(d, device=device)
+    par = header["params"]
+    if par is not None:
+        par = Params(**{k: (tuple(v) if k in ("omega", "omega_rate") else v) for k, v in par.items()})
+    return system, par
+
+
 def forces(params, system, total=False, want_phi=False, stream=None):
     """nb_forces: write system.ax/ay/az (Coulomb, or the total Verlet-state
     acceleration when total=True).  Returns phi (device tensor) if asked."""

@@ -328,7 +328,8 @@ def test_step_determinism_and_resume(nb):
 
 
 def test_checkpoint_resume_bitwise(nb, tmp_path):
-    """A run checkpointed to a file after 15 steps (System.state_dict) and
+    """A run checkpointed to a file after 15 steps (System.state_dict through
+    torch.save, and save_checkpoint's framework-free file with the params) and
     resumed in a fresh System continues bit for bit as the uninterrupted run:
     RF trap (time from the step counter), friction and Langevin noise (the
     Philox counter includes the step)."""
@@ -343,12 +344,16 @@ def test_checkpoint_resume_bitwise(nb, tmp_path):
     nb.step(par, b, 15)
     nb.sync_status()
     torch.save(b.state_dict(), tmp_path / "ckpt.pt")
+    nb.save_checkpoint(tmp_path / "ckpt.nbck", b, par)
     c = nb.System.from_state(torch.load(tmp_path / "ckpt.pt"))
-    assert c.step == 15
+    d, dpar = nb.load_checkpoint(tmp_path / "ckpt.nbck")  # the framework-free file, with its params
+    assert c.step == 15 and d.step == 15 and dpar == par
     nb.step(par, c, 15)
+    nb.step(dpar, d, 15)
     nb.sync_status()
     for t in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
         assert torch.equal(getattr(a, t), getattr(c, t)), t
+        assert torch.equal(getattr(a, t), getattr(d, t)), t
 
 
 @pytest.mark.parametrize("precision", ALL)

@@ -82,3 +82,38 @@ def test_system_state_round_trip(api, tmp_path):
     assert r.n == 17 and r.step == 41
     for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az", "q", "m"):
         assert torch.equal(getattr(r, k), getattr(s, k)), k
+
+
+def test_checkpoint_file_round_trip(api, tmp_path):
+    """save_checkpoint / load_checkpoint: the framework-free file keeps every
+    array, the step counter and the parameters bit for bit, with and without
+    q, m and params; malformed files raise ValueError."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(4)
+    n = 23
+    s = api.System(rng.standard_normal((3, n)) * 1e-5, rng.standard_normal((3, n)),
+                   q=rng.standard_normal(n), device="cpu", step=(1 << 40) + 3, m=rng.uniform(1, 2, n))
+    s.az.copy_(torch.from_numpy(rng.standard_normal(n)))
+    par = api.Params(k_coulomb=8.9875517923e9, mass=6.6e-26, charge=1.602176634e-19, soft2=1e-18,
+                     trap="rf", precision="df64", omega=(0.1, 2.0 / 3.0, 1e6), omega_rate=(0.0, -1e-3, 7.0),
+                     q_mathieu=0.3, omega_rf=6.283e7, rf_phase=1.0 / 7.0, gamma=1e-20, dt=2e-9,
+                     t0=1e-7, noise_T=5e-4, seed=(1 << 63) + 5, instance=9)
+    path = tmp_path / "state.nbck"
+    api.save_checkpoint(path, s, par)
+    r, p = api.load_checkpoint(path, device="cpu")
+    assert r.n == n and r.step == s.step and p == par
+    for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az", "q", "m"):
+        assert torch.equal(getattr(r, k), getattr(s, k)), k
+    # no charges, masses or params
+    s2 = api.System(rng.standard_normal((3, 5)), device="cpu", step=7)
+    api.save_checkpoint(tmp_path / "b.nbck", s2)
+    r2, p2 = api.load_checkpoint(tmp_path / "b.nbck", device="cpu")
+    assert p2 is None and r2.q is None and r2.m is None and r2.step == 7
+    assert torch.equal(r2.x, s2.x)
+    # malformed files
+    raw = path.read_bytes()
+    for bad in (b"XXXXXXX\n" + raw[8:], raw[:-8], raw + b"\0"):
+        (tmp_path / "bad.nbck").write_bytes(bad)
+        with pytest.raises(ValueError):
+            api.load_checkpoint(tmp_path / "bad.nbck", device="cpu")
