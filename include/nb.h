@@ -185,8 +185,10 @@ nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi,
  * of the multi-kernel steps.
  * Step windows: for larger n up to 4096 and nsteps >= 32 (nb_set_tuning kind 6
  * changes both), the middle steps of the call run as replays of one CUDA
- * graph of 8 steps, captured on a private stream at the first such call and
- * kept while every kernel argument is unchanged; the epilogues then read the
+ * graph of 8 steps, captured on a private stream at the first such call for
+ * a given set of kernel arguments (system arrays, parameters, plan) and kept
+ * for reuse (up to four per stream, the least recently used replaced by a
+ * new capture); the epilogues then read the
  * step index from two counters in the stream's scratch.  The replays run
  * the same kernels on the same data in the same order on `stream`, so the
  * results are bitwise those of plain launches.  They are not used while `stream` is

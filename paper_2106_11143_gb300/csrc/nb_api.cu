@@ -44,14 +44,16 @@ nb_status fail(nb_status s, const char *fmt, ...) {
                   __FILE__, __LINE__);                                                 \
   } while (0)
 
-// A captured two-step window of nb_step, replayed for the middle steps of a
-// long call at small n, and the bytes of every kernel argument it was
-// captured with (it is valid while they are unchanged).
+// A captured window of nb_step (STEP_WINDOW steps), replayed for the middle
+// steps of a long call at small n, and the bytes of every kernel argument it
+// was captured with (it is valid while they are unchanged).
 struct StepGraph {
   std::vector<unsigned char> key;
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels = 0;  // kernel launches per replay
+  uint64_t last = 0;     // the arena's use counter at its last replay
 };
+constexpr size_t STEP_WINDOW_CACHE = 4;  // windows kept per stream (least recently used goes)
 
 // Scratch owned by the library for one (device, stream).
 struct Arena {
@@ -59,8 +61,9 @@ struct Arena {
   size_t cap = 0;
   unsigned *err = nullptr;  // 256 B: device error word at 0, step counters at 64 and 72,
                             // the double-float VJP's two exponents at 128
-  cudaStream_t cap_st = nullptr;  // private stream the step window is captured on
-  StepGraph sg;
+  cudaStream_t cap_st = nullptr;  // private stream the step windows are captured on
+  std::vector<StepGraph> windows;  // at most STEP_WINDOW_CACHE
+  uint64_t uses = 0;
 };
 
 int64_t *step_counters(Arena *a) { return reinterpret_cast<int64_t *>(reinterpret_cast<char *>(a->err) + 64); }
@@ -376,7 +379,7 @@ std::vector<unsigned char> window_key(const Plan &pl, int mode, const Phys &p, c
 // copies c1 to c0, so each replay continues where the previous one ended.
 nb_status capture_window(Arena *a, const Plan &pl, int mode, const Phys &p, const StateView &v,
                          double *const *A, double *const *B, double *part, float *split,
-                         double soft2) {
+                         double soft2, StepGraph *out) {
   if (!a->cap_st) NB_CUDA_TRY(cudaStreamCreateWithFlags(&a->cap_st, cudaStreamNonBlocking));
   cudaStream_t cs = a->cap_st;
   int64_t *c = step_counters(a);
@@ -412,9 +415,37 @@ nb_status capture_window(Arena *a, const Plan &pl, int mode, const Phys &p, cons
   const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
   cudaGraphDestroy(g);
   if (ie != cudaSuccess) return fail(NB_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ie));
-  if (a->sg.exec) cudaGraphExecDestroy(a->sg.exec);  // a pending launch of it still completes
-  a->sg.exec = exec;
-  a->sg.kernels = kernels;
+  out->exec = exec;
+  out->kernels = kernels;
+  return NB_OK;
+}
+
+// The cached window with this key, captured (evicting the least recently
+// used one when the cache is full) if there is none.
+nb_status find_window(Arena *a, std::vector<unsigned char> &key, const Plan &pl, int mode, const Phys &p,
+                      const StateView &v, double *const *A, double *const *B, double *part, float *split,
+                      double soft2, StepGraph **out) {
+  ++a->uses;
+  for (StepGraph &g : a->windows)
+    if (g.key == key) {
+      g.last = a->uses;
+      *out = &g;
+      return NB_OK;
+    }
+  StepGraph fresh;
+  NB_TRY(capture_window(a, pl, mode, p, v, A, B, part, split, soft2, &fresh));
+  fresh.key.swap(key);
+  fresh.last = a->uses;
+  if (a->windows.size() >= STEP_WINDOW_CACHE) {
+    auto lru = std::min_element(a->windows.begin(), a->windows.end(),
+                                [](const StepGraph &x, const StepGraph &y) { return x.last < y.last; });
+    cudaGraphExecDestroy(lru->exec);  // a pending launch of it still completes
+    *lru = std::move(fresh);
+    *out = &*lru;
+  } else {
+    a->windows.push_back(std::move(fresh));
+    *out = &a->windows.back();
+  }
   return NB_OK;
 }
 
@@ -525,12 +556,10 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void 
   if (reps > 0) {
     NvtxRange sub_("nb_step: step windows");
     std::vector<unsigned char> key = window_key(pl, mode, p, v, buf(pre), buf(pre + 1), part, split, a);
-    if (!a->sg.exec || a->sg.key != key) {
-      NB_TRY(capture_window(a, pl, mode, p, v, buf(pre), buf(pre + 1), part, split, params->soft2));
-      a->sg.key.swap(key);
-    }
-    for (int64_t r = 0; r < reps; ++r) NB_CUDA_TRY(cudaGraphLaunch(a->sg.exec, st));
-    count_launches(a->sg.kernels * (uint64_t)reps);
+    StepGraph *wg = nullptr;
+    NB_TRY(find_window(a, key, pl, mode, p, v, buf(pre), buf(pre + 1), part, split, params->soft2, &wg));
+    for (int64_t r = 0; r < reps; ++r) NB_CUDA_TRY(cudaGraphLaunch(wg->exec, st));
+    count_launches(wg->kernels * (uint64_t)reps);
   }
   double **P = buf(nsteps - 1);
   NB_TRY(pair_forces(pl, mode, n, P[0], P[1], P[2], sys->q, params->soft2, part, split, st));
@@ -917,7 +946,8 @@ nb_status nb_release(void) {
   for (auto &kv : g_arenas) {
     if (cudaSetDevice(kv.first.first) != cudaSuccess) { rc = NB_ECUDA; continue; }
     cudaDeviceSynchronize();
-    if (kv.second.sg.exec && cudaGraphExecDestroy(kv.second.sg.exec) != cudaSuccess) rc = NB_ECUDA;
+    for (StepGraph &g : kv.second.windows)
+      if (g.exec && cudaGraphExecDestroy(g.exec) != cudaSuccess) rc = NB_ECUDA;
     if (kv.second.cap_st && cudaStreamDestroy(kv.second.cap_st) != cudaSuccess) rc = NB_ECUDA;
     if (kv.second.buf && cudaFree(kv.second.buf) != cudaSuccess) rc = NB_ECUDA;
     if (kv.second.err && cudaFree(kv.second.err) != cudaSuccess) rc = NB_ECUDA;

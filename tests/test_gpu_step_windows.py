@@ -109,6 +109,35 @@ def test_windows_recapture_on_changed_arguments(nb):
     _equal(pb, wb)
 
 
+def test_window_cache_reuse_and_eviction(nb):
+    """Four systems alternating on one stream keep their four windows (one
+    capture each, no recapture); a fifth evicts the least recently used,
+    which the next call recaptures; every run equals plain launches."""
+    ws = [_setup(nb, 300 + 10 * k, "fp64")[0] for k in range(5)]
+    par = nb.Params.from_phys(dict(ws[0]["phys"], noise_T=0.5e-3))
+
+    def run(windows, order):
+        nb.set_tuning("force", "fp64", 0, 0, 0)
+        nb.set_tuning("small_steps", "fp64", 0, 1 << 40, 1, R=0)
+        if not windows:
+            nb.set_tuning("step_windows", "fp64", 0, 1 << 40, 1, R=0)
+        sys_ = [nb.System(w["pos"], w["vel"]) for w in ws]
+        for s in sys_:
+            nb.forces(par, s, total=True)
+        for k in order:
+            nb.step(par, sys_[k], 33)
+        torch.cuda.synchronize()
+        nb.sync_status()
+        nb.set_tuning("force", "fp64", 0, 0, 0)
+        return sys_
+
+    order = [0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 4, 3]
+    plain = run(False, order)
+    win = run(True, order)
+    for a, b in zip(plain, win):
+        _equal(a, b)
+
+
 def test_windows_on_a_user_stream_and_default_stream(nb):
     w, _, par = _setup(nb, 300, "fp64")
     plain, _ = _run(nb, par, w, [64], False, "fp64")
