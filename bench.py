@@ -64,6 +64,8 @@ def parse():
                     help="profiling case: two nb_forces calls per precision at --n, no timing")
     ap.add_argument("--profile-vjp", action="store_true",
                     help="profiling case: two nb_forces_vjp calls at --n, no timing")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="profiling case: small-n steps (single-block at n = 16, windows at n = 1000)")
     ap.add_argument("--cpu-sweep", action="store_true",
                     help="the oracle's force evaluation per N on one core and on all host cores, "
                          "beside the GPU force evaluation (one JSON line per N)")
@@ -460,6 +462,28 @@ def profile_vjp(args):
     print("profile case done: n=%d" % w["n"])
 
 
+def profile_small(args):
+    """Small case for ncu: fp64 steps of the small-n paths in a static trap.
+    First 200 steps at n = 16 (one launch of the single-block kernel), then
+    40 steps at n = 1000 (drift, 7 plain steps, 4 replays of the 8-step
+    window, the last step: pair kernel and eight-lane epilogue per step)."""
+    import math
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2106_11143_gb300 as nb
+    from paper_2106_11143_gb300 import workloads as W
+    phys = W.phys(omega=(2 * math.pi * 1e6, 2 * math.pi * 1e6, 2 * math.pi * 200e3))
+    par = nb.Params.from_phys(phys)
+    for n, k in ((16, 200), (1000, 40)):
+        c = 4e-6 * (n / (4.0 / 3.0 * math.pi * 25.0)) ** (1.0 / 3.0)
+        pos, vel = W.random_cloud(n, seed=21, semi_axes=(c, c, 5 * c))
+        s = nb.System(pos, vel)
+        nb.forces(par, s, total=True)
+        nb.step(par, s, k)
+    nb.sync_status()
+    print("profile case done")
+
+
 def cpu_sweep(sizes=(10, 100, 1000, 10000, 100000), target_s=2.0):
     """One force evaluation per N: the FP64 oracle (as it stands) on one host
     core and on all of them, and the GPU (nb_forces, fp64 and mixed_split;
@@ -521,6 +545,8 @@ if __name__ == "__main__":
     a = parse()
     if a.cpu_sweep:
         cpu_sweep()
+    elif a.profile_small:
+        profile_small(a)
     elif a.profile_vjp:
         profile_vjp(a)
     elif a.profile_forces:

@@ -176,8 +176,8 @@ nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi,
  * pair-force launch and one epilogue launch (which also performs the next
  * drift), plus the FP32 position split for NB_MIXED_SPLIT; one drift launch
  * per call; no host synchronisation.
- * Small systems: up to n = 48 ions (NB_FP64, NB_DF64, NB_MIXED,
- * NB_MIXED_SPLIT), 32 (NB_FP64_RSQ*) or 16 (NB_FP64_SQRTDIV) -- nb_set_tuning kind 7
+ * Small systems: up to n = 48 ions (NB_DF64), 16 (NB_FP64_SQRTDIV) or 32
+ * (the other precisions) -- nb_set_tuning kind 7
  * changes the bounds, up to 512 ions and 227 KB of shared memory -- the call
  * runs in one thread block: one launch per min(16384, max(64, 2^28/n^2))
  * steps, positions in shared memory, the one-sided plan's pair items and

@@ -318,10 +318,8 @@ int64_t small_steps_per_launch(int64_t n) {
 int64_t small_default_n(int mode) {
   switch (mode) {
     case MODE_SQRTDIV: return 16;  // an FP64 square root and division per pair
-    case MODE_RSQ:
-    case MODE_RSQ_NR1:
-    case MODE_RSQ_NR2: return 32;
-    default: return 48;
+    case MODE_DF64: return 48;     // its pair term runs on the FP32 pipe
+    default: return 32;
   }
 }
 

@@ -151,17 +151,24 @@ __global__ void k_epi_step(Phys p, StateView s, const double *__restrict__ cx,
 // per ion leaves the chunk sum a long chain of dependent loads and adds on a
 // few SMs.  Lane u of an ion's group forms slot_sum3's running sum u (chunks
 // u, u+8, ...), three shuffle levels add the eight in slot_sum3's pairing, so
-// the sum is bitwise the same, and lane 0 completes the ion.
-__global__ void k_epi_step8(Phys p, StateView s, const double *__restrict__ cx,
-                            const double *__restrict__ cy, const double *__restrict__ cz,
-                            const double *__restrict__ part, int n_jc, int64_t soff,
-                            const int64_t *cin, int64_t *cout, int64_t cout_off, double *nx,
-                            double *ny, double *nz, unsigned *err) {
-  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+// the sum is bitwise the same.  The block's 32 sums then go through shared
+// memory to its first warp, which kicks one ion per lane: a warp instruction
+// of the kick's FP64 chain then serves 32 ions, not the 4 group leaders of a
+// warp.  Blocks of EPI8_THREADS threads (32 ions).
+// Ion counts up to which the epilogue runs with eight lanes per ion.
+constexpr int64_t EPI8_MAX_N = 2048;
+constexpr int EPI8_THREADS = 256;
+
+__global__ void __launch_bounds__(EPI8_THREADS)
+    k_epi_step8(Phys p, StateView s, const double *__restrict__ cx, const double *__restrict__ cy,
+                const double *__restrict__ cz, const double *__restrict__ part, int n_jc, int64_t soff,
+                const int64_t *cin, int64_t *cout, int64_t cout_off, double *nx, double *ny, double *nz,
+                unsigned *err) {
+  const int64_t g = ((int64_t)blockIdx.x * EPI8_THREADS + threadIdx.x) >> 3;
   const int u = threadIdx.x & 7;
-  const int64_t i = g < s.n ? g : s.n - 1;  // every lane takes part in the shuffles
+  const int64_t ig = g < s.n ? g : s.n - 1;  // every lane takes part in the shuffles
   double cs[3] = {0.0, 0.0, 0.0};
-  const double *pi = part + i;
+  const double *pi = part + ig;
   for (int jc = u; jc < n_jc; jc += 8) {
     const double *q = pi + (int64_t)jc * 3 * s.n;
     cs[0] += __ldcs(q);
@@ -176,7 +183,19 @@ __global__ void k_epi_step8(Phys p, StateView s, const double *__restrict__ cx,
       if ((u & (2 * d - 1)) == 0) cs[c] = cs[c] + o;
     }
   }
-  if (u != 0 || g >= s.n) return;
+  __shared__ double csum[3][EPI8_THREADS / 8];
+  if (u == 0) {
+    csum[0][threadIdx.x >> 3] = cs[0];
+    csum[1][threadIdx.x >> 3] = cs[1];
+    csum[2][threadIdx.x >> 3] = cs[2];
+  }
+  __syncthreads();
+  if (threadIdx.x >= EPI8_THREADS / 8) return;
+  const int64_t i = (int64_t)blockIdx.x * (EPI8_THREADS / 8) + threadIdx.x;
+  if (i >= s.n) return;
+  cs[0] = csum[0][threadIdx.x];
+  cs[1] = csum[1][threadIdx.x];
+  cs[2] = csum[2][threadIdx.x];
   const int64_t base = cin ? *cin : 0;
   const int64_t snew = base + soff;
   if (cout && i == 0) *cout = base + cout_off;
@@ -196,16 +215,13 @@ __global__ void k_epi_step8(Phys p, StateView s, const double *__restrict__ cx,
   if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
-// Ion counts up to which the epilogue runs with eight lanes per ion.
-constexpr int64_t EPI8_MAX_N = 2048;
-
 cudaError_t launch_epi_step(const Phys &p, const StateView &s, const double *cx, const double *cy,
                             const double *cz, const double *part, int n_jc, int64_t snew,
                             double *nx, double *ny, double *nz, unsigned *err, cudaStream_t st,
                             const int64_t *cin, int64_t *cout, int64_t cout_off) {
   const int T = 256;
   if (s.n <= EPI8_MAX_N)
-    k_epi_step8<<<blocks_for(8 * s.n, T), T, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout, cout_off,
+    k_epi_step8<<<blocks_for(8 * s.n, EPI8_THREADS), EPI8_THREADS, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout, cout_off,
                                                       nx, ny, nz, err);
   else
     k_epi_step<<<blocks_for(s.n, T), T, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout, cout_off,

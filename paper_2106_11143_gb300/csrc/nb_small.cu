@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1)
   if (MODE == MODE_DF64) split_f64(p.soft2, s2h, s2l);
 
   double r[3] = {0.0, 0.0, 0.0}, v[3] = {0.0, 0.0, 0.0}, a[3] = {0.0, 0.0, 0.0};
+  const KickConst kc = kick_consts(p, s, own ? tid : 0);  // once for all the launch's steps
   if (own) {
     v[0] = s.vx[tid]; v[1] = s.vy[tid]; v[2] = s.vz[tid];
     a[0] = s.ax[tid]; a[1] = s.ay[tid]; a[2] = s.az[tid];
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1)
     if (own) {
       double cs[3];
       slot_sum3(n_jc, [&](int jc, int c) { return part[(jc * 3 + c) * n + tid]; }, cs);
-      bad |= verlet_kick(p, s, tid, step0 + st + 1, r, cs, v, a);
+      bad |= verlet_kick_k(p, kc, tid, step0 + st + 1, r, cs, v, a);
       if (st + 1 < nsteps) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) r[c] = verlet_drift(r[c], v[c], a[c], dt);

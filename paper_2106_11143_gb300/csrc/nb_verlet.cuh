@@ -95,46 +95,64 @@ __device__ __forceinline__ double verlet_drift(double r, double v, double a, dou
   return r + v * dt + 0.5 * dt * dt * a;
 }
 
+// The kick's per-ion constants, which depend only on the ion and the
+// parameters: the Coulomb prefactor, the trap scale of its species, the
+// friction factors 1 / (1 + gamma dt/(2 m_i)) and gamma/m_i, and the Langevin
+// amplitude.  Several are FP64 divisions, long dependent chains on GB300, so a
+// kernel that kicks the same ion many times forms them once; the values are
+// the same wherever they are formed.
+struct KickConst {
+  double pref, ts, inv, g, sig;
+};
+__device__ __forceinline__ KickConst kick_consts(const Phys &p, const StateView &s, int64_t i) {
+  KickConst k;
+  k.pref = coulomb_pref(p, s, i);
+  k.ts = trap_scale(p, s, i);
+  const double mi = ion_mass(p, s, i);
+  k.inv = 1.0 / (1.0 + p.gamma * p.dt / (2.0 * mi));
+  k.g = p.gamma / mi;
+  k.sig = p.noise_T > 0.0 ? sqrt(2.0 * p.gamma * KB * p.noise_T * p.dt) / mi : 0.0;
+  return k;
+}
+
 // Kick of ion i at positions r (step index snew, time t0 + snew dt), given
-// its pair sum cs = sum_j w_j (r_i - r_j) / s_ij^3:
+// its pair sum cs = sum_j w_j (r_i - r_j) / s_ij^3 and its constants kc:
 //   a+_cons = k_C q_i/m_i cs + trap(r, t)   (Eq. 1)
 //   v+ = (v + (a + a+_cons) dt/2) * [1 / (1 + gamma dt/(2 m_i))]  [+ Langevin kick]
 //   a+ = a+_cons - (gamma/m_i) v+
 // v and a hold the ion's velocity and acceleration on entry and the new ones
 // on return.  Returns true if any of them is not finite.
-__device__ __forceinline__ bool verlet_kick(const Phys &p, const StateView &s, int64_t i,
-                                            int64_t snew, const double r[3], const double cs[3],
-                                            double v[3], double a[3]) {
+__device__ __forceinline__ bool verlet_kick_k(const Phys &p, const KickConst &kc, int64_t i,
+                                              int64_t snew, const double r[3], const double cs[3],
+                                              double v[3], double a[3]) {
   const double dt = p.dt;
   const double t = p.t0 + (double)snew * dt;
-  const double pref = coulomb_pref(p, s, i);
   double tr[3];
   trap_accel(p, t, r[0], r[1], r[2], tr[0], tr[1], tr[2]);
-  const double ts = trap_scale(p, s, i);
-  tr[0] *= ts;
-  tr[1] *= ts;
-  tr[2] *= ts;
-  const double mi = ion_mass(p, s, i);
-  const double inv = 1.0 / (1.0 + p.gamma * dt / (2.0 * mi));  // one division for the three components
-  const double g = p.gamma / mi;
+  tr[0] *= kc.ts;
+  tr[1] *= kc.ts;
+  tr[2] *= kc.ts;
   double xi[3] = {0.0, 0.0, 0.0};
-  double sig = 0.0;
-  if (p.noise_T > 0.0) {
-    sig = sqrt(2.0 * p.gamma * KB * p.noise_T * dt) / mi;
-    normals3(p.seed, p.instance, snew, i, xi);
-  }
+  if (p.noise_T > 0.0) normals3(p.seed, p.instance, snew, i, xi);
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double ucons = pref * cs[k] + tr[k];
-    double vn = (v[k] + 0.5 * dt * (a[k] + ucons)) * inv;
-    vn += sig * xi[k];
-    const double an = ucons - g * vn;
+    const double ucons = kc.pref * cs[k] + tr[k];
+    double vn = (v[k] + 0.5 * dt * (a[k] + ucons)) * kc.inv;
+    vn += kc.sig * xi[k];
+    const double an = ucons - kc.g * vn;
     v[k] = vn;
     a[k] = an;
     bad |= not_finite(vn) || not_finite(an);
   }
   return bad;
+}
+
+// The kick with its constants formed on the spot.
+__device__ __forceinline__ bool verlet_kick(const Phys &p, const StateView &s, int64_t i,
+                                            int64_t snew, const double r[3], const double cs[3],
+                                            double v[3], double a[3]) {
+  return verlet_kick_k(p, kick_consts(p, s, i), i, snew, r, cs, v, a);
 }
 
 }  // namespace nb
