@@ -265,7 +265,7 @@ def run_e2e(nb, w, precision, steps, world, flush):
 
 
 SYMMETRIC = {"fp64", "df64", "mixed", "mixed_split"}  # half-pair kernel from SYM_FROM[path] ions
-SYM_FROM = {"fp64": 3000, "df64": 3000, "mixed": 2500, "mixed_split": 2500}
+SYM_FROM = {"fp64": 1500, "df64": 2000, "mixed": 1000, "mixed_split": 500}
 
 # DRAM bytes (read + write) per launch of the pair kernel, from one ncu capture
 # of this bench's command (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass;

@@ -267,9 +267,10 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
  * keep its one-sided force phase (by default ensembles whose instances all
  * have at most 4096 ions use the half-pair phase).  For kind 4
  * (the symmetric half-pair force kernel of the four force precisions): `block` ions
- * per block pair unit (128, 256, 512, 1024) and R = 1 to use it or 0 to disable
- * it for that n range (by default it is used from n = 3000 in NB_FP64 and
- * NB_DF64 and from n = 2500 in NB_MIXED and NB_MIXED_SPLIT).  For kind 5
+ * per block pair unit (32, 64, 128, 256, 512, 1024) and R = 1 to use it or 0
+ * to disable it for that n range (by default it is used from n = 500 in
+ * NB_MIXED_SPLIT, 1000 in NB_MIXED, 1500 in NB_FP64 and 2000 in NB_DF64).
+ * For kind 5
  * (the symmetric VJP kernel; `precision` NB_FP64): `block` ions per block
  * pair unit (128 or 256) and R = 1 / 0 to use / disable it (by default it is
  * used from n = 2500).  For kind 6 (step windows of nb_step): R = 1 to
@@ -277,7 +278,8 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
  * they are used for n <= 4096 and nsteps >= 32).  For kind 7 (single-block
  * steps of small systems in nb_step): R = 1 to use them or 0 not to, for n
  * in [n_lo, n_hi] (`block` >= 1, not used; the kernel's own limits still
- * apply).  The latest
+ * apply).  For kind 8 (the step epilogue, every precision; pass NB_FP64):
+ * R = 1 for eight threads per ion (the default), 0 for one.  The latest
  * matching entry wins; block == 0 removes every override.  Results stay
  * deterministic for a fixed shape; different shapes may differ in the last
  * bits (summation order), except kind 3, which is shape-independent.     */

@@ -390,7 +390,7 @@ def plan_batched(offsets, n_bins):
 
 
 KINDS = {"force": 0, "potential": 1, "vjp": 2, "ensemble": 3, "symmetric": 4, "symmetric_vjp": 5,
-         "step_windows": 6, "small_steps": 7}
+         "step_windows": 6, "small_steps": 7, "epilogue_lanes": 8}
 
 
 def set_tuning(kind, precision, n_lo, n_hi, block, R=1, blocks_per_sm=16):

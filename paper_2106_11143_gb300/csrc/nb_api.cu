@@ -698,16 +698,19 @@ nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n
     tuning_clear();
     return NB_OK;
   }
-  if (kind < 0 || kind > 7) return fail(NB_EINVAL, "kind must be 0..7");
+  if (kind < 0 || kind > 8) return fail(NB_EINVAL, "kind must be 0..8");
   if (precision < NB_FP64 || precision > NB_FP64_RSQ_NR2) return fail(NB_EINVAL, "bad precision");
   if (n_lo < 0 || n_hi < n_lo) return fail(NB_EINVAL, "bad n range");
   if (kind == 4) {
-    if (block != 128 && block != 256 && block != 512 && block != 1024)
-      return fail(NB_EINVAL, "symmetric block must be 128, 256, 512 or 1024 ions");
+    if (block != 32 && block != 64 && block != 128 && block != 256 && block != 512 && block != 1024)
+      return fail(NB_EINVAL, "symmetric block must be 32, 64, 128, 256, 512 or 1024 ions");
     if (R != 0 && R != 1) return fail(NB_EINVAL, "R must be 1 (use) or 0 (disable)");
   } else if (kind == 5) {
     if (block != 128 && block != 256) return fail(NB_EINVAL, "symmetric VJP block must be 128 or 256 ions");
     if (R != 0 && R != 1) return fail(NB_EINVAL, "R must be 1 (use) or 0 (disable)");
+  } else if (kind == 8) {
+    if (block < 1) return fail(NB_EINVAL, "block must be >= 1 (it is not used)");
+    if (R != 0 && R != 1) return fail(NB_EINVAL, "R must be 1 (eight lanes) or 0 (one lane)");
   } else if (kind == 7) {
     if (block < 1) return fail(NB_EINVAL, "block must be >= 1 (it is not used)");
     if (R != 0 && R != 1) return fail(NB_EINVAL, "R must be 1 (use) or 0 (disable)");

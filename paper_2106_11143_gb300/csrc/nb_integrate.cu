@@ -147,16 +147,14 @@ __global__ void k_epi_step(Phys p, StateView s, const double *__restrict__ cx,
   if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
-// The same epilogue with eight lanes per ion, for small n, where one thread
-// per ion leaves the chunk sum a long chain of dependent loads and adds on a
-// few SMs.  Lane u of an ion's group forms slot_sum3's running sum u (chunks
+// The same epilogue with eight lanes per ion (the default), where one thread
+// per ion leaves the chunk sum a long chain of dependent loads and adds, on
+// few SMs at small n.  Lane u of an ion's group forms slot_sum3's running sum u (chunks
 // u, u+8, ...), three shuffle levels add the eight in slot_sum3's pairing, so
 // the sum is bitwise the same.  The block's 32 sums then go through shared
 // memory to its first warp, which kicks one ion per lane: a warp instruction
 // of the kick's FP64 chain then serves 32 ions, not the 4 group leaders of a
 // warp.  Blocks of EPI8_THREADS threads (32 ions).
-// Ion counts up to which the epilogue runs with eight lanes per ion.
-constexpr int64_t EPI8_MAX_N = 2048;
 constexpr int EPI8_THREADS = 256;
 
 __global__ void __launch_bounds__(EPI8_THREADS)
@@ -220,7 +218,13 @@ cudaError_t launch_epi_step(const Phys &p, const StateView &s, const double *cx,
                             double *nx, double *ny, double *nz, unsigned *err, cudaStream_t st,
                             const int64_t *cin, int64_t *cout, int64_t cout_off) {
   const int T = 256;
-  if (s.n <= EPI8_MAX_N)
+  // Eight lanes per ion by default: measured on GB300 it was faster at every
+  // n up to 1e5 (17-32 % of a step at n = 2500-6000) and level at 1e5, where
+  // the step is the pair kernel.  Tuning kind 8 (R = 0) keeps one thread per ion.
+  bool eight = true;
+  int tb = 0, tr = 0, tbps = 0;
+  if (tuning_lookup(8, 0, s.n, &tb, &tr, &tbps)) eight = tr == 1;
+  if (eight)
     k_epi_step8<<<blocks_for(8 * s.n, EPI8_THREADS), EPI8_THREADS, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout, cout_off,
                                                       nx, ny, nz, err);
   else

@@ -517,20 +517,26 @@ static double sym_partial_cap() {
 Plan make_plan(int64_t n, int mode, int kind) {
   Plan pl;
   // Symmetric half-pair kernel for the force paths, while the
-  // per-partner-block partials (nbk * 3n doubles) fit the cap above.  Block
-  // sizes, the fastest measured on GB300 counting the epilogue's reads of the
-  // partials: 128-ion blocks (4 warps) up to n = 32768, then 256, and 512
-  // from n = 60000; split: 128 below n = 4096, 256 below 8000, then 512-ion
-  // blocks with two P-ions per lane.
+  // per-partner-block partials (nbk * 3n doubles) fit the cap above.  Where
+  // it starts and its block sizes are the fastest measured in step sweeps on
+  // GB300, counting the epilogue's reads of the partials: from n = 500
+  // (split), 1000 (mixed), 1500 (fp64) or 2000 (df64); 32-ion blocks (one
+  // warp) first, then 64 from n = 2000-2500, 128 from n = 2500-4096, 256
+  // from n = 32768 and 512 from n = 60000; split: 256 from n = 4096 and
+  // 512-ion blocks with two P-ions per lane from n = 8000.
   if (kind == 0 && (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || mode == MODE_SPLIT)) {
     int G;
-    if (mode == MODE_SPLIT)
-      G = n >= 8000 ? 16 : (n >= 4096 ? 8 : 4);
-    else
-      G = n >= 60000 ? 16 : (n >= 32768 ? 8 : 4);
-    // from n = 3000 (fp64, df64) or 2500 (mixed, split): where it beat the
-    // one-sided kernel in step sweeps on GB300
-    bool use = n >= ((mode == MODE_FP64 || mode == MODE_DF64) ? 3000 : 2500);
+    bool use;
+    if (mode == MODE_SPLIT) {
+      use = n >= 500;
+      G = n >= 8000 ? 16 : (n >= 4096 ? 8 : (n >= 2500 ? 4 : (n >= 2000 ? 2 : 1)));
+    } else {
+      const int64_t from = mode == MODE_MIXED ? 1000 : (mode == MODE_FP64 ? 1500 : 2000);
+      const int64_t g2 = mode == MODE_MIXED ? 2000 : 2500;  // 64-ion blocks from here
+      const int64_t g4 = mode == MODE_MIXED ? 3000 : 4096;  // 128-ion blocks from here
+      use = n >= from;
+      G = n >= 60000 ? 16 : (n >= 32768 ? 8 : (n >= g4 ? 4 : (n >= g2 ? 2 : 1)));
+    }
     int tb = 0, tr = 0, tbps = 0;
     if (tuning_lookup(4, mode, n, &tb, &tr, &tbps)) {
       use = tr != 0;

@@ -530,8 +530,25 @@ static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, cons
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
                             const double *z, const double *q, const PosF32 &pf, double soft2,
                             double *part, cudaStream_t st) {
-  if (G != 4 && G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
+  if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
   constexpr int S = SYM_THREADS_SMALL, L = SYM_THREADS;
+  if (G <= 2) {  // 32- and 64-ion blocks at small n: one warp per 32-ion tile
+    switch (mode) {
+      case MODE_FP64:
+        return G == 1 ? launch_sym_m<MODE_FP64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
+                      : launch_sym_m<MODE_FP64, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+      case MODE_DF64:
+        return G == 1 ? launch_sym_m<MODE_DF64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
+                      : launch_sym_m<MODE_DF64, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+      case MODE_MIXED:
+        return G == 1 ? launch_sym_m<MODE_MIXED, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
+                      : launch_sym_m<MODE_MIXED, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+      case MODE_SPLIT:
+        return G == 1 ? launch_sym_m<MODE_SPLIT, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
+                      : launch_sym_m<MODE_SPLIT, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   const bool small = G == 4;  // 4 warps for 128-ion blocks
   switch (mode) {
     case MODE_FP64:

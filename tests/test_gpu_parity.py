@@ -435,7 +435,7 @@ def test_symmetric_kernel_small_and_ragged(nb, orc, precision):
     rng = np.random.default_rng(17)
     try:
         for k, (n, block) in enumerate([(2, 256), (257, 256), (1000, 256), (2049, 512), (4100, 1024),
-                                        (6000, 512)]):
+                                        (6000, 512), (33, 32), (700, 32), (95, 64), (1501, 64)]):
             nb.set_tuning("symmetric", precision, 1, 1 << 40, block, R=1)
             pos, _ = W.random_cloud(n, seed=300 + k)
             q = W.E_CHARGE * rng.choice([-1.0, 1.0, 2.0], size=n) if k % 2 else None
