@@ -278,8 +278,9 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
  * they are used for n <= 4096 and nsteps >= 32).  For kind 7 (single-block
  * steps of small systems in nb_step): R = 1 to use them or 0 not to, for n
  * in [n_lo, n_hi] (`block` >= 1, not used; the kernel's own limits still
- * apply).  For kind 8 (the step epilogue, every precision; pass NB_FP64):
- * R = 1 for eight threads per ion (the default), 0 for one.  The latest
+ * apply).  For kind 8 (the epilogues of nb_forces, nb_step and
+ * nb_forces_vjp, every precision; pass NB_FP64): R = 1 for eight threads per
+ * ion (the default), 0 for one.  The latest
  * matching entry wins; block == 0 removes every override.  Results stay
  * deterministic for a fixed shape; different shapes may differ in the last
  * bits (summation order), except kind 3, which is shape-independent.     */

@@ -23,14 +23,81 @@ __device__ __forceinline__ void chunk_sum3(const double *__restrict__ part, int 
   slot_sum3(n_jc, [&](int jc, int c) { return __ldcs(p + ((int64_t)jc * 3 + c) * n); }, out);
 }
 
+// The epilogues run with EPI_THREADS threads per block, one of two ways:
+//  - one thread per ion, adding its chunk partials with chunk_sum3;
+//  - eight lanes per ion (the default): lane u forms slot_sum3's running sum u
+//    (chunks u, u+8, ...), three shuffle levels add the eight in slot_sum3's
+//    pairing, and the block's 32 sums go through shared memory to its first
+//    warp, which finishes one ion per lane.  The dependent chain of the sum is
+//    spread over eight threads, and the FP64 tail of the epilogue still serves
+//    32 ions per warp instruction.
+// Both give the same sums, bit for bit.  epi_sums returns false for threads
+// without an ion (the caller then returns); it holds a block barrier in the
+// eight-lane form, so every thread of the block must call it.
+constexpr int EPI_THREADS = 256;
+
+template <bool EIGHT>
+__device__ __forceinline__ bool epi_sums(const double *__restrict__ part, int n_jc, int64_t n,
+                                         int64_t &i, double cs[3]) {
+  if (!EIGHT) {
+    i = (int64_t)blockIdx.x * EPI_THREADS + threadIdx.x;
+    if (i >= n) return false;
+    chunk_sum3(part, n_jc, n, i, cs);
+    return true;
+  }
+  const int64_t g = ((int64_t)blockIdx.x * EPI_THREADS + threadIdx.x) >> 3;
+  const int u = threadIdx.x & 7;
+  const int64_t ig = g < n ? g : n - 1;  // every lane takes part in the shuffles
+  cs[0] = cs[1] = cs[2] = 0.0;
+  const double *pi = part + ig;
+  for (int jc = u; jc < n_jc; jc += 8) {
+    const double *q = pi + (int64_t)jc * 3 * n;
+    cs[0] += __ldcs(q);
+    cs[1] += __ldcs(q + n);
+    cs[2] += __ldcs(q + 2 * n);
+  }
+#pragma unroll
+  for (int d = 1; d < 8; d <<= 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double o = __shfl_down_sync(0xffffffffu, cs[c], d, 8);
+      if ((u & (2 * d - 1)) == 0) cs[c] = cs[c] + o;
+    }
+  }
+  __shared__ double csum[3][EPI_THREADS / 8];
+  if (u == 0) {
+    csum[0][threadIdx.x >> 3] = cs[0];
+    csum[1][threadIdx.x >> 3] = cs[1];
+    csum[2][threadIdx.x >> 3] = cs[2];
+  }
+  __syncthreads();
+  if (threadIdx.x >= EPI_THREADS / 8) return false;
+  i = (int64_t)blockIdx.x * (EPI_THREADS / 8) + threadIdx.x;
+  if (i >= n) return false;
+  cs[0] = csum[0][threadIdx.x];
+  cs[1] = csum[1][threadIdx.x];
+  cs[2] = csum[2][threadIdx.x];
+  return true;
+}
+
+// Eight lanes per ion unless tuning kind 8 says one (R = 0) for this n:
+// measured on GB300 the eight-lane form was faster at every n up to 1e5
+// (17-32 % of a step at n = 2500-6000) and level at 1e5.
+static bool epi_eight(int64_t n) {
+  int tb = 0, tr = 0, tbps = 0;
+  if (tuning_lookup(8, 0, n, &tb, &tr, &tbps)) return tr == 1;
+  return true;
+}
+static int epi_blocks(int64_t n, bool eight) { return blocks_for(eight ? 8 * n : n, EPI_THREADS); }
+
 // ---------------------------------------------------------------------------
-__global__ void k_epi_forces(Phys p, StateView s, const double *__restrict__ part, int n_jc,
-                             int flags, double t, unsigned *err) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.n) return;
-  const double pref = coulomb_pref(p, s, i);
+template <bool EIGHT>
+__device__ __forceinline__ void epi_forces(const Phys &p, const StateView &s, const double *part,
+                                           int n_jc, int flags, double t, unsigned *err) {
+  int64_t i;
   double a[3];
-  chunk_sum3(part, n_jc, s.n, i, a);
+  if (!epi_sums<EIGHT>(part, n_jc, s.n, i, a)) return;
+  const double pref = coulomb_pref(p, s, i);
 #pragma unroll
   for (int c = 0; c < 3; ++c) a[c] *= pref;
   if (flags & NB_ACC_TOTAL) {
@@ -47,24 +114,36 @@ __global__ void k_epi_forces(Phys p, StateView s, const double *__restrict__ par
   s.az[i] = a[2];
   if (not_finite(a[0]) || not_finite(a[1]) || not_finite(a[2])) atomicOr(err, ERR_NONFINITE);
 }
+__global__ void __launch_bounds__(EPI_THREADS)
+    k_epi_forces(Phys p, StateView s, const double *__restrict__ part, int n_jc, int flags, double t,
+                 unsigned *err) {
+  epi_forces<false>(p, s, part, n_jc, flags, t, err);
+}
+__global__ void __launch_bounds__(EPI_THREADS)
+    k_epi_forces8(Phys p, StateView s, const double *__restrict__ part, int n_jc, int flags, double t,
+                  unsigned *err) {
+  epi_forces<true>(p, s, part, n_jc, flags, t, err);
+}
 
 cudaError_t launch_epi_forces(const Phys &p, const StateView &s, const double *part, int n_jc,
                               int flags, double t, unsigned *err, cudaStream_t st) {
-  const int T = 256;
-  k_epi_forces<<<blocks_for(s.n, T), T, 0, st>>>(p, s, part, n_jc, flags, t, err);
+  const bool eight = epi_eight(s.n);
+  if (eight)
+    k_epi_forces8<<<epi_blocks(s.n, true), EPI_THREADS, 0, st>>>(p, s, part, n_jc, flags, t, err);
+  else
+    k_epi_forces<<<epi_blocks(s.n, false), EPI_THREADS, 0, st>>>(p, s, part, n_jc, flags, t, err);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_epi_vjp(Phys p, StateView s, const double *__restrict__ part, int n_jc,
-                          const double *__restrict__ lx, const double *__restrict__ ly,
-                          const double *__restrict__ lz, double *gx, double *gy, double *gz,
-                          int flags, double t) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.n) return;
-  const double pref = coulomb_pref(p, s, i);
+template <bool EIGHT>
+__device__ __forceinline__ void epi_vjp(const Phys &p, const StateView &s, const double *part, int n_jc,
+                                        const double *lx, const double *ly, const double *lz, double *gx,
+                                        double *gy, double *gz, int flags, double t) {
+  int64_t i;
   double g[3];
-  chunk_sum3(part, n_jc, s.n, i, g);
+  if (!epi_sums<EIGHT>(part, n_jc, s.n, i, g)) return;
+  const double pref = coulomb_pref(p, s, i);
 #pragma unroll
   for (int c = 0; c < 3; ++c) g[c] *= pref;
   if (flags & NB_ACC_TOTAL) {
@@ -79,12 +158,26 @@ __global__ void k_epi_vjp(Phys p, StateView s, const double *__restrict__ part, 
   gy[i] = g[1];
   gz[i] = g[2];
 }
+__global__ void __launch_bounds__(EPI_THREADS)
+    k_epi_vjp(Phys p, StateView s, const double *__restrict__ part, int n_jc, const double *__restrict__ lx,
+              const double *__restrict__ ly, const double *__restrict__ lz, double *gx, double *gy,
+              double *gz, int flags, double t) {
+  epi_vjp<false>(p, s, part, n_jc, lx, ly, lz, gx, gy, gz, flags, t);
+}
+__global__ void __launch_bounds__(EPI_THREADS)
+    k_epi_vjp8(Phys p, StateView s, const double *__restrict__ part, int n_jc, const double *__restrict__ lx,
+               const double *__restrict__ ly, const double *__restrict__ lz, double *gx, double *gy,
+               double *gz, int flags, double t) {
+  epi_vjp<true>(p, s, part, n_jc, lx, ly, lz, gx, gy, gz, flags, t);
+}
 
 cudaError_t launch_epi_vjp(const Phys &p, const StateView &s, const double *part, int n_jc,
                            const double *lx, const double *ly, const double *lz, double *gx,
                            double *gy, double *gz, int flags, double t, cudaStream_t st) {
-  const int T = 256;
-  k_epi_vjp<<<blocks_for(s.n, T), T, 0, st>>>(p, s, part, n_jc, lx, ly, lz, gx, gy, gz, flags, t);
+  if (epi_eight(s.n))
+    k_epi_vjp8<<<epi_blocks(s.n, true), EPI_THREADS, 0, st>>>(p, s, part, n_jc, lx, ly, lz, gx, gy, gz, flags, t);
+  else
+    k_epi_vjp<<<epi_blocks(s.n, false), EPI_THREADS, 0, st>>>(p, s, part, n_jc, lx, ly, lz, gx, gy, gz, flags, t);
   return cudaGetLastError();
 }
 
@@ -119,19 +212,18 @@ cudaError_t launch_drift(const Phys &p, const StateView &s, double *px, double *
 // there.  The counter form lets one captured graph of steps be replayed with
 // a step index that advances from replay to replay (cin and cout are never
 // the same word, so no thread reads what another writes).
-__global__ void k_epi_step(Phys p, StateView s, const double *__restrict__ cx,
-                           const double *__restrict__ cy, const double *__restrict__ cz,
-                           const double *__restrict__ part, int n_jc, int64_t soff,
-                           const int64_t *cin, int64_t *cout, int64_t cout_off, double *nx,
-                           double *ny, double *nz, unsigned *err) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.n) return;
+template <bool EIGHT>
+__device__ __forceinline__ void epi_step(const Phys &p, const StateView &s, const double *cx,
+                                         const double *cy, const double *cz, const double *part, int n_jc,
+                                         int64_t soff, const int64_t *cin, int64_t *cout, int64_t cout_off,
+                                         double *nx, double *ny, double *nz, unsigned *err) {
+  int64_t i;
+  double cs[3];
+  if (!epi_sums<EIGHT>(part, n_jc, s.n, i, cs)) return;
   const int64_t base = cin ? *cin : 0;
   const int64_t snew = base + soff;
   if (cout && i == 0) *cout = base + cout_off;
   const double r[3] = {cx[i], cy[i], cz[i]};
-  double cs[3];
-  chunk_sum3(part, n_jc, s.n, i, cs);
   double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
   double a[3] = {s.ax[i], s.ay[i], s.az[i]};
   const bool bad = verlet_kick(p, s, i, snew, r, cs, v, a);
@@ -146,90 +238,31 @@ __global__ void k_epi_step(Phys p, StateView s, const double *__restrict__ cx,
   }
   if (bad) atomicOr(err, ERR_NONFINITE);
 }
-
-// The same epilogue with eight lanes per ion (the default), where one thread
-// per ion leaves the chunk sum a long chain of dependent loads and adds, on
-// few SMs at small n.  Lane u of an ion's group forms slot_sum3's running sum u (chunks
-// u, u+8, ...), three shuffle levels add the eight in slot_sum3's pairing, so
-// the sum is bitwise the same.  The block's 32 sums then go through shared
-// memory to its first warp, which kicks one ion per lane: a warp instruction
-// of the kick's FP64 chain then serves 32 ions, not the 4 group leaders of a
-// warp.  Blocks of EPI8_THREADS threads (32 ions).
-constexpr int EPI8_THREADS = 256;
-
-__global__ void __launch_bounds__(EPI8_THREADS)
+__global__ void __launch_bounds__(EPI_THREADS)
+    k_epi_step(Phys p, StateView s, const double *__restrict__ cx, const double *__restrict__ cy,
+               const double *__restrict__ cz, const double *__restrict__ part, int n_jc, int64_t soff,
+               const int64_t *cin, int64_t *cout, int64_t cout_off, double *nx, double *ny, double *nz,
+               unsigned *err) {
+  epi_step<false>(p, s, cx, cy, cz, part, n_jc, soff, cin, cout, cout_off, nx, ny, nz, err);
+}
+__global__ void __launch_bounds__(EPI_THREADS)
     k_epi_step8(Phys p, StateView s, const double *__restrict__ cx, const double *__restrict__ cy,
                 const double *__restrict__ cz, const double *__restrict__ part, int n_jc, int64_t soff,
                 const int64_t *cin, int64_t *cout, int64_t cout_off, double *nx, double *ny, double *nz,
                 unsigned *err) {
-  const int64_t g = ((int64_t)blockIdx.x * EPI8_THREADS + threadIdx.x) >> 3;
-  const int u = threadIdx.x & 7;
-  const int64_t ig = g < s.n ? g : s.n - 1;  // every lane takes part in the shuffles
-  double cs[3] = {0.0, 0.0, 0.0};
-  const double *pi = part + ig;
-  for (int jc = u; jc < n_jc; jc += 8) {
-    const double *q = pi + (int64_t)jc * 3 * s.n;
-    cs[0] += __ldcs(q);
-    cs[1] += __ldcs(q + s.n);
-    cs[2] += __ldcs(q + 2 * s.n);
-  }
-#pragma unroll
-  for (int d = 1; d < 8; d <<= 1) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double o = __shfl_down_sync(0xffffffffu, cs[c], d, 8);
-      if ((u & (2 * d - 1)) == 0) cs[c] = cs[c] + o;
-    }
-  }
-  __shared__ double csum[3][EPI8_THREADS / 8];
-  if (u == 0) {
-    csum[0][threadIdx.x >> 3] = cs[0];
-    csum[1][threadIdx.x >> 3] = cs[1];
-    csum[2][threadIdx.x >> 3] = cs[2];
-  }
-  __syncthreads();
-  if (threadIdx.x >= EPI8_THREADS / 8) return;
-  const int64_t i = (int64_t)blockIdx.x * (EPI8_THREADS / 8) + threadIdx.x;
-  if (i >= s.n) return;
-  cs[0] = csum[0][threadIdx.x];
-  cs[1] = csum[1][threadIdx.x];
-  cs[2] = csum[2][threadIdx.x];
-  const int64_t base = cin ? *cin : 0;
-  const int64_t snew = base + soff;
-  if (cout && i == 0) *cout = base + cout_off;
-  const double r[3] = {cx[i], cy[i], cz[i]};
-  double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
-  double a[3] = {s.ax[i], s.ay[i], s.az[i]};
-  const bool bad = verlet_kick(p, s, i, snew, r, cs, v, a);
-  s.vx[i] = v[0]; s.vy[i] = v[1]; s.vz[i] = v[2];
-  s.ax[i] = a[0]; s.ay[i] = a[1]; s.az[i] = a[2];
-  if (nx) {
-    nx[i] = verlet_drift(r[0], v[0], a[0], p.dt);
-    ny[i] = verlet_drift(r[1], v[1], a[1], p.dt);
-    nz[i] = verlet_drift(r[2], v[2], a[2], p.dt);
-  } else {
-    s.x[i] = r[0]; s.y[i] = r[1]; s.z[i] = r[2];
-  }
-  if (bad) atomicOr(err, ERR_NONFINITE);
+  epi_step<true>(p, s, cx, cy, cz, part, n_jc, soff, cin, cout, cout_off, nx, ny, nz, err);
 }
 
 cudaError_t launch_epi_step(const Phys &p, const StateView &s, const double *cx, const double *cy,
                             const double *cz, const double *part, int n_jc, int64_t snew,
                             double *nx, double *ny, double *nz, unsigned *err, cudaStream_t st,
                             const int64_t *cin, int64_t *cout, int64_t cout_off) {
-  const int T = 256;
-  // Eight lanes per ion by default: measured on GB300 it was faster at every
-  // n up to 1e5 (17-32 % of a step at n = 2500-6000) and level at 1e5, where
-  // the step is the pair kernel.  Tuning kind 8 (R = 0) keeps one thread per ion.
-  bool eight = true;
-  int tb = 0, tr = 0, tbps = 0;
-  if (tuning_lookup(8, 0, s.n, &tb, &tr, &tbps)) eight = tr == 1;
-  if (eight)
-    k_epi_step8<<<blocks_for(8 * s.n, EPI8_THREADS), EPI8_THREADS, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout, cout_off,
-                                                      nx, ny, nz, err);
+  if (epi_eight(s.n))
+    k_epi_step8<<<epi_blocks(s.n, true), EPI_THREADS, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout,
+                                                                cout_off, nx, ny, nz, err);
   else
-    k_epi_step<<<blocks_for(s.n, T), T, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout, cout_off,
-                                                 nx, ny, nz, err);
+    k_epi_step<<<epi_blocks(s.n, false), EPI_THREADS, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout,
+                                                                cout_off, nx, ny, nz, err);
   return cudaGetLastError();
 }
 

@@ -192,21 +192,26 @@ def test_windows_off_above_default_n(nb):
 @pytest.mark.parametrize("precision", ["fp64", "mixed_split"])
 @pytest.mark.parametrize("n", [100, 3001, 9000])
 def test_epilogue_lanes_bitwise(nb, precision, n):
-    """The eight-lane epilogue (the default) and the one-thread-per-ion
-    epilogue (tuning kind 8, R = 0) add the chunk partials in the same order
-    and apply the same kick: bitwise the same steps, through one-sided and
-    symmetric plans, with noise and the RF trap."""
+    """The eight-lane epilogues (the default) and the one-thread-per-ion
+    epilogues (tuning kind 8, R = 0) add the chunk partials in the same order
+    and apply the same tail: bitwise the same forces, VJP and steps, through
+    one-sided and symmetric plans, with noise and the RF trap."""
     w, phys, par = _setup(nb, n, precision)
-    out = []
+    lam = np.random.default_rng(n).standard_normal((3, n))
+    out, acc, vjp = [], [], []
     for R in (1, 0):
         nb.set_tuning("force", "fp64", 0, 0, 0)
         nb.set_tuning("small_steps", precision, 0, 1 << 40, 1, R=0)
         nb.set_tuning("epilogue_lanes", "fp64", 0, 1 << 40, 1, R=R)
         s = nb.System(w["pos"], w["vel"])
         nb.forces(par, s, total=True)
+        acc.append(s.acc().clone())
+        vjp.append(nb.forces_vjp(par, s, lam, total=True))
         nb.step(par, s, 37)
         torch.cuda.synchronize()
         nb.sync_status()
         out.append(s)
     nb.set_tuning("force", "fp64", 0, 0, 0)
+    assert torch.equal(acc[0], acc[1])
+    assert torch.equal(vjp[0], vjp[1])
     _equal(out[0], out[1])
