@@ -27,8 +27,8 @@ import torch
 from . import api
 from . import workloads as W
 
-# n buckets of the one-sided force kernel, the default below n = 4096:
-# (lo, hi, representative n)
+# n buckets of the one-sided force kernel (the default below n = 500-2000,
+# by precision, and for the ladder modes): (lo, hi, representative n)
 BUCKETS = [(1, 1500, 1024), (1501, 4095, 3000)]
 FORCE_SHAPES = [(b, r, bps) for b in (64, 128, 256) for r in (1, 2, 4) for bps in (4, 8, 16, 32)]
 SMALL_SHAPES = [(b, 1, bps) for b in (32, 64, 128) for bps in (8, 16, 32, 64)]
@@ -78,8 +78,9 @@ def tune_pair(precision, quick=False, log=print):
     return out
 
 
-SYM_BUCKETS = [(4096, 10000, 8192), (10001, 40000, 16384), (40001, 1 << 31, 100000)]
-SYM_BLOCKS = (128, 256, 512, 1024)
+SYM_BUCKETS = [(500, 1499, 1000), (1500, 2499, 2000), (2500, 4095, 3000), (4096, 10000, 8192),
+               (10001, 40000, 16384), (40001, 1 << 31, 100000)]
+SYM_BLOCKS = (32, 64, 128, 256, 512, 1024)
 
 
 def _time_step(par, sysm, reps):
