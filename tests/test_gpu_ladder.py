@@ -95,3 +95,35 @@ def test_workload_runs_module(nb):
     assert r["steps"] == 10 and r["device_ms"] > 0 and np.isfinite(r["final_energy_J"][3])
     k = runs.kz(nsteps=4, chunk=2)
     assert k["steps"] == 4 and k["instances"] == 512
+
+
+def test_autotuner_quick_round_trip(nb, tmp_path):
+    """The autotuner in quick mode (one-sided shapes at n = 3000, symmetric
+    blocks at n = 1e5, fp64 and mixed_split): every entry is a valid override;
+    applied from its JSON cache, the forces agree with the default shapes to
+    rounding (a shape only reorders the sums)."""
+    import json
+    import torch
+    from paper_2106_11143_gb300 import tune
+    from paper_2106_11143_gb300 import workloads as W
+    entries = []
+    for prec in ("fp64", "mixed_split"):
+        entries += tune.tune_pair(prec, quick=True, log=lambda *a: None)
+        entries += tune.tune_symmetric(prec, quick=True, log=lambda *a: None)
+    assert entries and all(e["ms"] > 0 for e in entries)
+    path = tmp_path / "cache.json"
+    json.dump({"device": torch.cuda.get_device_name(), "entries": entries}, open(path, "w"))
+    pos, _ = W.random_cloud(3000, seed=8)
+    par = nb.Params.from_phys(W.phys())
+    s = nb.System(pos)
+    nb.forces(par, s)
+    ref = s.acc().clone()
+    try:
+        assert tune.load(str(path))
+        nb.forces(par, s)
+        torch.cuda.synchronize()
+        nb.sync_status()
+        tuned = s.acc()
+        assert torch.max(torch.abs(tuned - ref)).item() <= 1e-12 * torch.max(torch.abs(ref)).item()
+    finally:
+        nb.set_tuning("force", "fp64", 0, 0, 0)
