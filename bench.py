@@ -62,6 +62,8 @@ def parse():
                     help="large: the N=1e5 headline; kz: the 512-instance ensemble (extra line)")
     ap.add_argument("--profile-forces", action="store_true",
                     help="profiling case: two nb_forces calls per precision at --n, no timing")
+    ap.add_argument("--one-sided", action="store_true",
+                    help="with --profile-forces: the one-sided force kernel at any n")
     ap.add_argument("--profile-vjp", action="store_true",
                     help="profiling case: two nb_forces_vjp calls at --n, no timing")
     ap.add_argument("--profile-small", action="store_true",
@@ -436,6 +438,9 @@ def profile_forces(args):
     from paper_2106_11143_gb300 import workloads as W
     w = W.cloud_large(n=args.n)
     sysm = nb.System(w["pos"], w["vel"])
+    if args.one_sided:  # the one-sided kernel, as the ladder modes use it at every n
+        for prec in ("fp64", "df64", "mixed", "mixed_split"):
+            nb.set_tuning("symmetric", prec, 0, 1 << 40, 128, R=0)
     for _ in range(2):
         for prec in ("fp64", "df64", "mixed", "mixed_split"):
             nb.forces(nb.Params.from_phys(w["phys"], precision=prec), sysm)
