@@ -50,7 +50,7 @@ typedef enum {
   NB_ENONFINITE = 3,  /* a non-finite acceleration or velocity was produced */
   NB_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
   NB_ENOMEM = 5,      /* scratch allocation failed */
-  NB_ENOTSUP = 6      /* valid request this build does not implement */
+  NB_ENOTSUP = 6      /* a valid request the library does not support */
 } nb_status;
 
 /* Arithmetic of the pair interaction (the O(N^2) inner loop).
