@@ -258,6 +258,18 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
                           uint16_t *order, uint16_t *bin_start, double *max_load,
                           double *mean_load);
 
+/* Host-only: the launch plan a call at n ions would use, for kind 0 (the
+ * force kernel of nb_forces / nb_step in `precision`), 1 (the potential
+ * kernel) or 2 (the VJP kernel), with the current tuning overrides:
+ * out[0] threads per block (one-sided) or 256 / 128 (symmetric), out[1] ions
+ * per thread R, out[2] partners per j-chunk, out[3] i-tiles, out[4] partial
+ * slots n_jc (j-chunks, or partner blocks of the symmetric kernel), out[5]
+ * 1 for the symmetric kernel, out[6] its ions per block / 32, out[7] 1 if
+ * nb_step would run the single-block path (kind 0).  Without a usable GPU
+ * it plans for 152 SMs and a 2 GB cap on the symmetric partials.  No
+ * device work.                                                            */
+nb_status nb_plan_info(int32_t kind, int32_t precision, int64_t n, int64_t out[8]);
+
 /* Launch-shape override (used by the autotuner, paper_2106_11143_gb300/
  * tune.py).  For kind 0 (force), 1 (potential), 2 (VJP) pair kernels in
  * `precision` and n in [n_lo, n_hi]: `block` threads per block (32, 64, 128

@@ -90,10 +90,11 @@ def lib():
         L.nb_launch_count.restype = C.c_uint64
         L.nb_rinv3_probe.argtypes = [C.c_int32, C.c_int64, _dp, _dp, _dp, C.c_double, _dp, V]
         L.nb_rsqrt_seed_probe.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, V]
+        L.nb_plan_info.argtypes = [C.c_int32, C.c_int32, C.c_int64, I64P]
         for f in ("nb_forces", "nb_step", "nb_energy", "nb_forces_vjp", "nb_sync_status",
                   "nb_release", "nb_timing_enable", "nb_timing_read", "nb_step_batched",
                   "nb_plan_batched", "nb_set_tuning", "nb_energy_noalloc", "nb_traj_forward",
-                  "nb_traj_backward", "nb_rinv3_probe", "nb_rsqrt_seed_probe"):
+                  "nb_traj_backward", "nb_rinv3_probe", "nb_rsqrt_seed_probe", "nb_plan_info"):
             getattr(L, f).restype = C.c_int
         _LIB = L
     return _LIB
@@ -387,6 +388,18 @@ def plan_batched(offsets, n_bins):
                                  start.ctypes.data_as(C.POINTER(C.c_uint16)),
                                  C.byref(mx), C.byref(mean)), "nb_plan_batched")
     return order[:n_inst], start, mx.value, mean.value
+
+
+PLAN_KINDS = {"force": 0, "potential": 1, "vjp": 2}
+PLAN_FIELDS = ("block", "R", "jchunk", "n_it", "n_jc", "symmetric", "G", "single_block")
+
+
+def plan_info(kind, precision, n):
+    """nb_plan_info: the launch plan a call at n ions would use (host only)."""
+    out = (C.c_int64 * 8)()
+    _check(lib().nb_plan_info(PLAN_KINDS[kind] if isinstance(kind, str) else int(kind), PRECISIONS[precision],
+                              int(n), out), "nb_plan_info")
+    return dict(zip(PLAN_FIELDS, (int(v) for v in out)))
 
 
 KINDS = {"force": 0, "potential": 1, "vjp": 2, "ensemble": 3, "symmetric": 4, "symmetric_vjp": 5,

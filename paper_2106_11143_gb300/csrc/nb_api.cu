@@ -692,6 +692,23 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
   return NB_OK;
 }
 
+nb_status nb_plan_info(int32_t kind, int32_t precision, int64_t n, int64_t out[8]) {
+  if (!out) return fail(NB_EINVAL, "out is NULL");
+  if (kind < 0 || kind > 2) return fail(NB_EINVAL, "kind must be 0 (force), 1 (potential) or 2 (VJP)");
+  if (precision < NB_FP64 || precision > NB_FP64_RSQ_NR2) return fail(NB_EINVAL, "bad precision");
+  if (n < 1) return fail(NB_EINVAL, "n must be >= 1");
+  const Plan pl = make_plan(n, kind == 0 ? precision : MODE_FP64, kind);
+  out[0] = pl.block;
+  out[1] = pl.R;
+  out[2] = pl.jchunk;
+  out[3] = pl.n_it;
+  out[4] = pl.n_jc;
+  out[5] = pl.sym;
+  out[6] = pl.G;
+  out[7] = kind == 0 && use_small_steps(pl, precision, n) ? 1 : 0;
+  return NB_OK;
+}
+
 nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n_hi, int32_t block,
                         int32_t R, int32_t blocks_per_sm) {
   if (block == 0) {

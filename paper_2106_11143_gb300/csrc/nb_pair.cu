@@ -451,10 +451,14 @@ cudaError_t launch_split_positions(int64_t n, const double *x, const double *y, 
 // Plan: i-tile and j-chunk sizes.  Blocks of one to four warps; enough
 // (i-tile, j-chunk) blocks for about 16 per SM so the last wave is short;
 // j-chunks of at least 4 tiles so the partial-sum traffic stays small.
+// SMs of the current device; without a usable device (host-only planning),
+// the GB300's 152.
 int device_sm_count() {
   int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
   return sms;
 }
 
@@ -505,7 +509,10 @@ static double sym_partial_cap() {
   static std::mutex mu;
   static double cap[64] = {0.0};
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 2e9;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 2e9;
+  }
   std::lock_guard<std::mutex> lk(mu);
   if (cap[dev] == 0.0) {
     cudaDeviceProp prop;

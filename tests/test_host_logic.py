@@ -117,3 +117,69 @@ def test_checkpoint_file_round_trip(api, tmp_path):
         (tmp_path / "bad.nbck").write_bytes(bad)
         with pytest.raises(ValueError):
             api.load_checkpoint(tmp_path / "bad.nbck", device="cpu")
+
+
+PLAN_NS = [1, 2, 3, 7, 8, 15, 16, 17, 31, 32, 33, 47, 48, 49, 63, 64, 65, 100, 127, 128, 129, 255, 256,
+           257, 499, 500, 501, 999, 1000, 1001, 1499, 1500, 1501, 1999, 2000, 2047, 2048, 2499, 2500,
+           2999, 3000, 3001, 4095, 4096, 4097, 7999, 8000, 8191, 8192, 9999, 10000, 24000, 32767,
+           32768, 59999, 60000, 100000, 262151]
+
+
+def test_plan_invariants(api):
+    """Every launch plan (host only, no GPU) covers all n ions and all
+    partners: the one-sided kernel's i-tiles and j-chunks tile [0, n) and its
+    grid stays within the launch limits; the symmetric kernel has one partial
+    slot per partner block of a supported size; the single-block path is
+    offered only within its 512-ion limit and never with the symmetric
+    kernel."""
+    import math
+    for kind, precs in (("force", list(api.PRECISIONS)), ("potential", ["fp64"]), ("vjp", ["fp64"])):
+        for prec in precs:
+            for n in PLAN_NS:
+                p = api.plan_info(kind, prec, n)
+                if p["symmetric"]:
+                    assert p["G"] in ((1, 2, 4, 8, 16, 32) if kind == "force" else (4, 8)), (kind, prec, n, p)
+                    assert p["n_jc"] == math.ceil(n / (32 * p["G"])), (kind, prec, n, p)
+                    assert p["n_jc"] * 3 * n * 8 <= 2e9  # the host-only cap on the partials
+                else:
+                    assert p["block"] in (32, 64, 128, 256) and p["R"] in (1, 2, 4), (kind, prec, n, p)
+                    assert p["n_it"] == math.ceil(n / (p["block"] * p["R"])), (kind, prec, n, p)
+                    assert p["jchunk"] >= 1
+                    assert (p["n_jc"] - 1) * p["jchunk"] < n <= p["n_jc"] * p["jchunk"], (kind, prec, n, p)
+                    assert p["n_jc"] <= 65535  # grid.y
+                if p["single_block"]:
+                    assert kind == "force" and n <= 512 and not p["symmetric"], (prec, n, p)
+
+
+def test_plan_thresholds(api):
+    """The documented defaults: the symmetric force kernel from n = 500
+    (mixed_split), 1000 (mixed), 1500 (fp64) and 2000 (df64), never in the
+    ladder modes; the symmetric VJP from n = 2500; the single-block steps up
+    to 32 ions (48 for df64, 16 for sqrtdiv); and the tuning overrides."""
+    for prec, start in (("mixed_split", 500), ("mixed", 1000), ("fp64", 1500), ("df64", 2000)):
+        assert not api.plan_info("force", prec, start - 1)["symmetric"]
+        assert api.plan_info("force", prec, start)["symmetric"]
+    for prec in ("sqrtdiv", "rsq", "rsq_nr1", "rsq_nr2"):
+        assert not api.plan_info("force", prec, 100000)["symmetric"]
+    assert not api.plan_info("vjp", "fp64", 2499)["symmetric"]
+    assert api.plan_info("vjp", "fp64", 2500)["symmetric"]
+    for prec, top in (("fp64", 32), ("mixed", 32), ("mixed_split", 32), ("df64", 48), ("sqrtdiv", 16),
+                      ("rsq", 32), ("rsq_nr1", 32), ("rsq_nr2", 32)):
+        assert api.plan_info("force", prec, top)["single_block"] == 1, prec
+        assert api.plan_info("force", prec, top + 1)["single_block"] == 0, prec
+    try:
+        api.set_tuning("symmetric", "fp64", 0, 1 << 40, 128, R=0)
+        assert not api.plan_info("force", "fp64", 100000)["symmetric"]
+        api.set_tuning("symmetric", "fp64", 0, 1 << 40, 64, R=1)
+        p = api.plan_info("force", "fp64", 600)
+        assert p["symmetric"] and p["G"] == 2
+        api.set_tuning("small_steps", "fp64", 0, 1 << 40, 1, R=1)
+        assert api.plan_info("force", "fp64", 400)["single_block"] == 0  # symmetric plan: not eligible
+        api.set_tuning("force", "fp64", 0, 0, 0)
+        api.set_tuning("small_steps", "fp64", 0, 1 << 40, 1, R=1)
+        assert api.plan_info("force", "fp64", 200)["single_block"] == 1
+        assert api.plan_info("force", "fp64", 513)["single_block"] == 0  # above the block's limit
+    finally:
+        api.set_tuning("force", "fp64", 0, 0, 0)
+    with pytest.raises(api.NBError):
+        api.plan_info("force", "fp64", 0)
