@@ -65,6 +65,20 @@ def test_tuning_validation(api):
         api.set_tuning("symmetric_vjp", "fp64", 0, 100, 128, R=2)
     api.set_tuning("symmetric_vjp", "fp64", 0, 100, 256, R=0)
     api.set_tuning("force", "fp64", 0, 100, 64, R=2, blocks_per_sm=8)
+    # step windows, single-block steps, epilogue lanes: R is 0 or 1, block >= 1
+    for kind in ("step_windows", "small_steps", "epilogue_lanes"):
+        api.set_tuning(kind, "fp64", 0, 100, 1, R=0)
+        api.set_tuning(kind, "fp64", 0, 100, 64, R=1)
+        with pytest.raises(api.NBError):
+            api.set_tuning(kind, "fp64", 0, 100, 1, R=2)
+        with pytest.raises(api.NBError):
+            api.set_tuning(kind, "fp64", 0, 100, -1, R=1)
+    with pytest.raises(api.NBError):
+        api.set_tuning(9, "fp64", 0, 100, 1, R=1)  # no such kind
+    for block in (32, 64):  # the small symmetric blocks
+        api.set_tuning("symmetric", "fp64", 0, 100, block, R=1)
+    with pytest.raises(api.NBError):
+        api.set_tuning("symmetric", "fp64", 0, 100, 96, R=1)
     api.set_tuning("force", "fp64", 0, 0, 0)  # clear
 
 
