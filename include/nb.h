@@ -260,7 +260,8 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
 
 /* Host-only: the launch plan a call at n ions would use, for kind 0 (the
  * force kernel of nb_forces / nb_step in `precision`), 1 (the potential
- * kernel) or 2 (the VJP kernel), with the current tuning overrides:
+ * kernel) or 2 (the VJP kernel, fp64 and df64 alike; for kinds 1 and 2
+ * `precision` is validated but does not change the plan), with the current tuning overrides:
  * out[0] threads per block (one-sided) or 256 / 128 (symmetric), out[1] ions
  * per thread R, out[2] partners per j-chunk, out[3] i-tiles, out[4] partial
  * slots n_jc (j-chunks, or partner blocks of the symmetric kernel), out[5]
@@ -274,7 +275,9 @@ nb_status nb_plan_info(int32_t kind, int32_t precision, int64_t n, int64_t out[8
  * tune.py).  For kind 0 (force), 1 (potential), 2 (VJP) pair kernels in
  * `precision` and n in [n_lo, n_hi]: `block` threads per block (32, 64, 128
  * or 256), `R` ions per thread (1, 2, 4; force kernel only) and about
- * `blocks_per_sm` (i-tile, j-chunk) blocks per SM.  For kind 3 (the ensemble
+ * `blocks_per_sm` (i-tile, j-chunk) blocks per SM.  The potential and VJP
+ * plans are shared by every precision and read only the NB_FP64 entries
+ * (kinds 1, 2 and 5): an override there also shapes the NB_DF64 VJP.  For kind 3 (the ensemble
  * kernel): `block` threads per block (multiple of 32, <= 512), and R = 0 to
  * keep its one-sided force phase (by default ensembles whose instances all
  * have at most 4096 ions use the half-pair phase).  For kind 4
@@ -283,7 +286,7 @@ nb_status nb_plan_info(int32_t kind, int32_t precision, int64_t n, int64_t out[8
  * to disable it for that n range (by default it is used from n = 500 in
  * NB_MIXED_SPLIT, 1000 in NB_MIXED, 1500 in NB_FP64 and 2000 in NB_DF64).
  * For kind 5
- * (the symmetric VJP kernel; `precision` NB_FP64): `block` ions per block
+ * (the symmetric VJP kernel of NB_FP64 and NB_DF64; pass NB_FP64): `block` ions per block
  * pair unit (128 or 256) and R = 1 / 0 to use / disable it (by default it is
  * used from n = 2500).  For kind 6 (step windows of nb_step): R = 1 to
  * use them or 0 not to, for calls of at least `block` steps (by default
