@@ -197,3 +197,23 @@ def test_plan_thresholds(api):
         api.set_tuning("force", "fp64", 0, 0, 0)
     with pytest.raises(api.NBError):
         api.plan_info("force", "fp64", 0)
+
+
+def test_vjp_and_potential_plans_shared_by_precisions(api):
+    """The potential and VJP plans do not depend on the precision argument
+    (the NB_DF64 VJP runs on the fp64 VJP plan), and a symmetric-VJP override
+    given for NB_FP64 reshapes them all."""
+    for n in (100, 2499, 2500, 16383, 16384, 100000):
+        for kind in ("potential", "vjp"):
+            base = api.plan_info(kind, "fp64", n)
+            for prec in ("df64", "mixed", "mixed_split"):
+                assert api.plan_info(kind, prec, n) == base, (kind, prec, n)
+    try:
+        api.set_tuning("symmetric_vjp", "fp64", 0, 1 << 40, 256, R=1)
+        for prec in ("fp64", "df64"):
+            p = api.plan_info("vjp", prec, 3000)
+            assert p["symmetric"] and p["G"] == 8, (prec, p)
+        api.set_tuning("symmetric_vjp", "fp64", 0, 1 << 40, 128, R=0)
+        assert not api.plan_info("vjp", "df64", 100000)["symmetric"]
+    finally:
+        api.set_tuning("force", "fp64", 0, 0, 0)
