@@ -217,3 +217,26 @@ def test_vjp_and_potential_plans_shared_by_precisions(api):
         assert not api.plan_info("vjp", "df64", 100000)["symmetric"]
     finally:
         api.set_tuning("force", "fp64", 0, 0, 0)
+
+
+def test_bench_roofline_and_kernel_label(api):
+    """bench.py's roofline entry: convention-A flops (20 per interaction, N^2
+    interactions per step) over the kernel time, against peaks from unit
+    counts (2 FP64 or 128 FP32 FMA lanes per SM, 152 SMs, 2070 MHz); and its
+    kernel label follows the library's own plan at every precision."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    assert abs(bench.PEAK_TFLOPS["f32"] - 80.54784) < 1e-6
+    assert abs(bench.PEAK_TFLOPS["fp64"] - 1.25856) < 1e-6
+    r = bench.roofline("mixed_split", 100000, 4.853)
+    assert abs(r["achieved"] - 20 * 1e10 / 4.853e-3 / 1e12) < 1e-3
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-4
+    assert r["traffic"] == bench.NCU_TRAFFIC[("mixed_split", 100000)]
+    assert bench.roofline("fp64", 100000, 91.0)["peak"] == round(bench.PEAK_TFLOPS["fp64"], 2)
+    for prec in ("fp64", "df64", "mixed", "mixed_split"):
+        for n in (bench.SYM_FROM[prec] - 1, bench.SYM_FROM[prec], 16384, 100000):
+            sym = api.plan_info("force", prec, n)["symmetric"] == 1
+            assert bench.roofline(prec, n, 1.0)["kernel"].startswith("k_pair_sym" if sym else "k_pair_force"), \
+                (prec, n)
