@@ -25,12 +25,13 @@ __device__ __forceinline__ void chunk_sum3(const double *__restrict__ part, int 
 
 // The epilogues run with EPI_THREADS threads per block, one of two ways:
 //  - one thread per ion, adding its chunk partials with chunk_sum3;
-//  - eight lanes per ion (the default): lane u forms slot_sum3's running sum u
-//    (chunks u, u+8, ...), three shuffle levels add the eight in slot_sum3's
-//    pairing, and the block's 32 sums go through shared memory to its first
-//    warp, which finishes one ion per lane.  The dependent chain of the sum is
-//    spread over eight threads, and the FP64 tail of the epilogue still serves
-//    32 ions per warp instruction.
+//  - eight threads per ion (the default): warp u of a block forms slot_sum3's
+//    running sum u (chunks u, u+8, ...) for the block's 32 ions, and the
+//    eight sums go through shared memory to the first warp, which adds them in
+//    slot_sum3's pairing and finishes one ion per lane.  The dependent chain
+//    of the sum is spread over eight threads, each warp load reads 256
+//    contiguous bytes, and the FP64 tail still serves 32 ions per warp
+//    instruction.
 // Both give the same sums, bit for bit.  epi_sums returns false for threads
 // without an ion (the caller then returns); it holds a block barrier in the
 // eight-lane form, so every thread of the block must call it.
@@ -45,9 +46,13 @@ __device__ __forceinline__ bool epi_sums(const double *__restrict__ part, int n_
     chunk_sum3(part, n_jc, n, i, cs);
     return true;
   }
-  const int64_t g = ((int64_t)blockIdx.x * EPI_THREADS + threadIdx.x) >> 3;
-  const int u = threadIdx.x & 7;
-  const int64_t ig = g < n ? g : n - 1;  // every lane takes part in the shuffles
+  // Warp u of the block forms running sum u (slots u, u+8, ...) for the
+  // block's 32 ions, one ion per lane: each load of a warp reads one slot of
+  // 32 consecutive ions, 256 contiguous bytes (two L1 lines).
+  static_assert(EPI_THREADS == 256, "eight warps, one per running sum");
+  const int u = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * 32 + l;
+  const int64_t ig = g < n ? g : n - 1;  // every warp reaches the barrier
   cs[0] = cs[1] = cs[2] = 0.0;
   const double *pi = part + ig;
   for (int jc = u; jc < n_jc; jc += 8) {
@@ -56,33 +61,25 @@ __device__ __forceinline__ bool epi_sums(const double *__restrict__ part, int n_
     cs[1] += __ldcs(q + n);
     cs[2] += __ldcs(q + 2 * n);
   }
-#pragma unroll
-  for (int d = 1; d < 8; d <<= 1) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double o = __shfl_down_sync(0xffffffffu, cs[c], d, 8);
-      if ((u & (2 * d - 1)) == 0) cs[c] = cs[c] + o;
-    }
-  }
-  __shared__ double csum[3][EPI_THREADS / 8];
-  if (u == 0) {
-    csum[0][threadIdx.x >> 3] = cs[0];
-    csum[1][threadIdx.x >> 3] = cs[1];
-    csum[2][threadIdx.x >> 3] = cs[2];
-  }
+  __shared__ double csum[3][8][32];
+  csum[0][u][l] = cs[0];
+  csum[1][u][l] = cs[1];
+  csum[2][u][l] = cs[2];
   __syncthreads();
-  if (threadIdx.x >= EPI_THREADS / 8) return false;
-  i = (int64_t)blockIdx.x * (EPI_THREADS / 8) + threadIdx.x;
+  if (threadIdx.x >= 32) return false;
+  i = g;
   if (i >= n) return false;
-  cs[0] = csum[0][threadIdx.x];
-  cs[1] = csum[1][threadIdx.x];
-  cs[2] = csum[2][threadIdx.x];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {  // slot_sum3's pairing of the eight running sums
+    const double(*s)[32] = csum[c];
+    cs[c] = ((s[0][l] + s[1][l]) + (s[2][l] + s[3][l])) + ((s[4][l] + s[5][l]) + (s[6][l] + s[7][l]));
+  }
   return true;
 }
 
-// Eight lanes per ion unless tuning kind 8 says one (R = 0) for this n:
-// measured on GB300 the eight-lane form was faster at every n up to 1e5
-// (17-32 % of a step at n = 2500-6000) and level at 1e5.
+// Eight threads per ion unless tuning kind 8 says one (R = 0) for this n:
+// measured on GB300 the eight-thread form was faster at every n up to 1e5
+// (17-32 % of a step at n = 2500-6000; 148 against 170 us at 1e5).
 static bool epi_eight(int64_t n) {
   int tb = 0, tr = 0, tbps = 0;
   if (tuning_lookup(8, 0, n, &tb, &tr, &tbps)) return tr == 1;
