@@ -35,9 +35,11 @@
 
 namespace nb {
 
-// 256 threads (8 warps) per item; 128 (4 warps) for 128-ion blocks (G = 4),
-// which give enough items to fill the GPU from n = 4096.  The staggered
-// schedule needs at least as many P-tiles as warps.
+// Threads per item: one warp per 32-ion tile for 32- and 64-ion blocks
+// (G <= 2, the small n where items are few); 128 (4 warps) for 128-ion
+// blocks (G = 4); 256 (8 warps) above, and 512 for the split kernel's
+// 1024-ion blocks.  The staggered schedule needs at least as many P-tiles
+// as warps.
 constexpr int SYM_THREADS = 256;
 constexpr int SYM_THREADS_SMALL = 128;
 constexpr double SYM_FAR = 1e18;
