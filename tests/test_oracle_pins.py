@@ -380,6 +380,72 @@ def test_forces_vjp_matches_fd(orc):
         assert rel(np.sum(g * delta), fd) < 1e-7
 
 
+def _verlet_1d(x0, v0, w, dt, T):
+    """Exact discrete velocity-Verlet solution of x'' = -w^2 x after T steps
+    (Sec. II update; cos th = 1 - (w dt)^2/2): x_T and its derivatives with
+    respect to x0, v0 and w."""
+    th = math.acos(1 - (w * dt) ** 2 / 2)
+    s, c, sT, cT = math.sin(th), math.cos(th), math.sin(T * th), math.cos(T * th)
+    xT = x0 * cT + dt * v0 * sT / s
+    dx_dth = -T * x0 * sT + dt * v0 * (T * cT * s - sT * c) / (s * s)
+    dth_dw = w * dt * dt / s
+    return xT, cT, dt * sT / s, dx_dth * dth_dw
+
+
+def test_trajectory_loss_single_ion_closed_form(orc):
+    """One ion (no Coulomb term) in a static harmonic trap: the trajectory
+    loss L = (m/2) sum_k w_k^2 x_T,k^2 + |x_T - target|^2 and its gradients
+    follow from the exact discrete Verlet solution x_T = x0 cos(T th) +
+    dt v0 sin(T th)/sin(th), component by component.  A forward that drops
+    the dt^2 a/2 drift term, takes a_0 at the wrong state, or a loss that
+    drops the trap energy or the target term fails here."""
+    m, dt, T = W.MASS_40U, 3e-9, 700
+    w = (2 * math.pi * 1.1e6, 2 * math.pi * 0.8e6, 2 * math.pi * 210e3)
+    x0 = np.array([[1.3e-6], [-2.1e-6], [4.7e-6]])
+    v0 = np.array([[0.21], [-0.07], [0.33]])
+    tgt = np.array([[0.4e-6], [0.9e-6], [-3.0e-6]])
+    p = P(orc, omega=w, dt=dt)
+    loss, gx, gv, gw = orc.trajectory_grad(p, x0, v0, T, tgt)
+    L_ref = 0.0
+    for k in range(3):
+        xT, dxx, dxv, dxw = _verlet_1d(x0[k, 0], v0[k, 0], w[k], dt, T)
+        dLdx = m * w[k] ** 2 * xT + 2 * (xT - tgt[k, 0])
+        L_ref += 0.5 * m * w[k] ** 2 * xT ** 2 + (xT - tgt[k, 0]) ** 2
+        amp = abs(dLdx) * math.hypot(1.0, dt / math.sin(math.acos(1 - (w[k] * dt) ** 2 / 2)))
+        assert abs(gx[k, 0] - dLdx * dxx) <= 1e-9 * amp, k
+        assert abs(gv[k, 0] - dLdx * dxv) <= 1e-9 * amp, k
+        gw_ref = m * w[k] * xT ** 2 + dLdx * dxw
+        assert rel(gw[k], gw_ref) < 1e-8, (k, gw[k], gw_ref)
+    assert rel(loss, L_ref) < 1e-11
+
+
+def test_trajectory_loss_matches_run_and_energy(orc):
+    """With Coulomb interactions: the adjoint's own forward and loss equal a
+    run of the pinned integrator (or_run, Sec. II) followed by the pinned
+    energies (or_energy) and the squared distance to the target, evaluated
+    here separately.  The target sits 3 pm from the run's final positions, so
+    the three terms are of one size (about 1e-22 in the loss's plain SI sum)
+    and a forward that strays by more than about 1e-14 m changes the loss."""
+    rng = np.random.default_rng(31)
+    n, nsteps = 6, 250
+    a, c = W.cold_fluid_spheroid(n, 2 * math.pi * 1e6, 2 * math.pi * 200e3)
+    x0 = W.ellipsoid_uniform(n, (a, a, c), rng)
+    v0 = W.thermal_velocities(n, 1e-3, W.MASS_40U, rng)
+    p = P(orc, omega=(2 * math.pi * 1e6, 2 * math.pi * 0.9e6, 2 * math.pi * 200e3), dt=2e-9)
+    ax, ay, az = orc.accel(p, 0.0, *x0)
+    st = dict(x=x0[0], y=x0[1], z=x0[2], vx=v0[0], vy=v0[1], vz=v0[2], ax=ax, ay=ay, az=az, step=0)
+    st = orc.run(p, st, nsteps)
+    xT = np.stack([st["x"], st["y"], st["z"]])
+    target = xT + 3e-12 * rng.choice([-1.0, 1.0], size=(3, n))
+    loss = orc.trajectory_grad(p, x0, v0, nsteps, target)[0]
+    e = orc.energy(p, 0, *xT, st["vx"], st["vy"], st["vz"])
+    d2 = float(np.sum((xT - target) ** 2))
+    ref = math.fsum([e[1], e[2], d2])
+    for term in (e[1], e[2], d2):  # trap, Coulomb and target terms all count
+        assert term > 0.05 * ref, (e, d2)
+    assert rel(loss, ref) < 1e-9, (loss, ref)
+
+
 def test_trajectory_grad_matches_fd(orc):
     """Discrete adjoint of the Verlet trajectory vs Richardson-extrapolated
     central differences, in random x0 directions and in each omega_k."""
