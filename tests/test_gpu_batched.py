@@ -9,6 +9,8 @@ import torch
 
 from paper_2106_11143_gb300 import workloads as W
 
+import floors
+
 pytestmark = pytest.mark.gpu
 
 
@@ -47,12 +49,6 @@ def oracle_instance(orc, phys, off, pos, vel, k, nsteps, eps=0.0):
     return orc.run(p, st, nsteps)
 
 
-def contract_floor(ref, nsteps, dt):
-    """Trajectory drift that the force contract itself allows: a force error
-    of 1e-12 of the largest acceleration in every step, accumulated over the
-    run (velocity: k dt eps |a|; position: k^2 dt^2 eps |a|)."""
-    amax = max(np.max(np.abs(ref[k])) for k in ("ax", "ay", "az"))
-    return nsteps * nsteps * dt * dt * 1e-12 * amax, nsteps * dt * 1e-12 * amax
 
 
 def run_gpu(nb, phys, off, pos, vel, nsteps, chunks=1, precision="fp64"):
@@ -83,12 +79,15 @@ def test_batched_matches_oracle_per_instance(nb, orc, precision):
         rv = np.stack([ref["vx"], ref["vy"], ref["vz"]])
         up = np.stack([ulp["x"], ulp["y"], ulp["z"]])
         uv = np.stack([ulp["vx"], ulp["vy"], ulp["vz"]])
-        dp, dv = np.max(np.abs(gp[:, i0:i1] - rp)), np.max(np.abs(gv[:, i0:i1] - rv))
+        ep, ev = floors.per_ion(gp[:, i0:i1] - rp), floors.per_ion(gv[:, i0:i1] - rv)
         sp, sv = np.max(np.abs(up - rp)), np.max(np.abs(uv - rv))
-        print("instance %d (n=%d): gpu dp=%.3g dv=%.3g | self dp=%.3g dv=%.3g" % (k, sizes[k], dp, dv, sp, sv))
-        fp, fv = contract_floor(ref, nsteps, phys["dt"])
-        assert dp <= 10 * sp + fp
-        assert dv <= 10 * sv + fv
+        print("instance %d (n=%d): gpu dp=%.3g dv=%.3g | self dp=%.3g dv=%.3g"
+              % (k, sizes[k], np.max(ep), np.max(ev), sp, sv))
+        ph = dict(phys)
+        ph["instance"] = k
+        fp, fv = floors.contract_floor(orc, orc.make_params(**ph), [pos[:, i0:i1], rp], nsteps, phys["dt"])
+        assert np.all(ep <= 10 * sp + fp), k
+        assert np.all(ev <= 10 * sv + fv), k
 
 
 def test_batched_equals_standalone_instances(nb):
@@ -171,12 +170,15 @@ def test_full_ensemble_sampled(nb, orc, precision):
         rp = np.stack([ref["x"], ref["y"], ref["z"]])
         uv = np.stack([ulp["vx"], ulp["vy"], ulp["vz"]])
         up = np.stack([ulp["x"], ulp["y"], ulp["z"]])
-        dv, sv = np.max(np.abs(gv[:, i0:i1] - rv)), np.max(np.abs(uv - rv))
-        dp, sp = np.max(np.abs(gp[:, i0:i1] - rp)), np.max(np.abs(up - rp))
-        print("instance %d (n=%d): gpu dp=%.3g dv=%.3g | self dp=%.3g dv=%.3g" % (k, sizes[k], dp, dv, sp, sv))
-        fp, fv = contract_floor(ref, nsteps, phys["dt"])
-        assert dv <= 10 * sv + fv
-        assert dp <= 10 * sp + fp
+        ev, sv = floors.per_ion(gv[:, i0:i1] - rv), np.max(np.abs(uv - rv))
+        ep, sp = floors.per_ion(gp[:, i0:i1] - rp), np.max(np.abs(up - rp))
+        print("instance %d (n=%d): gpu dp=%.3g dv=%.3g | self dp=%.3g dv=%.3g"
+              % (k, sizes[k], np.max(ep), np.max(ev), sp, sv))
+        ph = dict(phys)
+        ph["instance"] = int(k)
+        fp, fv = floors.contract_floor(orc, orc.make_params(**ph), [pos[:, i0:i1], rp], nsteps, phys["dt"])
+        assert np.all(ev <= 10 * sv + fv), k
+        assert np.all(ep <= 10 * sp + fp), k
 
 
 @pytest.mark.parametrize("precision", ["fp64", "df64"])

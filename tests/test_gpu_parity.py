@@ -14,6 +14,8 @@ import torch
 
 from paper_2106_11143_gb300 import workloads as W
 
+import floors
+
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6}
@@ -238,6 +240,19 @@ def _gpu_traj(nb, phys, pos, vel, nsteps, precision="fp64", chunks=1, q=None):
     return sysm
 
 
+def _assert_traj_per_ion(orc, phys, pos0, sysm, ref, nsteps, tol_p, tol_v):
+    """Per ion: |x_gpu - x_oracle| <= tol_p + the force contract's position
+    floor of that ion, and the same for velocities (floors.contract_floor)."""
+    gp = sysm.pos().cpu().numpy()
+    gv = sysm.vel().cpu().numpy()
+    rp = np.stack([ref["x"], ref["y"], ref["z"]])
+    rv = np.stack([ref["vx"], ref["vy"], ref["vz"]])
+    fp, fv = floors.contract_floor(orc, oparams(orc, phys), [pos0, rp], nsteps, phys["dt"])
+    ep, ev = floors.per_ion(gp - rp), floors.per_ion(gv - rv)
+    assert np.all(ep <= tol_p + fp), (int(np.argmax(ep - fp)), float(np.max(ep - tol_p - fp)))
+    assert np.all(ev <= tol_v + fv), (int(np.argmax(ev - fv)), float(np.max(ev - tol_v - fv)))
+
+
 def _traj_errs(sysm, ref):
     gp = sysm.pos().cpu().numpy()
     gv = sysm.vel().cpu().numpy()
@@ -265,12 +280,10 @@ def test_trajectory_parity(nb, orc, which, precision):
     L = np.max(np.abs(w["pos"]))
     V = math.sqrt(W.K_B * 10e-3 / W.MASS_40U)
     print("%s: gpu dp=%.3g dv=%.3g | oracle self dp=%.3g dv=%.3g" % (which, dp, dv, dp_self, dv_self))
-    amax = max(np.max(np.abs(ref[k])) for k in ("ax", "ay", "az"))
-    k, dt = nsteps, phys["dt"]
-    # 10x the oracle's own one-ulp sensitivity, plus the drift the force
-    # contract allows (a 1e-12 relative force error in every step)
-    assert dp <= max(10 * dp_self, 1e-14 * L) + k * k * dt * dt * 1e-12 * amax
-    assert dv <= max(10 * dv_self, 1e-14 * V) + k * dt * 1e-12 * amax
+    # 10x the oracle's own one-ulp sensitivity, plus, per ion, the drift the
+    # force contract allows (floors.contract_floor)
+    _assert_traj_per_ion(orc, phys, w["pos"], sysm, ref, nsteps, max(10 * dp_self, 1e-14 * L),
+                         max(10 * dv_self, 1e-14 * V))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
@@ -287,10 +300,8 @@ def test_trajectory_full_size_rf(nb, orc, precision):
     L = np.max(np.abs(w["pos"]))
     V = math.sqrt(W.K_B * 10e-3 / W.MASS_40U)
     print("rf N=16384 %s: gpu dp=%.3g dv=%.3g | oracle self dp=%.3g dv=%.3g" % (precision, dp, dv, dp_self, dv_self))
-    amax = max(np.max(np.abs(ref[k])) for k in ("ax", "ay", "az"))
-    k, dt = nsteps, phys["dt"]
-    assert dp <= max(10 * dp_self, 1e-14 * L) + k * k * dt * dt * 1e-12 * amax
-    assert dv <= max(10 * dv_self, 1e-14 * V) + k * dt * 1e-12 * amax
+    _assert_traj_per_ion(orc, phys, w["pos"], sysm, ref, nsteps, max(10 * dp_self, 1e-14 * L),
+                         max(10 * dv_self, 1e-14 * V))
 
 
 def _traj_errs_np(a, b):
