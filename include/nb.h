@@ -344,11 +344,14 @@ nb_status nb_traj_backward(const nb_params *params, const nb_system *sys, int64_
  * this serves callers that cannot call cudaMalloc -- cudaMalloc may
  * synchronise the device, which a latency-bound loop cannot afford, and under
  * a host framework that owns device memory through its own pool it can fail
- * or take memory budgeted elsewhere.  Same inputs, outputs and arithmetic as
- * nb_energy (out[4] in HOST memory; synchronises the stream).  Its scratch is
- * one fixed 8 MiB device array inside the library, held on every GPU that
- * loads the library until the process exits; n above what it can hold (about
- * 1,000,000) is rejected with NB_EINVAL and a message in nb_last_error().
+ * or take memory budgeted elsewhere.  Same inputs, outputs, argument checks
+ * and arithmetic as nb_energy (out[4] in HOST memory; synchronises the
+ * stream).  Its scratch is one fixed 8 MiB device array inside the library,
+ * held on every GPU that loads the library until the process exits; n above
+ * what it can hold is rejected with NB_EINVAL and a message in
+ * nb_last_error().  With the default plan on a 152-SM GB300 the limit is
+ * about n = 1,000,000; a potential-kernel tuning override (nb_set_tuning
+ * kind 1) or a GPU with more SMs can lower it.
  * All calls share that array: calls that may overlap on the GPU (other
  * streams, unordered host threads) race and must be serialised.  The first
  * call on each device looks up the array's device address with that device

@@ -23,8 +23,8 @@ cudaError_t launch_chunk_sum1(int64_t n, const double *part, int n_jc, double sc
                               cudaStream_t st);
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
 nb_status fail(nb_status s, const char *fmt, ...) {
   char buf[512];
@@ -35,6 +35,8 @@ nb_status fail(nb_status s, const char *fmt, ...) {
   g_last_error = buf;
   return s;
 }
+
+namespace {
 
 #define NB_CUDA_TRY(call)                                                              \
   do {                                                                                 \
@@ -115,6 +117,15 @@ struct Carver {
 };
 
 bool finite(double v) { return std::isfinite(v); }
+bool aligned8(const void *ptr) { return ((uintptr_t)ptr & 7u) == 0; }
+
+nb_status check_array(const void *ptr, const char *name) {
+  if (!ptr) return fail(NB_EINVAL, "%s is NULL", name);
+  if (!aligned8(ptr)) return fail(NB_EINVAL, "%s is not 8-byte aligned", name);
+  return NB_OK;
+}
+
+}  // namespace
 
 nb_status check_params(const nb_params *p) {
   if (!p) return fail(NB_EINVAL, "params is NULL");
@@ -134,20 +145,6 @@ nb_status check_params(const nb_params *p) {
   if (p->reserved != 0) return fail(NB_EINVAL, "params.reserved must be 0");
   return NB_OK;
 }
-
-bool aligned8(const void *ptr) { return ((uintptr_t)ptr & 7u) == 0; }
-
-nb_status check_array(const void *ptr, const char *name) {
-  if (!ptr) return fail(NB_EINVAL, "%s is NULL", name);
-  if (!aligned8(ptr)) return fail(NB_EINVAL, "%s is not 8-byte aligned", name);
-  return NB_OK;
-}
-
-#define NB_TRY(expr)          \
-  do {                        \
-    nb_status s_ = (expr);    \
-    if (s_ != NB_OK) return s_; \
-  } while (0)
 
 nb_status check_system(const nb_system *s, bool need_v, bool need_a) {
   if (!s) return fail(NB_EINVAL, "system is NULL");
@@ -206,6 +203,8 @@ StateView to_view(const nb_system *s) {
   v.m = s->m;
   return v;
 }
+
+namespace {
 
 // Scratch need of one force evaluation.
 size_t force_bytes(const Plan &pl, int mode, int64_t n, bool extra_pos, bool phi, const Plan &plp) {

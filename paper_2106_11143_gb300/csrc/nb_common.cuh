@@ -591,6 +591,18 @@ struct Plan {
 Plan make_plan(int64_t n, int mode, int kind);  // kind: 0 force, 1 phi, 2 vjp
 int device_sm_count();
 
+// Host-side argument checks shared by every entry point (nb_api.cu): they
+// record a message for nb_last_error() and return NB_EINVAL before any CUDA
+// call.  fail() records a printf-style message and returns `s`.
+nb_status fail(nb_status s, const char *fmt, ...);
+nb_status check_params(const nb_params *p);
+nb_status check_system(const nb_system *s, bool need_v, bool need_a);
+#define NB_TRY(expr)            \
+  do {                          \
+    nb_status s_ = (expr);      \
+    if (s_ != NB_OK) return s_; \
+  } while (0)
+
 // Launch accounting and optional event timing of pair kernels (nb_api.cu).
 void count_launches(uint64_t k);
 void record_error(const char *msg);  // message returned by nb_last_error()
@@ -648,6 +660,9 @@ __device__ __forceinline__ double trap_scale(const Phys &p, const StateView &s, 
   const double qi = s.q ? s.q[i] : p.charge;
   return (qi / ion_mass(p, s, i)) / (p.charge / p.mass);
 }
+// The kernels' view of the ABI structs (nb_api.cu).
+Phys to_phys(const nb_params *p);
+StateView to_view(const nb_system *s);
 cudaError_t launch_epi_forces(const Phys &p, const StateView &s, const double *part, int n_jc,
                               int flags, double t, unsigned *err, cudaStream_t st);
 cudaError_t launch_epi_vjp(const Phys &p, const StateView &s, const double *part, int n_jc,

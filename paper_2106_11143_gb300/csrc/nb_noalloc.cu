@@ -19,7 +19,6 @@
 // ordering) race on it and give wrong results; serialise them.  Each call
 // overwrites every scratch word it reads before reading it, so nothing has
 // to start at zero and the contents left by the previous call do not matter.
-#include <cstdio>
 #include <mutex>
 
 #include "nb_common.cuh"
@@ -27,8 +26,11 @@
 namespace nb {
 
 // Scratch capacity: 8 MiB of doubles.  It bounds n through the launch plan of
-// the potential kernel: n_jc * n + 3 * ENERGY_BLOCKS + 4 doubles must fit,
-// which holds for every n up to 1,000,000.
+// the potential kernel: n_jc * n + 3 * ENERGY_BLOCKS + 4 doubles must fit.
+// With the default plan on a 152-SM GB300 that holds for every n up to about
+// 1,000,000 (n_jc * n is about the SM count times the plan's blocks per SM
+// times its block size); a potential-kernel tuning override (nb_set_tuning
+// kind 1) or a GPU with more SMs can lower the limit.
 constexpr size_t NOALLOC_SCRATCH_DOUBLES = (size_t)1 << 20;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
@@ -65,70 +67,42 @@ using namespace nb;
 extern "C" nb_status nb_energy_noalloc(const nb_params *params, const nb_system *sys,
                                        double out[4], void *stream) {
   NvtxRange range_("nb_energy_noalloc");
-  if (!params || !sys || !out) return NB_EINVAL;
-  if (!(params->mass > 0.0) || params->soft2 < 0.0 || params->reserved != 0 ||
-      (params->trap != NB_TRAP_HARMONIC && params->trap != NB_TRAP_RF))
-    return NB_EINVAL;
+  // The same host-side checks as nb_energy, before any CUDA call.
+  NB_TRY(check_params(params));
+  NB_TRY(check_system(sys, true, false));
+  if (!out) return fail(NB_EINVAL, "out is NULL");
   const int64_t n = sys->n;
-  if (n < 0) return NB_EINVAL;
   if (n == 0) {
     out[0] = out[1] = out[2] = out[3] = 0.0;
     return NB_OK;
   }
-  if (!sys->x || !sys->y || !sys->z || !sys->vx || !sys->vy || !sys->vz) return NB_EINVAL;
   const Plan pl = make_plan(n, MODE_FP64, 1);
   const size_t need = (size_t)pl.n_jc * (size_t)n + 3 * ENERGY_BLOCKS + 4;
-  if (need > NOALLOC_SCRATCH_DOUBLES) {
-    char msg[256];
-    snprintf(msg, sizeof(msg),
-             "nb_energy_noalloc: n = %lld needs %zu scratch doubles, above its fixed %zu "
-             "(8 MiB); use nb_energy",
-             (long long)n, need, NOALLOC_SCRATCH_DOUBLES);
-    record_error(msg);
-    return NB_EINVAL;
-  }
+  if (need > NOALLOC_SCRATCH_DOUBLES)
+    return fail(NB_EINVAL,
+                "nb_energy_noalloc: n = %lld needs %zu scratch doubles, above its fixed %zu "
+                "(8 MiB); use nb_energy",
+                (long long)n, need, NOALLOC_SCRATCH_DOUBLES);
   double *scratch = nullptr;
-  if (noalloc_scratch(&scratch) != cudaSuccess) return NB_ECUDA;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess)
+    return fail(NB_ECUDA, "nb_energy_noalloc: cudaGetSymbolAddress of the scratch array failed: %s",
+                cudaGetErrorString(e));
   double *ppart = scratch;
   double *bpart = ppart + (size_t)pl.n_jc * (size_t)n;
   double *out4 = bpart + 3 * ENERGY_BLOCKS;
-
-  Phys p;
-  p.k_coulomb = params->k_coulomb;
-  p.mass = params->mass;
-  p.charge = params->charge;
-  p.soft2 = params->soft2;
-  p.trap = params->trap;
-  p.precision = params->precision;
-  for (int k = 0; k < 3; ++k) {
-    p.omega[k] = params->omega[k];
-    p.omega_rate[k] = params->omega_rate[k];
-  }
-  p.q_mathieu = params->q_mathieu;
-  p.omega_rf = params->omega_rf;
-  p.rf_phase = params->rf_phase;
-  p.gamma = params->gamma;
-  p.dt = params->dt;
-  p.t0 = params->t0;
-  p.noise_T = params->noise_T;
-  p.seed = params->seed;
-  p.instance = params->instance;
-  StateView v;
-  v.n = n;
-  v.x = sys->x; v.y = sys->y; v.z = sys->z;
-  v.vx = sys->vx; v.vy = sys->vy; v.vz = sys->vz;
-  v.ax = sys->ax; v.ay = sys->ay; v.az = sys->az;
-  v.q = sys->q;
-  v.m = sys->m;
+  const Phys p = to_phys(params);
+  const StateView v = to_view(sys);
   const double t = params->t0 + (double)sys->step * params->dt;
   cudaStream_t st = (cudaStream_t)stream;
-  if (launch_pair_phi(pl, n, sys->x, sys->y, sys->z, sys->q, params->charge, params->soft2,
-                      ppart, st) != cudaSuccess)
-    return NB_ECUDA;
-  if (launch_energy(p, v, ppart, pl.n_jc, t, bpart, out4, st) != cudaSuccess) return NB_ECUDA;
-  count_launches(3);
-  if (cudaMemcpyAsync(out, out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return NB_ECUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return NB_ECUDA;
+  e = launch_pair_phi(pl, n, sys->x, sys->y, sys->z, sys->q, params->charge, params->soft2, ppart, st);
+  if (e == cudaSuccess) e = launch_energy(p, v, ppart, pl.n_jc, t, bpart, out4, st);
+  if (e == cudaSuccess) {
+    count_launches(3);
+    e = cudaMemcpyAsync(out, out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess)
+    return fail(NB_ECUDA, "nb_energy_noalloc: %s", cudaGetErrorString(e));
   return NB_OK;
 }

@@ -219,6 +219,21 @@ def test_vjp_and_potential_plans_shared_by_precisions(api):
         api.set_tuning("force", "fp64", 0, 0, 0)
 
 
+def test_noalloc_capacity_holds_to_a_million(api):
+    """nb_energy_noalloc's fixed array (2^20 doubles) holds the potential
+    plan's partials (n_jc * n) plus 3 * 128 + 4 reduction doubles for every
+    n up to 1e6 with the default plan on 152 SMs (the host-only planner's
+    GPU), and no longer at 1.1e6, which its GPU test rejects."""
+    cap = 1 << 20
+    ns = sorted(set(np.unique(np.geomspace(1, 1_000_000, 400).astype(np.int64)).tolist()
+                    + list(range(999_000, 1_000_001, 97)) + [1_000_000]))
+    for n in ns:
+        p = api.plan_info("potential", "fp64", n)
+        assert p["n_jc"] * n + 3 * 128 + 4 <= cap, (n, p)
+    p = api.plan_info("potential", "fp64", 1_100_000)
+    assert p["n_jc"] * 1_100_000 + 388 > cap
+
+
 def test_bench_roofline_and_kernel_label(api):
     """bench.py's roofline entry: convention-A flops (20 per interaction, N^2
     interactions per step) over the kernel time, against peaks from unit
