@@ -196,6 +196,31 @@ nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi,
 nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps,
                   void *stream);
 
+/* ---- i-range sharding (Sec. VI.C's static ownership of target ions) ----
+ * One rank (one GPU) owns the ions [i0, i1) of the system; every rank holds
+ * all n positions.  A velocity-Verlet step of nb_step is split around the
+ * one exchange it needs:
+ *   nb_step_range_drift   r_i += v_i dt + a_i dt^2/2 for the owned ions;
+ *   (the caller exchanges the owned positions so every rank has all n,
+ *    e.g. one all-gather of 3 (i1 - i0) doubles per rank)
+ *   nb_step_range_kick    a+_i from all n positions at t + dt and the kick
+ *                         of the owned ions, exactly as nb_step's epilogue
+ *                         (friction, trap, Langevin draws keyed by the
+ *                         global ion index); advances sys->step by one.
+ * The pair sums come from the one-sided kernel with the chunks of the full
+ * one-sided plan, so the ranks' results, put together, are bitwise those
+ * of a single call with the symmetric kernel disabled (nb_set_tuning kind
+ * 4, R = 0).  Only the owned entries of x (drift) and of v and a (kick) are
+ * written.  0 <= i0 <= i1 <= n, else NB_EINVAL; i0 == i1 does nothing (the
+ * kick still advances the step counter).  nb_forces_range writes the
+ * acceleration of the owned ions only, as nb_forces (flags) would.       */
+nb_status nb_forces_range(const nb_params *params, const nb_system *sys, int64_t i0, int64_t i1,
+                          int flags, void *stream);
+nb_status nb_step_range_drift(const nb_params *params, nb_system *sys, int64_t i0, int64_t i1,
+                              void *stream);
+nb_status nb_step_range_kick(const nb_params *params, nb_system *sys, int64_t i0, int64_t i1,
+                             void *stream);
+
 /* Energies at the current state, written to HOST memory out[4] =
  * {kinetic, trap, Coulomb, total} in joules:
  *   kinetic = (m/2) sum |v|^2,
@@ -263,13 +288,24 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
  * kernel) or 2 (the VJP kernel, fp64 and df64 alike; for kinds 1 and 2
  * `precision` is validated but does not change the plan), with the current tuning overrides:
  * out[0] threads per block (one-sided) or 256 / 128 (symmetric), out[1] ions
- * per thread R, out[2] partners per j-chunk, out[3] i-tiles, out[4] partial
- * slots n_jc (j-chunks, or partner blocks of the symmetric kernel), out[5]
+ * per thread R, out[2] partners per j-chunk, out[3] i-tiles (one-sided) or
+ * blocks nbk (symmetric), out[4] partial slots n_jc (j-chunks; 1 for the
+ * symmetric kernel, which adds into one slot in a fixed round order), out[5]
  * 1 for the symmetric kernel, out[6] its ions per block / 32, out[7] 1 if
  * nb_step would run the single-block path (kind 0).  Without a usable GPU
- * it plans for 152 SMs and a 2 GB cap on the symmetric partials.  No
- * device work.                                                            */
+ * it plans for 152 SMs.  No device work.                                  */
 nb_status nb_plan_info(int32_t kind, int32_t precision, int64_t n, int64_t out[8]);
+
+/* Host-only: the work schedule of the half-pair kernels for nbk blocks
+ * (1 <= nbk <= 60000): item t (0 <= t < nbk (nbk + 1) / 2) is the block pair
+ * (P[t], Q[t]), P <= Q, in round round[t].  Each round touches every block
+ * exactly once (a round-robin tournament; a block's own pairs, P == Q, take
+ * its one free round), items are numbered round by round, and every item
+ * adds its sums into the output after the previous round's items of the same
+ * blocks, which fixes the order of each ion's sum (the paper's Sec. VI.C
+ * static ownership, made deterministic for a GPU).  Arrays in HOST memory.
+ * No GPU.                                                                 */
+nb_status nb_sym_schedule(int32_t nbk, int32_t *P, int32_t *Q, int32_t *round);
 
 /* Launch-shape override (used by the autotuner, paper_2106_11143_gb300/
  * tune.py).  For kind 0 (force), 1 (potential), 2 (VJP) pair kernels in
@@ -380,6 +416,19 @@ nb_status nb_rinv3_probe(int precision, int64_t n, const double *dx, const doubl
  * (rsqrt.approx.ftz.f32, Sec. IV's counterpart of RSQRT14), for the seed's
  * error bound.  Device arrays of n floats, caller-owned; asynchronous.      */
 nb_status nb_rsqrt_seed_probe(int64_t n, const float *x, float *y, void *stream);
+
+/* Throughput of one instruction kind on every SM of the current device: the
+ * measured denominators of the ALU rooflines (Sec. VI reports the method's
+ * speed as a fraction of the FMA peak; this is that peak on the GPU).
+ * kind: 0 FP64 FMA, 1 FP64 add, 2 FP64 multiply, 3 FP32 FMA, 4 FP32 add,
+ * 5 FP32 reciprocal square root (MUFU).  Two blocks of 512 threads per SM
+ * each run eight independent dependence chains for 16 * iters instructions
+ * (1 <= iters <= 2^24).  out (HOST, 3 doubles): out[0] lanes retired per
+ * clock per SM (median over SMs, from the SM cycle counter), out[1] the SM
+ * clock in MHz over the launch (cycles / event time), out[2] the launch's
+ * duration in ms.  Allocates a few KB of device memory for the clock
+ * records and synchronises the stream.                                    */
+nb_status nb_pipe_probe(int32_t kind, int64_t iters, double out[3], void *stream);
 
 /* Synchronises `stream`, then returns and clears its device error word:
  * NB_OK, NB_ENONFINITE or NB_ETIMEOUT (or NB_ECUDA if the stream failed). */

@@ -91,10 +91,18 @@ def lib():
         L.nb_rinv3_probe.argtypes = [C.c_int32, C.c_int64, _dp, _dp, _dp, C.c_double, _dp, V]
         L.nb_rsqrt_seed_probe.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, V]
         L.nb_plan_info.argtypes = [C.c_int32, C.c_int32, C.c_int64, I64P]
+        L.nb_pipe_probe.argtypes = [C.c_int32, C.c_int64, _dp, V]
+        L.nb_forces_range.argtypes = [P, S, C.c_int64, C.c_int64, C.c_int, V]
+        L.nb_step_range_drift.argtypes = [P, S, C.c_int64, C.c_int64, V]
+        L.nb_step_range_kick.argtypes = [P, S, C.c_int64, C.c_int64, V]
+        I32P = C.POINTER(C.c_int32)
+        L.nb_sym_schedule.argtypes = [C.c_int32, I32P, I32P, I32P]
         for f in ("nb_forces", "nb_step", "nb_energy", "nb_forces_vjp", "nb_sync_status",
                   "nb_release", "nb_timing_enable", "nb_timing_read", "nb_step_batched",
                   "nb_plan_batched", "nb_set_tuning", "nb_energy_noalloc", "nb_traj_forward",
-                  "nb_traj_backward", "nb_rinv3_probe", "nb_rsqrt_seed_probe", "nb_plan_info"):
+                  "nb_traj_backward", "nb_rinv3_probe", "nb_rsqrt_seed_probe", "nb_plan_info",
+                  "nb_pipe_probe", "nb_sym_schedule", "nb_forces_range", "nb_step_range_drift",
+                  "nb_step_range_kick"):
             getattr(L, f).restype = C.c_int
         _LIB = L
     return _LIB
@@ -330,6 +338,30 @@ def step(params, system, nsteps, stream=None):
     system.step = s.step
 
 
+def forces_range(params, system, i0, i1, total=False, stream=None):
+    """nb_forces_range: the acceleration of ions [i0, i1) from all n ions,
+    written into system.ax/ay/az[i0:i1] only."""
+    s = system.to_c()
+    _check(lib().nb_forces_range(C.byref(params.to_c()), C.byref(s), int(i0), int(i1),
+                                 NB_ACC_TOTAL if total else NB_ACC_COULOMB, _stream(stream)), "nb_forces_range")
+
+
+def step_range_drift(params, system, i0, i1, stream=None):
+    """nb_step_range_drift: the drift half of a Verlet step for ions [i0, i1)."""
+    s = system.to_c()
+    _check(lib().nb_step_range_drift(C.byref(params.to_c()), C.byref(s), int(i0), int(i1), _stream(stream)),
+           "nb_step_range_drift")
+
+
+def step_range_kick(params, system, i0, i1, stream=None):
+    """nb_step_range_kick: forces from all n (drifted) positions and the kick
+    of ions [i0, i1); advances system.step by one."""
+    s = system.to_c()
+    _check(lib().nb_step_range_kick(C.byref(params.to_c()), C.byref(s), int(i0), int(i1), _stream(stream)),
+           "nb_step_range_kick")
+    system.step = s.step
+
+
 def energy(params, system, stream=None):
     """nb_energy: (kinetic, trap, Coulomb, total) in J as a numpy array."""
     out = np.empty(4)
@@ -436,6 +468,31 @@ def rsqrt_seed_probe(x, stream=None):
     _check(lib().nb_rsqrt_seed_probe(x.numel(), x.data_ptr(), y.data_ptr(), _stream(stream)),
            "nb_rsqrt_seed_probe")
     return y
+
+
+PIPE_KINDS = {"dfma": 0, "dadd": 1, "dmul": 2, "ffma": 3, "fadd": 4, "mufu_rsq": 5}
+# default rounds of 16 x 8 instructions per thread: a few ms per kind
+PIPE_ITERS = {"dfma": 256, "dadd": 256, "dmul": 256, "ffma": 4096, "fadd": 4096, "mufu_rsq": 1024}
+
+
+def pipe_probe(kind, iters=None, stream=None):
+    """nb_pipe_probe: measured throughput of one instruction kind on every SM.
+    Returns {"lanes_per_clk_per_sm", "sm_mhz", "ms"}."""
+    out = (C.c_double * 3)()
+    it = PIPE_ITERS[kind] if iters is None else int(iters)
+    _check(lib().nb_pipe_probe(PIPE_KINDS[kind], it, out, _stream(stream)), "nb_pipe_probe")
+    return {"lanes_per_clk_per_sm": out[0], "sm_mhz": out[1], "ms": out[2]}
+
+
+def sym_schedule(nbk):
+    """nb_sym_schedule: (P, Q, round) int32 arrays of the half-pair kernels'
+    work items for nbk blocks (host only)."""
+    m = nbk * (nbk + 1) // 2
+    P, Q, R = (np.empty(m, dtype=np.int32) for _ in range(3))
+    i32 = C.POINTER(C.c_int32)
+    _check(lib().nb_sym_schedule(int(nbk), P.ctypes.data_as(i32), Q.ctypes.data_as(i32), R.ctypes.data_as(i32)),
+           "nb_sym_schedule")
+    return P, Q, R
 
 
 def sync_status(stream=None):

@@ -16,6 +16,7 @@
 #include <utility>
 
 #include "nb_common.cuh"
+#include "nb_symsched.cuh"
 
 namespace nb {
 
@@ -209,7 +210,7 @@ namespace {
 // Scratch need of one force evaluation.
 size_t force_bytes(const Plan &pl, int mode, int64_t n, bool extra_pos, bool phi, const Plan &plp) {
   Carver c;
-  c.take<double>((size_t)pl.n_jc * 3 * n);
+  c.take<double>(part_doubles(pl, n, 3));
   if (mode == MODE_SPLIT) c.take<float>(6 * (size_t)n);
   if (extra_pos) c.take<double>(3 * (size_t)n);
   if (phi) c.take<double>((size_t)plp.n_jc * n);
@@ -219,7 +220,7 @@ size_t force_bytes(const Plan &pl, int mode, int64_t n, bool extra_pos, bool phi
 // Force evaluation at positions (x, y, z) into `part`.
 nb_status pair_forces(const Plan &pl, int mode, int64_t n, const double *x, const double *y,
                       const double *z, const double *q, double soft2, double *part, float *split,
-                      cudaStream_t st) {
+                      unsigned *err, cudaStream_t st) {
   PosF32 pf{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   if (mode == MODE_SPLIT) {
     NB_CUDA_TRY(launch_split_positions(n, x, y, z, split, st));
@@ -227,7 +228,7 @@ nb_status pair_forces(const Plan &pl, int mode, int64_t n, const double *x, cons
     pf = PosF32{split, split + n, split + 2 * n, split + 3 * n, split + 4 * n, split + 5 * n};
   }
   timing_begin(st);
-  NB_CUDA_TRY(launch_pair_force(pl, mode, n, x, y, z, q, pf, soft2, part, st));
+  NB_CUDA_TRY(launch_pair_force(pl, mode, n, x, y, z, q, pf, soft2, part, err, st));
   timing_end(st);
   count_launches(1);
   return NB_OK;
@@ -341,7 +342,7 @@ struct KeyBytes {
   }
 };
 
-static_assert(sizeof(Phys) == 160 && sizeof(StateView) == 96 && sizeof(Plan) == 32,
+static_assert(sizeof(Phys) == 160 && sizeof(StateView) == 104 && sizeof(Plan) == 40,
               "a new field of Phys, StateView or Plan must join window_key");
 
 std::vector<unsigned char> window_key(const Plan &pl, int mode, const Phys &p, const StateView &v,
@@ -350,7 +351,7 @@ std::vector<unsigned char> window_key(const Plan &pl, int mode, const Phys &p, c
   KeyBytes k;
   k.put(mode);
   k.put(tuning_generation());
-  k.put(pl.block); k.put(pl.R); k.put(pl.jchunk); k.put(pl.n_it); k.put(pl.n_jc); k.put(pl.sym); k.put(pl.G);
+  k.put(pl.block); k.put(pl.R); k.put(pl.jchunk); k.put(pl.n_it); k.put(pl.n_jc); k.put(pl.sym); k.put(pl.G); k.put(pl.nbk);
   k.put(p.k_coulomb); k.put(p.mass); k.put(p.charge); k.put(p.soft2); k.put(p.trap); k.put(p.precision);
   for (int c = 0; c < 3; ++c) {
     k.put(p.omega[c]);
@@ -359,7 +360,7 @@ std::vector<unsigned char> window_key(const Plan &pl, int mode, const Phys &p, c
   k.put(p.q_mathieu); k.put(p.omega_rf); k.put(p.rf_phase); k.put(p.gamma); k.put(p.dt); k.put(p.t0);
   k.put(p.noise_T); k.put(p.seed); k.put(p.instance);
   k.put(v.n); k.put(v.x); k.put(v.y); k.put(v.z); k.put(v.vx); k.put(v.vy); k.put(v.vz);
-  k.put(v.ax); k.put(v.ay); k.put(v.az); k.put(v.q); k.put(v.m);
+  k.put(v.ax); k.put(v.ay); k.put(v.az); k.put(v.q); k.put(v.m); k.put(v.ion0);
   for (int c = 0; c < 3; ++c) {
     k.put(A[c]);
     k.put(B[c]);
@@ -388,7 +389,7 @@ nb_status capture_window(Arena *a, const Plan &pl, int mode, const Phys &p, cons
   for (int64_t k = 1; k <= STEP_WINDOW && rc == NB_OK && e == cudaSuccess; ++k) {
     double *const *P = (k % 2) ? A : B;
     double *const *Nx = (k % 2) ? B : A;
-    rc = pair_forces(pl, mode, v.n, P[0], P[1], P[2], v.q, soft2, part, split, cs);
+    rc = pair_forces(pl, mode, v.n, P[0], P[1], P[2], v.q, soft2, part, split, a->err, cs);
     if (rc != NB_OK) break;
     const int64_t *cin = k == 1 ? c : c + 1;
     const int64_t soff = k == 1 ? 1 : k - STEP_WINDOW;
@@ -471,13 +472,13 @@ nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi, 
   NB_TRY(get_arena(st, force_bytes(pl, mode, n, false, phi != nullptr, plp), &a));
   Carver cv;
   cv.base = a->buf;
-  double *part = cv.take<double>((size_t)pl.n_jc * 3 * n);
+  double *part = cv.take<double>(part_doubles(pl, n, 3));
   float *split = mode == MODE_SPLIT ? cv.take<float>(6 * (size_t)n) : nullptr;
   double *ppart = phi ? cv.take<double>((size_t)plp.n_jc * n) : nullptr;
   const Phys p = to_phys(params);
   const StateView v = to_view(sys);
   const double t = params->t0 + (double)sys->step * params->dt;
-  NB_TRY(pair_forces(pl, mode, n, sys->x, sys->y, sys->z, sys->q, params->soft2, part, split, st));
+  NB_TRY(pair_forces(pl, mode, n, sys->x, sys->y, sys->z, sys->q, params->soft2, part, split, a->err, st));
   NB_CUDA_TRY(launch_epi_forces(p, v, part, pl.n_jc, flags, t, a->err, st));
   count_launches(1);
   if (phi) {
@@ -521,7 +522,7 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void 
   NB_TRY(get_arena(st, force_bytes(pl, mode, n, true, false, pl), &a));
   Carver cv;
   cv.base = a->buf;
-  double *part = cv.take<double>((size_t)pl.n_jc * 3 * n);
+  double *part = cv.take<double>(part_doubles(pl, n, 3));
   float *split = mode == MODE_SPLIT ? cv.take<float>(6 * (size_t)n) : nullptr;
   double *other = cv.take<double>(3 * (size_t)n);
   double *ubuf[3] = {sys->x, sys->y, sys->z};
@@ -543,7 +544,7 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void 
   count_launches(1);
   for (int64_t s = 0; s < pre; ++s) {
     double **P = buf(s), **Nx = buf(s + 1);
-    NB_TRY(pair_forces(pl, mode, n, P[0], P[1], P[2], sys->q, params->soft2, part, split, st));
+    NB_TRY(pair_forces(pl, mode, n, P[0], P[1], P[2], sys->q, params->soft2, part, split, a->err, st));
     const int64_t snew = sys->step + s + 1;
     int64_t *cout = (windows && s + 1 == pre) ? ctr : nullptr;  // the windows' starting index
     NB_CUDA_TRY(launch_epi_step(p, v, P[0], P[1], P[2], part, pl.n_jc, snew, Nx[0], Nx[1], Nx[2], a->err, st,
@@ -559,7 +560,7 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void 
     count_launches(wg->kernels * (uint64_t)reps);
   }
   double **P = buf(nsteps - 1);
-  NB_TRY(pair_forces(pl, mode, n, P[0], P[1], P[2], sys->q, params->soft2, part, split, st));
+  NB_TRY(pair_forces(pl, mode, n, P[0], P[1], P[2], sys->q, params->soft2, part, split, a->err, st));
   NB_CUDA_TRY(launch_epi_step(p, v, P[0], P[1], P[2], part, pl.n_jc, sys->step + nsteps, nullptr, nullptr, nullptr,
                               a->err, st));
   count_launches(1);
@@ -601,6 +602,122 @@ nb_status nb_energy(const nb_params *params, const nb_system *sys, double out[4]
   return NB_OK;
 }
 
+}  // extern "C"
+
+namespace nb {
+namespace {
+
+// The view of ions [i0, i1) of a system: pointers offset by i0, n = i1 - i0,
+// ion0 = i0 (the global index that keys the Langevin draws).
+StateView range_view(const nb_system *sys, int64_t i0, int64_t i1) {
+  StateView v = to_view(sys);
+  auto off = [&](double *a) { return a ? a + i0 : a; };
+  v.n = i1 - i0;
+  v.x = off(v.x); v.y = off(v.y); v.z = off(v.z);
+  v.vx = off(v.vx); v.vy = off(v.vy); v.vz = off(v.vz);
+  v.ax = off(v.ax); v.ay = off(v.ay); v.az = off(v.az);
+  v.q = v.q ? v.q + i0 : nullptr;
+  v.m = v.m ? v.m + i0 : nullptr;
+  v.ion0 = i0;
+  return v;
+}
+
+nb_status check_range(const nb_system *sys, int64_t i0, int64_t i1) {
+  if (i0 < 0 || i1 < i0 || i1 > sys->n) return fail(NB_EINVAL, "range [%lld, %lld) not within [0, %lld)",
+                                                    (long long)i0, (long long)i1, (long long)sys->n);
+  return NB_OK;
+}
+
+// Coulomb sums of ions [i0, i1) from all n ions into `part` (the one-sided
+// kernel with the full plan's chunks), the FP32 position split first for
+// NB_MIXED_SPLIT.  Returns the plan used.
+nb_status range_pair_sums(const nb_params *params, const nb_system *sys, int64_t i0, int64_t i1,
+                          cudaStream_t st, Arena **arena, double **part_out, Plan *plan_out) {
+  const int64_t n = sys->n, ni = i1 - i0;
+  const int mode = params->precision;
+  const Plan pl = make_plan(n, mode, 0, false, ni);
+  Carver need;
+  need.take<double>((size_t)pl.n_jc * 3 * ni);
+  if (mode == MODE_SPLIT) need.take<float>(6 * (size_t)n);
+  NB_TRY(get_arena(st, need.off + 256, arena));
+  Carver cv;
+  cv.base = (*arena)->buf;
+  double *part = cv.take<double>((size_t)pl.n_jc * 3 * ni);
+  PosF32 pf{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (mode == MODE_SPLIT) {
+    float *split = cv.take<float>(6 * (size_t)n);
+    NB_CUDA_TRY(launch_split_positions(n, sys->x, sys->y, sys->z, split, st));
+    count_launches(1);
+    pf = PosF32{split, split + n, split + 2 * n, split + 3 * n, split + 4 * n, split + 5 * n};
+  }
+  timing_begin(st);
+  NB_CUDA_TRY(launch_pair_force_range(pl, mode, n, i0, ni, sys->x, sys->y, sys->z, sys->q, pf, params->soft2,
+                                      part, st));
+  timing_end(st);
+  count_launches(1);
+  *part_out = part;
+  *plan_out = pl;
+  return NB_OK;
+}
+
+}  // namespace
+}  // namespace nb
+
+extern "C" {
+
+nb_status nb_forces_range(const nb_params *params, const nb_system *sys, int64_t i0, int64_t i1, int flags,
+                          void *stream) {
+  NvtxRange range_("nb_forces_range");
+  NB_TRY(check_params(params));
+  NB_TRY(check_system(sys, (flags & NB_ACC_TOTAL) != 0, true));
+  if (flags & ~NB_ACC_TOTAL) return fail(NB_EINVAL, "unknown flags 0x%x", flags);
+  NB_TRY(check_range(sys, i0, i1));
+  if (i1 == i0) return NB_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena *a = nullptr;
+  double *part = nullptr;
+  Plan pl;
+  NB_TRY(range_pair_sums(params, sys, i0, i1, st, &a, &part, &pl));
+  const double t = params->t0 + (double)sys->step * params->dt;
+  NB_CUDA_TRY(launch_epi_forces(to_phys(params), range_view(sys, i0, i1), part, pl.n_jc, flags, t, a->err, st));
+  count_launches(1);
+  return NB_OK;
+}
+
+nb_status nb_step_range_drift(const nb_params *params, nb_system *sys, int64_t i0, int64_t i1, void *stream) {
+  NvtxRange range_("nb_step_range_drift");
+  NB_TRY(check_params(params));
+  NB_TRY(check_system(sys, true, true));
+  NB_TRY(check_range(sys, i0, i1));
+  if (!(params->dt > 0.0)) return fail(NB_EINVAL, "dt must be > 0");
+  if (i1 == i0) return NB_OK;
+  const StateView v = range_view(sys, i0, i1);
+  NB_CUDA_TRY(launch_drift(to_phys(params), v, v.x, v.y, v.z, (cudaStream_t)stream));
+  count_launches(1);
+  return NB_OK;
+}
+
+nb_status nb_step_range_kick(const nb_params *params, nb_system *sys, int64_t i0, int64_t i1, void *stream) {
+  NvtxRange range_("nb_step_range_kick");
+  NB_TRY(check_params(params));
+  NB_TRY(check_system(sys, true, true));
+  NB_TRY(check_range(sys, i0, i1));
+  if (!(params->dt > 0.0)) return fail(NB_EINVAL, "dt must be > 0");
+  if (i1 > i0) {
+    cudaStream_t st = (cudaStream_t)stream;
+    Arena *a = nullptr;
+    double *part = nullptr;
+    Plan pl;
+    NB_TRY(range_pair_sums(params, sys, i0, i1, st, &a, &part, &pl));
+    const StateView v = range_view(sys, i0, i1);
+    NB_CUDA_TRY(launch_epi_step(to_phys(params), v, v.x, v.y, v.z, part, pl.n_jc, sys->step + 1, nullptr, nullptr,
+                                nullptr, a->err, st));
+    count_launches(1);
+  }
+  sys->step += 1;
+  return NB_OK;
+}
+
 nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys, const double *lx,
                         const double *ly, const double *lz, double *gx, double *gy, double *gz,
                         int flags, void *stream) {
@@ -619,7 +736,7 @@ nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys, const dou
   cudaStream_t st = (cudaStream_t)stream;
   const Plan pl = make_plan(n, MODE_FP64, 2);
   Arena *a = nullptr;
-  NB_TRY(get_arena(st, (size_t)pl.n_jc * 3 * n * sizeof(double) + 512, &a));
+  NB_TRY(get_arena(st, part_doubles(pl, n, 3) * sizeof(double) + 512, &a));
   double *part = reinterpret_cast<double *>(a->buf);
   const Phys p = to_phys(params);
   const StateView v = to_view(sys);
@@ -629,7 +746,7 @@ nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys, const dou
     NB_CUDA_TRY(launch_vjp_scales(n, sys->x, sys->y, sys->z, lx, ly, lz, vjp_scales(a), st));
     count_launches(1);
   }
-  NB_CUDA_TRY(launch_pair_vjp(pl, n, sys->x, sys->y, sys->z, sys->q, lx, ly, lz, params->soft2, part, st, df,
+  NB_CUDA_TRY(launch_pair_vjp(pl, n, sys->x, sys->y, sys->z, sys->q, lx, ly, lz, params->soft2, part, a->err, st, df,
                               vjp_scales(a)));
   NB_CUDA_TRY(launch_epi_vjp(p, v, part, pl.n_jc, lx, ly, lz, gx, gy, gz, flags, t, st));
   count_launches(2);
@@ -700,11 +817,24 @@ nb_status nb_plan_info(int32_t kind, int32_t precision, int64_t n, int64_t out[8
   out[0] = pl.block;
   out[1] = pl.R;
   out[2] = pl.jchunk;
-  out[3] = pl.n_it;
+  out[3] = pl.sym ? pl.nbk : pl.n_it;
   out[4] = pl.n_jc;
   out[5] = pl.sym;
   out[6] = pl.G;
   out[7] = kind == 0 && use_small_steps(pl, precision, n) ? 1 : 0;
+  return NB_OK;
+}
+
+nb_status nb_sym_schedule(int32_t nbk, int32_t *P, int32_t *Q, int32_t *round) {
+  if (nbk < 1 || nbk > 60000) return fail(NB_EINVAL, "nbk must be in 1..60000");
+  if (!P || !Q || !round) return fail(NB_EINVAL, "output arrays must not be NULL");
+  const int64_t items = (int64_t)nbk * (nbk + 1) / 2;
+  for (int64_t t = 0; t < items; ++t) {
+    const SymItem it = sym_item((int)t, nbk);
+    P[t] = it.P;
+    Q[t] = it.Q;
+    round[t] = it.round;
+  }
   return NB_OK;
 }
 
@@ -847,8 +977,8 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
   Carver need;
   need.take<double>((size_t)slots * 3 * n);
   need.take<double>(18 * (size_t)n);
-  need.take<double>((size_t)pl.n_jc * 3 * n);
-  need.take<double>((size_t)plv.n_jc * 3 * n);
+  need.take<double>(part_doubles(pl, n, 3));
+  need.take<double>(part_doubles(plv, n, 3));
   need.take<double>(3 * ADJ_PART_BLOCKS);
   Arena *a = nullptr;
   NB_TRY(get_arena(st, need.off + 256, &a));
@@ -856,8 +986,8 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
   cv.base = a->buf;
   double *segbuf = cv.take<double>((size_t)slots * 3 * n);
   double *st18 = cv.take<double>(18 * (size_t)n);
-  double *fpart = cv.take<double>((size_t)pl.n_jc * 3 * n);
-  double *vpart = cv.take<double>((size_t)plv.n_jc * 3 * n);
+  double *fpart = cv.take<double>(part_doubles(pl, n, 3));
+  double *vpart = cv.take<double>(part_doubles(plv, n, 3));
   double *bpart = cv.take<double>(3 * ADJ_PART_BLOCKS);
   auto arr3 = [&](double *base) { return std::array<double *, 3>{base, base + n, base + 2 * n}; };
   const auto v3 = arr3(st18), a3 = arr3(st18 + 3 * n), xb = arr3(st18 + 6 * n), vb = arr3(st18 + 9 * n),
@@ -891,7 +1021,7 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
       count_launches(1);
       for (int64_t m = 0; m < len; ++m) {
         const auto P = slot(m + 1), Nx = slot(m + 2);
-        NB_CUDA_TRY(launch_pair_force(pl, mode, n, P[0], P[1], P[2], sys->q, nopf, params->soft2, fpart, st));
+        NB_CUDA_TRY(launch_pair_force(pl, mode, n, P[0], P[1], P[2], sys->q, nopf, params->soft2, fpart, a->err, st));
         NB_CUDA_TRY(launch_epi_step(p, sv, P[0], P[1], P[2], fpart, pl.n_jc, start + m + 1, Nx[0], Nx[1], Nx[2],
                                     a->err, st));
         count_launches(2);
@@ -911,7 +1041,7 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
         NB_CUDA_TRY(launch_vjp_scales(n, X[0], X[1], X[2], ab[0], ab[1], ab[2], vjp_scales(a), st));
         count_launches(1);
       }
-      NB_CUDA_TRY(launch_pair_vjp(plv, n, X[0], X[1], X[2], sys->q, ab[0], ab[1], ab[2], params->soft2, vpart, st,
+      NB_CUDA_TRY(launch_pair_vjp(plv, n, X[0], X[1], X[2], sys->q, ab[0], ab[1], ab[2], params->soft2, vpart, a->err, st,
                                   df, vjp_scales(a)));
       const double *xc[3] = {X[0], X[1], X[2]};
       NB_CUDA_TRY(launch_adj_epi(p, n, sys->q, xc, vpart, plv.n_jc, xb.data(), vb.data(), ab.data(),
@@ -925,7 +1055,7 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
     NB_CUDA_TRY(launch_vjp_scales(n, X0[0], X0[1], X0[2], ab[0], ab[1], ab[2], vjp_scales(a), st));
     count_launches(1);
   }
-  NB_CUDA_TRY(launch_pair_vjp(plv, n, X0[0], X0[1], X0[2], sys->q, ab[0], ab[1], ab[2], params->soft2, vpart, st,
+  NB_CUDA_TRY(launch_pair_vjp(plv, n, X0[0], X0[1], X0[2], sys->q, ab[0], ab[1], ab[2], params->soft2, vpart, a->err, st,
                               df, vjp_scales(a)));
   const double *x0c[3] = {X0[0], X0[1], X0[2]};
   NB_CUDA_TRY(launch_adj_epi(p, n, sys->q, x0c, vpart, plv.n_jc, xb.data(), vb.data(), ab.data(), wacc.data(),

@@ -582,13 +582,28 @@ struct Plan {
   int64_t jchunk = 0;
   int n_it = 0;
   int n_jc = 0;
-  // symmetric (half-pair) force kernel: blocks of 32 G ions; n_jc = number
-  // of blocks (one partial per partner block)
+  // symmetric (half-pair) kernels: nbk blocks of 32 G ions; they add into
+  // one output slot in a fixed round order (nb_symsched.cuh), so n_jc = 1
   int sym = 0;
   int G = 0;
+  int nbk = 0;
+  int pad_ = 0;
 };
 
-Plan make_plan(int64_t n, int mode, int kind);  // kind: 0 force, 1 phi, 2 vjp
+// kind: 0 force, 1 phi, 2 vjp.  allow_sym = false gives the one-sided plan;
+// ni >= 0 (one-sided only) sizes the i-tiles for ni target ions of an
+// i-range, keeping the chunks of the full plan.
+Plan make_plan(int64_t n, int mode, int kind, bool allow_sym = true, int64_t ni = -1);
+
+// The pair kernel's output buffer: the partial sums [n_jc][ncomp][n]
+// doubles, followed for the symmetric kernels by their schedule counters
+// (nbk + 1 ints, rounded up to whole doubles).
+inline size_t part_doubles(const Plan &pl, int64_t n, int ncomp) {
+  return (size_t)pl.n_jc * ncomp * (size_t)n + (pl.sym ? (size_t)(pl.nbk + 2) / 2 : 0);
+}
+inline int *part_sync(const Plan &pl, double *part, int64_t n, int ncomp) {
+  return pl.sym ? reinterpret_cast<int *>(part + (size_t)pl.n_jc * ncomp * (size_t)n) : nullptr;
+}
 int device_sm_count();
 
 // Host-side argument checks shared by every entry point (nb_api.cu): they
@@ -614,10 +629,17 @@ void timing_end(cudaStream_t st);
 struct PosF32 {  // split FP32 positions for MODE_SPLIT: hi and lo parts
   const float *xh, *yh, *zh, *xl, *yl, *zl;
 };
+// part: part_doubles(pl, n, 3) doubles; err: the stream's device error word
+// (the symmetric kernels set ERR_TIMEOUT there if a bounded wait gives up).
 cudaError_t launch_pair_force(const Plan &pl, int mode, int64_t n, const double *x,
                               const double *y, const double *z, const double *q,
-                              const PosF32 &pf, double soft2, double *part,
+                              const PosF32 &pf, double soft2, double *part, unsigned *err,
                               cudaStream_t st);
+// The one-sided force kernel for target ions [i0, i0 + ni) against all n:
+// part[(jc * 3 + c) * ni + i - i0]; pl from make_plan(n, mode, 0, false, ni).
+cudaError_t launch_pair_force_range(const Plan &pl, int mode, int64_t n, int64_t i0, int64_t ni,
+                                    const double *x, const double *y, const double *z, const double *q,
+                                    const PosF32 &pf, double soft2, double *part, cudaStream_t st);
 cudaError_t launch_pair_phi(const Plan &pl, int64_t n, const double *x, const double *y,
                             const double *z, const double *q, double charge, double soft2,
                             double *part, cudaStream_t st);
@@ -626,7 +648,8 @@ cudaError_t launch_pair_phi(const Plan &pl, int64_t n, const double *x, const do
 cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const double *y,
                             const double *z, const double *q, const double *lx,
                             const double *ly, const double *lz, double soft2, double *part,
-                            cudaStream_t st, bool df = false, const int *scales = nullptr);
+                            unsigned *err, cudaStream_t st, bool df = false,
+                            const int *scales = nullptr);
 // The largest biased exponents of the position and cotangent components
 // (scales[0], scales[1]); zeroes them first, on `st`.
 cudaError_t launch_vjp_scales(int64_t n, const double *x, const double *y, const double *z,
@@ -636,11 +659,11 @@ cudaError_t launch_split_positions(int64_t n, const double *x, const double *y,
                                    const double *z, float *out6, cudaStream_t st);
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
                             const double *z, const double *q, const PosF32 &pf, double soft2,
-                            double *part, cudaStream_t st);
+                            double *part, int *sync, unsigned *err, cudaStream_t st);
 cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const double *y,
                            const double *z, const double *q, const double *lx, const double *ly,
-                           const double *lz, double soft2, double *part, cudaStream_t st, bool df,
-                           const int *scales);
+                           const double *lz, double soft2, double *part, int *sync, unsigned *err,
+                           cudaStream_t st, bool df, const int *scales);
 
 // Epilogue kernels (nb_integrate.cu).
 struct StateView {
@@ -648,6 +671,7 @@ struct StateView {
   double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az;
   const double *q;
   const double *m = nullptr;  // per-ion mass (two species) or nullptr
+  int64_t ion0 = 0;           // global index of ion 0 of the view (an i-range's start)
 };
 
 // Mass of ion i, and the scale of its trap acceleration relative to the

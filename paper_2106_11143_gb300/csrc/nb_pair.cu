@@ -28,9 +28,11 @@
 namespace nb {
 
 // ---------------------------------------------------------------------------
-// Force kernel: part[(jc*3 + c)*n + i] = sum_{j in chunk jc} w_j d_ij^c / s_ij^3.
+// Force kernel: part[(jc*3 + c)*ni + i - i0] = sum_{j in chunk jc} w_j d_ij^c / s_ij^3
+// for the target ions i in [i0, i0 + ni) (all n ions: i0 = 0, ni = n) and the
+// source ions j of chunk jc of [0, n).
 template <int MODE, int R, bool QARR>
-__global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
+__global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk, int64_t i0, int64_t ni,
                                                     const double *__restrict__ x,
                                                     const double *__restrict__ y,
                                                     const double *__restrict__ z,
@@ -39,7 +41,8 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int B = blockDim.x;
   const int tid = threadIdx.x;
-  const int64_t ibase = (int64_t)blockIdx.x * B * R + tid;
+  const int64_t ibase = i0 + (int64_t)blockIdx.x * B * R + tid;
+  const int64_t iend = i0 + ni;
   const int64_t jb = (int64_t)blockIdx.y * jchunk;
   const int64_t je = min(jb + jchunk, n);
 
@@ -49,7 +52,7 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
   float af[R][3];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const int64_t i = min(ibase + (int64_t)r * B, n - 1);
+    const int64_t i = min(ibase + (int64_t)r * B, iend - 1);
     if (MODE == MODE_SPLIT) {
       xh[r] = pf.xh[i]; yh[r] = pf.yh[i]; zh[r] = pf.zh[i];
       xl[r] = pf.xl[i]; yl[r] = pf.yl[i]; zl[r] = pf.zl[i];
@@ -166,10 +169,10 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk,
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t i = ibase + (int64_t)r * B;
-    if (i < n) {
+    if (i < iend) {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        part[((int64_t)blockIdx.y * 3 + c) * n + i] =
+        part[((int64_t)blockIdx.y * 3 + c) * ni + (i - i0)] =
             (fp64_like(MODE) || MODE == MODE_DF64) ? ad[r][c] : ad[r][c] + cd[r][c];
     }
   }
@@ -353,45 +356,54 @@ __global__ void k_split_positions(int64_t n, const double *__restrict__ x,
 static int round_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 template <int MODE, int R>
-static cudaError_t launch_force_mr(const Plan &pl, int64_t n, const double *x, const double *y,
-                                   const double *z, const double *q, const PosF32 &pf,
+static cudaError_t launch_force_mr(const Plan &pl, int64_t n, int64_t i0, int64_t ni, const double *x,
+                                   const double *y, const double *z, const double *q, const PosF32 &pf,
                                    double soft2, double *part, cudaStream_t st) {
   const dim3 grid(pl.n_it, pl.n_jc);
   const size_t smem = (MODE == MODE_SPLIT ? 2 * sizeof(float4) : sizeof(D4)) * pl.block;
   if (q)
-    k_pair_force<MODE, R, true><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, pf, soft2, part);
+    k_pair_force<MODE, R, true><<<grid, pl.block, smem, st>>>(n, pl.jchunk, i0, ni, x, y, z, q, pf, soft2, part);
   else
-    k_pair_force<MODE, R, false><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, pf, soft2, part);
+    k_pair_force<MODE, R, false><<<grid, pl.block, smem, st>>>(n, pl.jchunk, i0, ni, x, y, z, q, pf, soft2, part);
   return cudaGetLastError();
 }
 
 template <int MODE>
-static cudaError_t launch_force_m(const Plan &pl, int64_t n, const double *x, const double *y,
-                                  const double *z, const double *q, const PosF32 &pf,
+static cudaError_t launch_force_m(const Plan &pl, int64_t n, int64_t i0, int64_t ni, const double *x,
+                                  const double *y, const double *z, const double *q, const PosF32 &pf,
                                   double soft2, double *part, cudaStream_t st) {
   switch (pl.R) {
-    case 1: return launch_force_mr<MODE, 1>(pl, n, x, y, z, q, pf, soft2, part, st);
-    case 2: return launch_force_mr<MODE, 2>(pl, n, x, y, z, q, pf, soft2, part, st);
-    case 4: return launch_force_mr<MODE, 4>(pl, n, x, y, z, q, pf, soft2, part, st);
+    case 1: return launch_force_mr<MODE, 1>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    case 2: return launch_force_mr<MODE, 2>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    case 4: return launch_force_mr<MODE, 4>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_pair_force_range(const Plan &pl, int mode, int64_t n, int64_t i0, int64_t ni,
+                                    const double *x, const double *y, const double *z, const double *q,
+                                    const PosF32 &pf, double soft2, double *part, cudaStream_t st) {
+  if (pl.sym || i0 < 0 || ni < 1 || i0 + ni > n) return cudaErrorInvalidValue;
+  switch (mode) {
+    case MODE_FP64: return launch_force_m<MODE_FP64>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    case MODE_MIXED: return launch_force_m<MODE_MIXED>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    case MODE_SPLIT: return launch_force_m<MODE_SPLIT>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    case MODE_DF64: return launch_force_m<MODE_DF64>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    case MODE_SQRTDIV: return launch_force_m<MODE_SQRTDIV>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    case MODE_RSQ: return launch_force_m<MODE_RSQ>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    case MODE_RSQ_NR1: return launch_force_m<MODE_RSQ_NR1>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    case MODE_RSQ_NR2: return launch_force_m<MODE_RSQ_NR2>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_pair_force(const Plan &pl, int mode, int64_t n, const double *x,
                               const double *y, const double *z, const double *q,
-                              const PosF32 &pf, double soft2, double *part, cudaStream_t st) {
-  if (pl.sym) return launch_pair_sym(mode, n, pl.n_jc, pl.G, x, y, z, q, pf, soft2, part, st);
-  switch (mode) {
-    case MODE_FP64: return launch_force_m<MODE_FP64>(pl, n, x, y, z, q, pf, soft2, part, st);
-    case MODE_MIXED: return launch_force_m<MODE_MIXED>(pl, n, x, y, z, q, pf, soft2, part, st);
-    case MODE_SPLIT: return launch_force_m<MODE_SPLIT>(pl, n, x, y, z, q, pf, soft2, part, st);
-    case MODE_DF64: return launch_force_m<MODE_DF64>(pl, n, x, y, z, q, pf, soft2, part, st);
-    case MODE_SQRTDIV: return launch_force_m<MODE_SQRTDIV>(pl, n, x, y, z, q, pf, soft2, part, st);
-    case MODE_RSQ: return launch_force_m<MODE_RSQ>(pl, n, x, y, z, q, pf, soft2, part, st);
-    case MODE_RSQ_NR1: return launch_force_m<MODE_RSQ_NR1>(pl, n, x, y, z, q, pf, soft2, part, st);
-    case MODE_RSQ_NR2: return launch_force_m<MODE_RSQ_NR2>(pl, n, x, y, z, q, pf, soft2, part, st);
-    default: return cudaErrorInvalidValue;
-  }
+                              const PosF32 &pf, double soft2, double *part, unsigned *err,
+                              cudaStream_t st) {
+  if (pl.sym)
+    return launch_pair_sym(mode, n, pl.nbk, pl.G, x, y, z, q, pf, soft2, part, part_sync(pl, part, n, 3), err, st);
+  return launch_pair_force_range(pl, mode, n, 0, n, x, y, z, q, pf, soft2, part, st);
 }
 
 cudaError_t launch_pair_phi(const Plan &pl, int64_t n, const double *x, const double *y,
@@ -410,9 +422,11 @@ cudaError_t launch_pair_phi(const Plan &pl, int64_t n, const double *x, const do
 cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const double *y,
                             const double *z, const double *q, const double *lx,
                             const double *ly, const double *lz, double soft2, double *part,
-                            cudaStream_t st, bool df, const int *scales) {
+                            unsigned *err, cudaStream_t st, bool df, const int *scales) {
   if (df && !scales) return cudaErrorInvalidValue;
-  if (pl.sym) return launch_vjp_sym(n, pl.n_jc, pl.G, x, y, z, q, lx, ly, lz, soft2, part, st, df, scales);
+  if (pl.sym)
+    return launch_vjp_sym(n, pl.nbk, pl.G, x, y, z, q, lx, ly, lz, soft2, part, part_sync(pl, part, n, 3), err,
+                          st, df, scales);
   const dim3 grid(pl.n_it, pl.n_jc);
   const size_t smem = 2 * sizeof(D4) * pl.block;
   if (df) {
@@ -502,36 +516,22 @@ bool tuning_lookup(int kind, int mode, int64_t n, int *block, int *R, int *bps) 
   return false;
 }
 
-// Largest scratch the symmetric kernel's per-partner-block partials may take:
-// a quarter of the current device's memory (queried once per device), 2 GB if
-// the query fails.
-static double sym_partial_cap() {
-  static std::mutex mu;
-  static double cap[64] = {0.0};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-    cudaGetLastError();
-    return 2e9;
-  }
-  std::lock_guard<std::mutex> lk(mu);
-  if (cap[dev] == 0.0) {
-    cudaDeviceProp prop;
-    cap[dev] = (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) ? 0.25 * (double)prop.totalGlobalMem : 2e9;
-  }
-  return cap[dev];
-}
+// The symmetric kernels number their work items with an int: at most
+// SYM_MAX_BLOCKS blocks (nbk (nbk + 1) / 2 items).
+constexpr int64_t SYM_MAX_BLOCKS = 60000;
 
-Plan make_plan(int64_t n, int mode, int kind) {
+Plan make_plan(int64_t n, int mode, int kind, bool allow_sym, int64_t ni) {
   Plan pl;
-  // Symmetric half-pair kernel for the force paths, while the
-  // per-partner-block partials (nbk * 3n doubles) fit the cap above.  Where
+  if (ni < 0) ni = n;
+  // Symmetric half-pair kernel for the force paths.  Where
   // it starts and its block sizes are the fastest measured in step sweeps on
   // GB300, counting the epilogue's reads of the partials: from n = 500
   // (split), 1000 (mixed), 1500 (fp64) or 2000 (df64); 32-ion blocks (one
   // warp) first, then 64 from n = 2000-2500, 128 from n = 2500-4096, 256
   // from n = 32768 and 512 from n = 60000; split: 256 from n = 4096 and
   // 512-ion blocks with two P-ions per lane from n = 8000.
-  if (kind == 0 && (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || mode == MODE_SPLIT)) {
+  if (allow_sym && kind == 0 &&
+      (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || mode == MODE_SPLIT)) {
     int G;
     bool use;
     if (mode == MODE_SPLIT) {
@@ -550,18 +550,19 @@ Plan make_plan(int64_t n, int mode, int kind) {
       G = tb / 32;
     }
     const int64_t nbk = (n + 32 * G - 1) / (32 * G);
-    if (use && (double)nbk * 3.0 * (double)n * 8.0 <= sym_partial_cap()) {
+    if (use && nbk <= SYM_MAX_BLOCKS) {
       pl.sym = 1;
       pl.G = G;
-      pl.n_jc = (int)nbk;
+      pl.nbk = (int)nbk;
+      pl.n_jc = 1;
       pl.block = 256;
       return pl;
     }
   }
   // Symmetric VJP kernel from n = 2500, where it beat the one-sided kernel
-  // on GB300 (128-ion blocks below n = 16384, 256 above), under the same
-  // cap; tuning kind 5 overrides (R = 0 disables).
-  if (kind == 2) {
+  // on GB300 (128-ion blocks below n = 16384, 256 above); tuning kind 5
+  // overrides (R = 0 disables).
+  if (allow_sym && kind == 2) {
     int G = n >= 16384 ? 8 : 4;
     bool use = n >= 2500;
     int tb = 0, tr = 0, tbps = 0;
@@ -570,10 +571,11 @@ Plan make_plan(int64_t n, int mode, int kind) {
       G = tb / 32;
     }
     const int64_t nbk = (n + 32 * G - 1) / (32 * G);
-    if (use && (double)nbk * 3.0 * (double)n * 8.0 <= sym_partial_cap()) {
+    if (use && nbk <= SYM_MAX_BLOCKS) {
       pl.sym = 1;
       pl.G = G;
-      pl.n_jc = (int)nbk;
+      pl.nbk = (int)nbk;
+      pl.n_jc = 1;
       pl.block = 128;
       return pl;
     }
@@ -617,6 +619,9 @@ Plan make_plan(int64_t n, int mode, int kind) {
   if (chunk >= pl.block) chunk = ((chunk + pl.block - 1) / pl.block) * pl.block;
   pl.jchunk = std::max<int64_t>(chunk, min_chunk);
   pl.n_jc = round_up(n, pl.jchunk);
+  // an i-range of ni targets keeps the full plan's chunks and tiles, so each
+  // of its ions gets the sums the full launch would give it
+  if (ni != n) pl.n_it = round_up(ni, it);
   return pl;
 }
 

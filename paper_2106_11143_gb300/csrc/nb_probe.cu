@@ -3,6 +3,11 @@
 // and the raw FP32 reciprocal-square-root seed it starts from.  They run the
 // same device functions as the pair kernels, so a caller can measure a mode's
 // error distribution against an exact reference over any set of inputs.
+#include <algorithm>
+#include <map>
+#include <utility>
+#include <vector>
+
 #include "nb_common.cuh"
 
 namespace nb {
@@ -84,5 +89,139 @@ extern "C" nb_status nb_rsqrt_seed_probe(int64_t n, const float *x, float *y, vo
   k_rsqrt_seed_probe<<<(unsigned)((n + T - 1) / T), T, 0, (cudaStream_t)stream>>>(n, x, y);
   if (cudaGetLastError() != cudaSuccess) return NB_ECUDA;
   count_launches(1);
+  return NB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pipe throughput probe: the rate at which every SM retires one instruction
+// kind (the denominator of the ALU rooflines).  Each thread runs eight
+// independent dependence chains of the instruction, issued from inline PTX
+// so that the compiler keeps every one, for `iters` rounds of 16; thread 0 of
+// each block records its SM and the SM clock before and after, between two
+// block barriers.
+namespace nb {
+
+constexpr int PIPE_THREADS = 512;
+constexpr int PIPE_BLOCKS_PER_SM = 2;
+constexpr int PIPE_CHAINS = 8;
+constexpr int PIPE_UNROLL = 16;
+
+template <int KIND>
+__device__ __forceinline__ void pipe_op(double &a, float &f, double b, double c, float fb, float fc) {
+  if (KIND == 0) asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(a) : "d"(b), "d"(c));
+  if (KIND == 1) asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(a) : "d"(c));
+  if (KIND == 2) asm volatile("mul.rn.f64 %0, %0, %1;" : "+d"(a) : "d"(b));
+  if (KIND == 3) asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(f) : "f"(fb), "f"(fc));
+  if (KIND == 4) asm volatile("add.rn.f32 %0, %0, %1;" : "+f"(f) : "f"(fc));
+  if (KIND == 5) asm volatile("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(f));
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(PIPE_THREADS) k_pipe_probe(int64_t iters, double b, double c,
+                                                             unsigned long long *clk, double *sink) {
+  double a[PIPE_CHAINS];
+  float f[PIPE_CHAINS];
+#pragma unroll
+  for (int k = 0; k < PIPE_CHAINS; ++k) {
+    a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    f[k] = 1.0f + 1e-3f * (float)(threadIdx.x + k);
+  }
+  const float fb = (float)b, fc = (float)c;
+  __syncthreads();
+  unsigned long long t0 = 0;
+  if (threadIdx.x == 0) t0 = clock64();
+  for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < PIPE_UNROLL; ++u)
+#pragma unroll
+      for (int k = 0; k < PIPE_CHAINS; ++k) pipe_op<KIND>(a[k], f[k], b, c, fb, fc);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long t1 = clock64();
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    clk[3 * blockIdx.x] = smid;
+    clk[3 * blockIdx.x + 1] = t0;
+    clk[3 * blockIdx.x + 2] = t1;
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < PIPE_CHAINS; ++k) s += a[k] + (double)f[k];
+  if (s == 12345.678) sink[0] = s;  // keeps the chains observable
+}
+
+template <int KIND>
+static cudaError_t launch_pipe(int blocks, int64_t iters, unsigned long long *clk, double *sink, cudaStream_t st) {
+  // factors that keep every chain finite and normal for any iteration count
+  const double b = (KIND == 2) ? 1.0 : 0.999999, c = (KIND == 1) ? 1e-300 : 1e-7;
+  k_pipe_probe<KIND><<<blocks, PIPE_THREADS, 0, st>>>(iters, b, c, clk, sink);
+  return cudaGetLastError();
+}
+
+}  // namespace nb
+
+extern "C" nb_status nb_pipe_probe(int32_t kind, int64_t iters, double out[3], void *stream) {
+  if (kind < 0 || kind > 5) return fail(NB_EINVAL, "nb_pipe_probe: unknown kind %d", kind);
+  if (iters < 1 || iters > ((int64_t)1 << 24)) return fail(NB_EINVAL, "nb_pipe_probe: iters out of range");
+  if (!out) return fail(NB_EINVAL, "nb_pipe_probe: out is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int sms = device_sm_count();
+  const int blocks = sms * PIPE_BLOCKS_PER_SM;
+  unsigned long long *clk = nullptr;
+  double *sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<unsigned long long> h(3 * (size_t)blocks);
+  cudaError_t e = cudaMalloc(&clk, sizeof(unsigned long long) * 3 * blocks + sizeof(double));
+  if (e == cudaSuccess) {
+    sink = reinterpret_cast<double *>(clk + 3 * blocks);
+    e = cudaEventCreate(&e0);
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) {
+    switch (kind) {
+      case 0: e = launch_pipe<0>(blocks, iters, clk, sink, st); break;
+      case 1: e = launch_pipe<1>(blocks, iters, clk, sink, st); break;
+      case 2: e = launch_pipe<2>(blocks, iters, clk, sink, st); break;
+      case 3: e = launch_pipe<3>(blocks, iters, clk, sink, st); break;
+      case 4: e = launch_pipe<4>(blocks, iters, clk, sink, st); break;
+      default: e = launch_pipe<5>(blocks, iters, clk, sink, st); break;
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), clk, sizeof(unsigned long long) * h.size(),
+                                            cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (clk) cudaFree(clk);
+  if (e != cudaSuccess) return fail(NB_ECUDA, "nb_pipe_probe: %s", cudaGetErrorString(e));
+  count_launches(1);
+  // per SM: the instructions its blocks retired over the span of its blocks
+  std::map<unsigned long long, std::pair<unsigned long long, unsigned long long>> span;
+  std::map<unsigned long long, int> nblk;
+  for (int b = 0; b < blocks; ++b) {
+    const unsigned long long sm = h[3 * b], t0 = h[3 * b + 1], t1 = h[3 * b + 2];
+    auto it = span.find(sm);
+    if (it == span.end()) span[sm] = {t0, t1};
+    else it->second = {std::min(it->second.first, t0), std::max(it->second.second, t1)};
+    ++nblk[sm];
+  }
+  std::vector<double> rate;
+  double cyc_max = 0.0;
+  for (auto &kv : span) {
+    const double cyc = (double)(kv.second.second - kv.second.first);
+    const double lane_ops = (double)nblk[kv.first] * PIPE_THREADS * (double)iters * PIPE_UNROLL * PIPE_CHAINS;
+    if (cyc > 0.0) rate.push_back(lane_ops / cyc);
+    cyc_max = std::max(cyc_max, cyc);
+  }
+  if (rate.empty()) return fail(NB_ECUDA, "nb_pipe_probe: no clock samples");
+  std::sort(rate.begin(), rate.end());
+  out[0] = rate[rate.size() / 2];             // lanes per clock per SM (median SM)
+  out[1] = ms > 0.0f ? cyc_max / (ms * 1e3) : 0.0;  // SM clock in MHz over the launch
+  out[2] = ms;
   return NB_OK;
 }

@@ -4,13 +4,15 @@
 // bound precisions (fp64, df64).
 //
 // The split and literal mixed precisions use it too (FP32 pair arithmetic
-// with per-step FP32 partials added into FP64).
+// with per-step FP32 partials added into FP64, or into double-float sums on
+// the FP32 pipe for split).
 //
 // Ions are grouped in blocks of BI = 32 G ions (G tiles of one warp).  One
-// CTA handles one work item, a block pair (P, Q) with P <= Q:
+// CTA handles one work item, a block pair (P, Q) with P <= Q, drawn from the
+// round-robin schedule of nb_symsched.cuh:
 //  - P < Q: both blocks' positions are staged in shared memory together with
-//    FP64 accumulators for P.  Each warp takes Q-tiles; for a Q-tile it
-//    visits the G P-tiles in the staggered order pt = (qs + k) mod G, one
+//    accumulators for P and Q.  Each warp takes Q-tiles; for a Q-tile it
+//    visits the P-tiles in the staggered order pt = (qs + k) mod G, one
 //    per __syncthreads-separated step k, so at any step the warps hold
 //    distinct P-tiles.  Within a step lane l holds P-ion l; the Q-tile's
 //    positions and its force accumulators rotate one lane per iteration
@@ -18,13 +20,12 @@
 //    the two tiles has been evaluated once and the Q data is back home.
 //  - P == Q: the block's internal pairs, one-sided (each ion against all
 //    others of the block).
-// Output: ion i of block B gets one partial sum per partner block X, in
-// part[(X*3 + c)*n + i]; the epilogue kernels add the nbk partials in block
-// order.  No atomics; the order of every sum is fixed, so the result is
-// bitwise reproducible.
+// Output: the item adds its sums into acc[c * n + i] in round order
+// (nb_symsched.cuh), so the result is bitwise reproducible with no partial
+// buffer and no atomics on the data.
 //
 // With per-ion charges the two sides carry different weights: ion i gets
-// q_j d/r^3 and ion j gets -q_i d/r^3 (the partial sums exclude the ion's own
+// q_j d/r^3 and ion j gets -q_i d/r^3 (the sums exclude the ion's own
 // charge, as in the one-sided kernel).  The ragged last block is padded with
 // weight-0 ions far away; only items that touch it apply the weights when
 // the charge is uniform.
@@ -32,6 +33,7 @@
 #include <mutex>
 
 #include "nb_common.cuh"
+#include "nb_symsched.cuh"
 
 namespace nb {
 
@@ -227,20 +229,40 @@ __device__ __forceinline__ void sym_step_split2(const float4 &h1, const float4 &
   }
 }
 
+// Where an item keeps the finished sums of its Q block (and a diagonal item
+// its block's sums): in the Q-tile's own 1 KB of staged positions, which only
+// the warp that owns that Q-tile reads, so it is free once that warp is done
+// with the tile.  Sum c of ion i of the block: [i / 32][c][i mod 32].
+__device__ __forceinline__ double &qsum(SD4 *posQ, int c, int i) {
+  return reinterpret_cast<double *>(posQ)[(i >> 5) * 128 + c * 32 + (i & 31)];
+}
+
+// Double-float accumulation on the FP32 pipe: (h, l) += v (TwoSum), for the
+// split path's per-step FP32 partials, so that its pair loop and tile
+// flushes issue no FP64 instruction.
+__device__ __forceinline__ void df_add(float &h, float &l, float v) {
+  float s, e;
+  two_sum_f(h, v, s, e);
+  h = s;
+  l += e;
+}
+
 // Off-diagonal item, split precision with 64-ion P-tiles (G >= 16, so that
 // the G/2 P-tiles outnumber the warps): warp w takes the Q-tiles qs = w,
 // w + 8, ...; at step k it holds P-tile (qs + k) mod G/2, distinct across
-// warps because all warps advance in lockstep through the barriers.
+// warps because all warps advance in lockstep through the barriers.  The
+// P sums are double-floats in shared memory (accPf: [3][BI] hi, then
+// [3][BI] lo), the Q sums double-floats in registers, stored as FP64 (qsum)
+// once the warp is done with its Q-tile.
 template <bool W, int NW>
-__device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, const SD4 *posQ, double *accP,
-                                                   int G, int BI, double soft2, int64_t n, int P,
-                                                   int64_t q0, int nq, double *part) {
+__device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, SD4 *posQ, float *accPf, int G, int BI,
+                                                   double soft2) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int GP = G >> 1;
   const float4 *fP = reinterpret_cast<const float4 *>(posP);
   const float4 *fQ = reinterpret_cast<const float4 *>(posQ);
   for (int qs = warp; qs < G; qs += NW) {
-    double aq[3] = {0.0, 0.0, 0.0};
+    float qh[3] = {0.0f, 0.0f, 0.0f}, ql[3] = {0.0f, 0.0f, 0.0f};
     const float4 *qhi = fQ + qs * 64 + lane, *qlo = fQ + 2 * BI + qs * 64 + lane;
     for (int k = 0; k < GP; ++k) {
       const int pt = (qs + k) % GP;
@@ -251,26 +273,29 @@ __device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, const SD4 *p
                          b);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        accP[c * BI + i1] += f32_to_f64(a1[c]);
-        accP[c * BI + i2] += f32_to_f64(a2[c]);
-        aq[c] += f32_to_f64(b[c]);
+        df_add(accPf[c * BI + i1], accPf[(3 + c) * BI + i1], a1[c]);
+        df_add(accPf[c * BI + i2], accPf[(3 + c) * BI + i2], a2[c]);
+        df_add(qh[c], ql[c], b[c]);
       }
     }
-    const int iq = qs * 32 + lane;
-    if (iq < nq)
+    __syncwarp();  // every lane is done reading the tile
 #pragma unroll
-      for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + q0 + iq] = aq[c];
+    for (int c = 0; c < 3; ++c) qsum(posQ, c, qs * 32 + lane) = f32_to_f64(qh[c]) + f32_to_f64(ql[c]);
   }
 }
 
+// Off-diagonal item in the other layouts.  The P sums go to accP in shared
+// memory (FP64, or double-float accPf for split), the Q sums (FP64) to qsum
+// once the warp is done with its Q-tile.
 template <int MODE, bool W, int NW>
-__device__ __forceinline__ void sym_offdiag(const SD4 *posP, const SD4 *posQ, double *accP, int G,
-                                            int BI, double soft2, float s2h, float s2l, int64_t n,
-                                            int P, int64_t q0, int nq, double *part) {
+__device__ __forceinline__ void sym_offdiag(const SD4 *posP, SD4 *posQ, double *accP, int G, int BI,
+                                            double soft2, float s2h, float s2l) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *accPf = reinterpret_cast<float *>(accP);
   for (int qs = warp; qs < G; qs += NW) {
     const SD4 qh = posQ[qs * 32 + lane];
     double aq[3] = {0.0, 0.0, 0.0};
+    float qfh[3] = {0.0f, 0.0f, 0.0f}, qfl[3] = {0.0f, 0.0f, 0.0f};
     for (int k = 0; k < G; ++k) {
       const int pt = (qs + k) % G;
       __syncthreads();  // all warps are at step k: their P-tiles are distinct
@@ -280,16 +305,21 @@ __device__ __forceinline__ void sym_offdiag(const SD4 *posP, const SD4 *posQ, do
         float a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
         if (MODE == MODE_MIXED) {
           sym_step_mixed<W>(pp, qh, (float)soft2, lane, a, b);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            accP[c * BI + ip] += f32_to_f64(a[c]);
+            aq[c] += f32_to_f64(b[c]);
+          }
         } else {
           const float4 *fP = reinterpret_cast<const float4 *>(posP);
           const float4 *fQ = reinterpret_cast<const float4 *>(posQ);
           sym_step_split<W>(fP[ip], fP[BI + ip], fQ + qs * 64 + lane, fQ + 2 * BI + qs * 64 + lane,
                             (float)soft2, lane, a, b);
-        }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          accP[c * BI + ip] += f32_to_f64(a[c]);
-          aq[c] += f32_to_f64(b[c]);
+          for (int c = 0; c < 3; ++c) {
+            df_add(accPf[c * BI + ip], accPf[(3 + c) * BI + ip], a[c]);
+            df_add(qfh[c], qfl[c], b[c]);
+          }
         }
       } else if (MODE == MODE_DF64) {
         float ah[3] = {0, 0, 0}, al[3] = {0, 0, 0}, bh[3] = {0, 0, 0}, bl[3] = {0, 0, 0};
@@ -309,10 +339,10 @@ __device__ __forceinline__ void sym_offdiag(const SD4 *posP, const SD4 *posQ, do
         }
       }
     }
-    const int iq = qs * 32 + lane;
-    if (iq < nq)
+    __syncwarp();  // every lane is done reading the tile
 #pragma unroll
-      for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + q0 + iq] = aq[c];
+    for (int c = 0; c < 3; ++c)
+      qsum(posQ, c, qs * 32 + lane) = (MODE == MODE_SPLIT) ? f32_to_f64(qfh[c]) + f32_to_f64(qfl[c]) : aq[c];
   }
 }
 
@@ -361,18 +391,15 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_s
                                                          const double *__restrict__ y,
                                                          const double *__restrict__ z,
                                                          const double *__restrict__ q, PosF32 pf,
-                                                         double soft2, double *__restrict__ part) {
+                                                         double soft2, double *__restrict__ acc,
+                                                         int *__restrict__ sync, unsigned *err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int BI = 32 * G;
   SD4 *posP = reinterpret_cast<SD4 *>(smem_raw);
   SD4 *posQ = posP + BI;
   double *accP = reinterpret_cast<double *>(posQ + (MODE == MODE_SPLIT ? 2 * BI : BI));  // [3][BI]
-  int t = blockIdx.x, P = 0;
-  while (t >= nbk - P) {  // item -> (P, Q), P <= Q, row by row
-    t -= nbk - P;
-    ++P;
-  }
-  const int Q = P + t;
+  const SymItem it = sym_item(sym_draw(sync), nbk);
+  const int P = it.P, Q = it.Q;
   const int64_t p0 = (int64_t)P * BI, q0 = (int64_t)Q * BI;
   const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
   const int tid = threadIdx.x;
@@ -387,7 +414,7 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_s
   if (MODE == MODE_DF64) split_f64(soft2, s2h, s2l);
   __syncthreads();
 
-  if (P == Q) {  // the block's own pairs, one-sided
+  if (P == Q) {  // the block's own pairs, one-sided; sums into qsum (posQ is not staged)
     for (int i = tid; i < np; i += NT) {
       const SD4 pi = posP[i];
       double a[3] = {0.0, 0.0, 0.0};
@@ -472,26 +499,34 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_s
         }
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + p0 + i] = a[c];
+      for (int c = 0; c < 3; ++c) qsum(posQ, c, i) = a[c];
     }
+    __syncthreads();
+    sym_commit<NT>(it, n, p0, np, q0, nq, acc, sync, err, [&](int c, int i) { return qsum(posQ, c, i); },
+                   [&](int c, int i) { return 0.0; });
     return;
   }
 
   const bool weighted = QARR || np < BI || nq < BI;
+  float *accPf = reinterpret_cast<float *>(accP);
   if (P2) {
     if (weighted)
-      sym_offdiag_split2<true, NT / 32>(posP, posQ, accP, G, BI, soft2, n, P, q0, nq, part);
+      sym_offdiag_split2<true, NT / 32>(posP, posQ, accPf, G, BI, soft2);
     else
-      sym_offdiag_split2<false, NT / 32>(posP, posQ, accP, G, BI, soft2, n, P, q0, nq, part);
+      sym_offdiag_split2<false, NT / 32>(posP, posQ, accPf, G, BI, soft2);
   } else if (weighted) {
-    sym_offdiag<MODE, true, NT / 32>(posP, posQ, accP, G, BI, soft2, s2h, s2l, n, P, q0, nq, part);
+    sym_offdiag<MODE, true, NT / 32>(posP, posQ, accP, G, BI, soft2, s2h, s2l);
   } else {
-    sym_offdiag<MODE, false, NT / 32>(posP, posQ, accP, G, BI, soft2, s2h, s2l, n, P, q0, nq, part);
+    sym_offdiag<MODE, false, NT / 32>(posP, posQ, accP, G, BI, soft2, s2h, s2l);
   }
   __syncthreads();
-  for (int i = tid; i < np; i += NT)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) part[((int64_t)Q * 3 + c) * n + p0 + i] = accP[c * BI + i];
+  if (MODE == MODE_SPLIT)
+    sym_commit<NT>(it, n, p0, np, q0, nq, acc, sync, err,
+                   [&](int c, int i) { return f32_to_f64(accPf[c * BI + i]) + f32_to_f64(accPf[(3 + c) * BI + i]); },
+                   [&](int c, int i) { return qsum(posQ, c, i); });
+  else
+    sym_commit<NT>(it, n, p0, np, q0, nq, acc, sync, err, [&](int c, int i) { return accP[c * BI + i]; },
+                   [&](int c, int i) { return qsum(posQ, c, i); });
 }
 
 size_t sym_smem_bytes(int G, int mode) {
@@ -501,7 +536,7 @@ size_t sym_smem_bytes(int G, int mode) {
 template <int MODE, bool P2, int NT>
 static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, const double *y,
                                 const double *z, const double *q, const PosF32 &pf, double soft2,
-                                double *part, cudaStream_t st) {
+                                double *part, int *sync, unsigned *err, cudaStream_t st) {
   static std::mutex mu;
   static bool done[64] = {false};
   int dev = 0;
@@ -520,54 +555,56 @@ static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, cons
       done[dev] = true;
     }
   }
+  e = cudaMemsetAsync(sync, 0, sizeof(int) * sym_sync_ints(nbk), st);
+  if (e != cudaSuccess) return e;
   const int items = nbk * (nbk + 1) / 2;
   const size_t smem = sym_smem_bytes(G, MODE);
   if (q)
-    k_pair_sym<MODE, true, P2, NT><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
+    k_pair_sym<MODE, true, P2, NT><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err);
   else
-    k_pair_sym<MODE, false, P2, NT><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part);
+    k_pair_sym<MODE, false, P2, NT><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
                             const double *z, const double *q, const PosF32 &pf, double soft2,
-                            double *part, cudaStream_t st) {
+                            double *part, int *sync, unsigned *err, cudaStream_t st) {
   if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
   constexpr int S = SYM_THREADS_SMALL, L = SYM_THREADS;
   if (G <= 2) {  // 32- and 64-ion blocks at small n: one warp per 32-ion tile
     switch (mode) {
       case MODE_FP64:
-        return G == 1 ? launch_sym_m<MODE_FP64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
-                      : launch_sym_m<MODE_FP64, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+        return G == 1 ? launch_sym_m<MODE_FP64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
+                      : launch_sym_m<MODE_FP64, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
       case MODE_DF64:
-        return G == 1 ? launch_sym_m<MODE_DF64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
-                      : launch_sym_m<MODE_DF64, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+        return G == 1 ? launch_sym_m<MODE_DF64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
+                      : launch_sym_m<MODE_DF64, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
       case MODE_MIXED:
-        return G == 1 ? launch_sym_m<MODE_MIXED, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
-                      : launch_sym_m<MODE_MIXED, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+        return G == 1 ? launch_sym_m<MODE_MIXED, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
+                      : launch_sym_m<MODE_MIXED, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
       case MODE_SPLIT:
-        return G == 1 ? launch_sym_m<MODE_SPLIT, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
-                      : launch_sym_m<MODE_SPLIT, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+        return G == 1 ? launch_sym_m<MODE_SPLIT, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
+                      : launch_sym_m<MODE_SPLIT, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
       default: return cudaErrorInvalidValue;
     }
   }
   const bool small = G == 4;  // 4 warps for 128-ion blocks
   switch (mode) {
     case MODE_FP64:
-      return small ? launch_sym_m<MODE_FP64, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
-                   : launch_sym_m<MODE_FP64, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+      return small ? launch_sym_m<MODE_FP64, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
+                   : launch_sym_m<MODE_FP64, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
     case MODE_DF64:
-      return small ? launch_sym_m<MODE_DF64, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
-                   : launch_sym_m<MODE_DF64, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+      return small ? launch_sym_m<MODE_DF64, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
+                   : launch_sym_m<MODE_DF64, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
     case MODE_MIXED:
-      return small ? launch_sym_m<MODE_MIXED, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
-                   : launch_sym_m<MODE_MIXED, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+      return small ? launch_sym_m<MODE_MIXED, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
+                   : launch_sym_m<MODE_MIXED, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
     case MODE_SPLIT:  // 64-ion P-tiles once the G/2 P-tiles outnumber the 8 warps
-      if (small) return launch_sym_m<MODE_SPLIT, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+      if (small) return launch_sym_m<MODE_SPLIT, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
       if (G == 32)  // 1024-ion blocks: 16 warps, so that the 16 P-tiles of 64 ions go round
-        return launch_sym_m<MODE_SPLIT, true, 512>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
-      return G >= 16 ? launch_sym_m<MODE_SPLIT, true, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st)
-                     : launch_sym_m<MODE_SPLIT, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, st);
+        return launch_sym_m<MODE_SPLIT, true, 512>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
+      return G >= 16 ? launch_sym_m<MODE_SPLIT, true, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
+                     : launch_sym_m<MODE_SPLIT, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -148,11 +148,12 @@ __device__ __forceinline__ bool verlet_kick_k(const Phys &p, const KickConst &kc
   return bad;
 }
 
-// The kick with its constants formed on the spot.
+// The kick with its constants formed on the spot; ion i of the view is ion
+// s.ion0 + i of the system, which keys its Langevin draws.
 __device__ __forceinline__ bool verlet_kick(const Phys &p, const StateView &s, int64_t i,
                                             int64_t snew, const double r[3], const double cs[3],
                                             double v[3], double a[3]) {
-  return verlet_kick_k(p, kick_consts(p, s, i), i, snew, r, cs, v, a);
+  return verlet_kick_k(p, kick_consts(p, s, i), s.ion0 + i, snew, r, cs, v, a);
 }
 
 }  // namespace nb

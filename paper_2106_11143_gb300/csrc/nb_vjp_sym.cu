@@ -4,16 +4,17 @@
 //   T = dl r^-3 - 3 (d . dl) r^-5 d
 // changes sign under i <-> j (both d and dl do), so one evaluation serves both
 // ions: g_i += w_j T and g_j -= w_i T.  The work is organised as in the force
-// kernel (nb_sym.cu): block pairs (P, Q), P <= Q, of BI = 32 G ions; each
-// warp takes Q-tiles and visits the P-tiles in the staggered order
-// pt = (qs + k) mod G, one per barrier-separated step, so the warps hold
-// distinct P-tiles and update their shared-memory accumulators without
-// atomics.  A lane holds one P-ion (position, weight and lam in registers);
-// the Q-tile (64 B per ion) sits twice in shared memory, so the entry
-// (lane + r) mod 32 of rotation r is a fixed offset from the lane's base; only
-// the Q accumulators rotate, by warp shuffle.  Diagonal items (P == Q) are
-// one-sided.  Output: one partial per partner block, part[(X*3 + c)*n + i],
-// summed in block order by the VJP epilogue: bitwise reproducible.
+// kernel (nb_sym.cu): block pairs (P, Q), P <= Q, of BI = 32 G ions, drawn
+// from the round-robin schedule of nb_symsched.cuh; each warp takes Q-tiles
+// and visits the P-tiles in the staggered order pt = (qs + k) mod G, one per
+// barrier-separated step, so the warps hold distinct P-tiles and update
+// their shared-memory accumulators without atomics.  A lane holds one P-ion
+// (position, weight and lam in registers); the Q-tile (64 B per ion) sits
+// twice in shared memory, so the entry (lane + r) mod 32 of rotation r is a
+// fixed offset from the lane's base; only the Q accumulators rotate, by warp
+// shuffle.  Diagonal items (P == Q) are one-sided.  Output: each item adds
+// its sums into acc[c * n + i] in round order (nb_symsched.cuh): bitwise
+// reproducible with no partial buffer.
 //
 // Four warps per block and 128-ion blocks at n < 16384 give enough items to
 // fill the GPU at the adjoint's sizes (528 items at n = 4096).
@@ -27,6 +28,7 @@
 #include <mutex>
 
 #include "nb_common.cuh"
+#include "nb_symsched.cuh"
 
 namespace nb {
 
@@ -124,6 +126,15 @@ __device__ __forceinline__ void vjp_stage(VD8 *dst, int i, int64_t g, int64_t n,
   }
 }
 
+// Where an item keeps its finished Q sums (and a diagonal item its block's
+// sums): at the start of the Q-tile's own 4 KB of staged entries (64 of 64 B
+// in the doubled layout), read only by the warp that owns the tile.  Sum c
+// of ion i of the block: double [i / 32][c][i mod 32] with a 512-double
+// stride per tile.
+__device__ __forceinline__ double &vqsum(VD8 *posQ, int c, int i) {
+  return reinterpret_cast<double *>(posQ)[(i >> 5) * 512 + c * 32 + (i & 31)];
+}
+
 template <bool QARR, bool DF>
 __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
@@ -134,18 +145,15 @@ __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, 
                                                          const double *__restrict__ ly,
                                                          const double *__restrict__ lz, double soft2,
                                                          const int *__restrict__ scales,
-                                                         double *__restrict__ part) {
+                                                         double *__restrict__ acc,
+                                                         int *__restrict__ sync, unsigned *err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int BI = 32 * G;
   VD8 *posP = reinterpret_cast<VD8 *>(smem_raw);
   VD8 *posQ = posP + BI;                                      // 2 BI entries (dup)
   double *accP = reinterpret_cast<double *>(posQ + 2 * BI);  // [3][BI]
-  int t = blockIdx.x, P = 0;
-  while (t >= nbk - P) {  // item -> (P, Q), P <= Q, row by row
-    t -= nbk - P;
-    ++P;
-  }
-  const int Q = P + t;
+  const SymItem it = sym_item(sym_draw(sync), nbk);
+  const int P = it.P, Q = it.Q;
   const int64_t p0 = (int64_t)P * BI, q0 = (int64_t)Q * BI;
   const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -180,8 +188,11 @@ __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, 
         for (int j = 0; j < np; ++j) vjp_eval<QARR>(pi, posP[j], soft2, a, dummy);
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + p0 + i] = a[c];
+      for (int c = 0; c < 3; ++c) vqsum(posQ, c, i) = a[c];
     }
+    __syncthreads();
+    sym_commit<VJP_THREADS>(it, n, p0, np, q0, nq, acc, sync, err,
+                            [&](int c, int i) { return vqsum(posQ, c, i); }, [&](int c, int i) { return 0.0; });
     return;
   }
 
@@ -247,23 +258,21 @@ __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, 
         aq[c] += b[c];
       }
     }
-    const int iq = qs * 32 + lane;
-    if (iq < nq)
+    __syncwarp();  // every lane is done reading the tile
 #pragma unroll
-      for (int c = 0; c < 3; ++c) part[((int64_t)P * 3 + c) * n + q0 + iq] = aq[c];
+    for (int c = 0; c < 3; ++c) vqsum(posQ, c, qs * 32 + lane) = aq[c];
   }
   __syncthreads();
-  for (int i = tid; i < np; i += VJP_THREADS)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) part[((int64_t)Q * 3 + c) * n + p0 + i] = accP[c * BI + i];
+  sym_commit<VJP_THREADS>(it, n, p0, np, q0, nq, acc, sync, err, [&](int c, int i) { return accP[c * BI + i]; },
+                          [&](int c, int i) { return vqsum(posQ, c, i); });
 }
 
 static size_t vjp_smem_bytes(int G) { return (size_t)32 * G * (3 * sizeof(VD8) + 3 * sizeof(double)); }
 
 cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const double *y,
                            const double *z, const double *q, const double *lx, const double *ly,
-                           const double *lz, double soft2, double *part, cudaStream_t st, bool df,
-                           const int *scales) {
+                           const double *lz, double soft2, double *part, int *sync, unsigned *err,
+                           cudaStream_t st, bool df, const int *scales) {
   if (G != 4 && G != 8) return cudaErrorInvalidValue;
   if (df && !scales) return cudaErrorInvalidValue;
   static std::mutex mu;
@@ -287,18 +296,20 @@ cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const dou
       done[dev] = true;
     }
   }
+  e = cudaMemsetAsync(sync, 0, sizeof(int) * sym_sync_ints(nbk), st);
+  if (e != cudaSuccess) return e;
   const int items = nbk * (nbk + 1) / 2;
   const size_t smem = vjp_smem_bytes(G);
   if (df) {
     if (q)
-      k_vjp_sym<true, true><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part);
+      k_vjp_sym<true, true><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part, sync, err);
     else
-      k_vjp_sym<false, true><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part);
+      k_vjp_sym<false, true><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part, sync, err);
   } else {
     if (q)
-      k_vjp_sym<true, false><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part);
+      k_vjp_sym<true, false><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part, sync, err);
     else
-      k_vjp_sym<false, false><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part);
+      k_vjp_sym<false, false><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part, sync, err);
   }
   return cudaGetLastError();
 }

@@ -85,7 +85,8 @@ def test_batched_matches_oracle_per_instance(nb, orc, precision):
               % (k, sizes[k], np.max(ep), np.max(ev), sp, sv))
         ph = dict(phys)
         ph["instance"] = k
-        fp, fv = floors.contract_floor(orc, orc.make_params(**ph), [pos[:, i0:i1], rp], nsteps, phys["dt"])
+        fp, fv = floors.contract_floor(orc, orc.make_params(**ph), [pos[:, i0:i1], rp], nsteps, phys["dt"],
+                                       vels=[vel[:, i0:i1], rv])
         assert np.all(ep <= 10 * sp + fp), k
         assert np.all(ev <= 10 * sv + fv), k
 
@@ -176,7 +177,8 @@ def test_full_ensemble_sampled(nb, orc, precision):
               % (k, sizes[k], np.max(ep), np.max(ev), sp, sv))
         ph = dict(phys)
         ph["instance"] = int(k)
-        fp, fv = floors.contract_floor(orc, orc.make_params(**ph), [pos[:, i0:i1], rp], nsteps, phys["dt"])
+        fp, fv = floors.contract_floor(orc, orc.make_params(**ph), [pos[:, i0:i1], rp], nsteps, phys["dt"],
+                                       vels=[vel[:, i0:i1], rv])
         assert np.all(ev <= 10 * sv + fv), k
         assert np.all(ep <= 10 * sp + fp), k
 

@@ -247,7 +247,7 @@ def _assert_traj_per_ion(orc, phys, pos0, sysm, ref, nsteps, tol_p, tol_v):
     gv = sysm.vel().cpu().numpy()
     rp = np.stack([ref["x"], ref["y"], ref["z"]])
     rv = np.stack([ref["vx"], ref["vy"], ref["vz"]])
-    fp, fv = floors.contract_floor(orc, oparams(orc, phys), [pos0, rp], nsteps, phys["dt"])
+    fp, fv = floors.contract_floor(orc, oparams(orc, phys), [pos0, rp], nsteps, phys["dt"], vels=[rv])
     ep, ev = floors.per_ion(gp - rp), floors.per_ion(gv - rv)
     assert np.all(ep <= tol_p + fp), (int(np.argmax(ep - fp)), float(np.max(ep - tol_p - fp)))
     assert np.all(ev <= tol_v + fv), (int(np.argmax(ev - fv)), float(np.max(ev - tol_v - fv)))
@@ -391,12 +391,12 @@ def test_full_size_sampled(nb, orc, precision):
     assert np.all(np.abs(g.sum(axis=1)) <= (1e-12 if precision in ("fp64", "df64") else 1e-6) * tot)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed_split"])
-def test_large_n_sampled(nb, orc, precision):
-    """N = 262151 (ragged): the symmetric kernel with about 4 GB of
-    per-partner-block partials (the scratch cap is a quarter of the device
-    memory); sampled ions against the oracle."""
-    n = 262151
+@pytest.mark.parametrize("precision,n", [("fp64", 262151), ("mixed_split", 262151), ("mixed_split", 2000003)])
+def test_large_n_sampled(nb, orc, precision, n):
+    """Ragged N = 262151 and N = 2000003: the symmetric kernel, which needs no
+    partial-sum buffer (it adds into the 3N output in round order), far past
+    where per-partner-block partials would have filled device memory;
+    sampled ions against the oracle."""
     pos, _ = W.random_cloud(n, seed=8, semi_axes=(300e-6, 300e-6, 1500e-6))
     phys = W.phys()
     g = gpu_forces(nb, phys, pos, precision=precision)

@@ -142,10 +142,10 @@ PLAN_NS = [1, 2, 3, 7, 8, 15, 16, 17, 31, 32, 33, 47, 48, 49, 63, 64, 65, 100, 1
 def test_plan_invariants(api):
     """Every launch plan (host only, no GPU) covers all n ions and all
     partners: the one-sided kernel's i-tiles and j-chunks tile [0, n) and its
-    grid stays within the launch limits; the symmetric kernel has one partial
-    slot per partner block of a supported size; the single-block path is
+    grid stays within the launch limits; the symmetric kernel's blocks of a
+    supported size cover [0, n); the single-block path is
     offered only within its 512-ion limit and never with the symmetric
-    kernel."""
+    kernel, which adds into a single output slot."""
     import math
     for kind, precs in (("force", list(api.PRECISIONS)), ("potential", ["fp64"]), ("vjp", ["fp64"])):
         for prec in precs:
@@ -153,8 +153,8 @@ def test_plan_invariants(api):
                 p = api.plan_info(kind, prec, n)
                 if p["symmetric"]:
                     assert p["G"] in ((1, 2, 4, 8, 16, 32) if kind == "force" else (4, 8)), (kind, prec, n, p)
-                    assert p["n_jc"] == math.ceil(n / (32 * p["G"])), (kind, prec, n, p)
-                    assert p["n_jc"] * 3 * n * 8 <= 2e9  # the host-only cap on the partials
+                    assert p["n_it"] == math.ceil(n / (32 * p["G"])), (kind, prec, n, p)  # blocks
+                    assert p["n_jc"] == 1 and p["n_it"] <= 60000, (kind, prec, n, p)
                 else:
                     assert p["block"] in (32, 64, 128, 256) and p["R"] in (1, 2, 4), (kind, prec, n, p)
                     assert p["n_it"] == math.ceil(n / (p["block"] * p["R"])), (kind, prec, n, p)
@@ -175,6 +175,13 @@ def test_plan_thresholds(api):
         assert api.plan_info("force", prec, start)["symmetric"]
     for prec in ("sqrtdiv", "rsq", "rsq_nr1", "rsq_nr2"):
         assert not api.plan_info("force", prec, 100000)["symmetric"]
+    # no memory cap: the half-pair kernel needs only its output, so it serves
+    # every size up to its 60000-block schedule limit
+    for prec in ("fp64", "df64", "mixed", "mixed_split"):
+        for n in (2_000_000, 20_000_000):
+            p = api.plan_info("force", prec, n)
+            assert p["symmetric"] and p["n_jc"] == 1, (prec, n, p)
+    assert api.plan_info("vjp", "fp64", 5_000_000)["symmetric"]
     assert not api.plan_info("vjp", "fp64", 2499)["symmetric"]
     assert api.plan_info("vjp", "fp64", 2500)["symmetric"]
     for prec, top in (("fp64", 32), ("mixed", 32), ("mixed_split", 32), ("df64", 48), ("sqrtdiv", 16),
@@ -219,6 +226,27 @@ def test_vjp_and_potential_plans_shared_by_precisions(api):
         api.set_tuning("force", "fp64", 0, 0, 0)
 
 
+def test_symmetric_schedule(api):
+    """The half-pair kernels' work schedule: every unordered block pair and
+    every block's own item exactly once; each round touches each block
+    exactly once, so the adds into a block happen one round after another;
+    items are numbered in round order (an item waits only on lower-numbered
+    ones, which keeps the grid progressing); rounds number nbk."""
+    for nbk in list(range(1, 41)) + [195, 196, 391, 1001]:
+        P, Q, R = api.sym_schedule(nbk)
+        assert len(P) == nbk * (nbk + 1) // 2
+        assert np.all(P <= Q) and np.all(P >= 0) and np.all(Q < nbk)
+        pairs = P.astype(np.int64) * nbk + Q
+        assert len(np.unique(pairs)) == len(pairs)  # each block pair once; with P <= Q: all of them
+        assert np.all(np.diff(R) >= 0) and R[0] == 0 and R[-1] == nbk - 1
+        for r in range(nbk):
+            sel = R == r
+            touched = np.concatenate([P[sel], Q[sel][Q[sel] != P[sel]]])
+            assert np.array_equal(np.sort(touched), np.arange(nbk)), (nbk, r)
+    with pytest.raises(api.NBError):
+        api.sym_schedule(0)
+
+
 def test_noalloc_capacity_holds_to_a_million(api):
     """nb_energy_noalloc's fixed array (2^20 doubles) holds the potential
     plan's partials (n_jc * n) plus 3 * 128 + 4 reduction doubles for every
@@ -235,23 +263,36 @@ def test_noalloc_capacity_holds_to_a_million(api):
 
 
 def test_bench_roofline_and_kernel_label(api):
-    """bench.py's roofline entry: convention-A flops (20 per interaction, N^2
-    interactions per step) over the kernel time, against peaks from unit
-    counts (2 FP64 or 128 FP32 FMA lanes per SM, 152 SMs, 2070 MHz); and its
-    kernel label follows the library's own plan at every precision."""
+    """bench.py's roofline entry: convention-A flops (20 per evaluation) on
+    the evaluations the planned kernel performs -- (N^2 + sum_b n_b^2)/2 for
+    the half-pair kernel's blocks, N^2 for the one-sided kernel -- over the
+    kernel time, against 2 flops x the measured lanes/clk/SM x 152 SMs x the
+    sampled clock; the kernel label follows the library's own plan."""
     import os
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
-    assert abs(bench.PEAK_TFLOPS["f32"] - 80.54784) < 1e-6
-    assert abs(bench.PEAK_TFLOPS["fp64"] - 1.25856) < 1e-6
-    r = bench.roofline("mixed_split", 100000, 4.853)
-    assert abs(r["achieved"] - 20 * 1e10 / 4.853e-3 / 1e12) < 1e-3
+    peaks = {"dfma": {"lanes_per_clk_per_sm": 2.0, "sm_mhz": 2070.0},
+             "ffma": {"lanes_per_clk_per_sm": 128.0, "sm_mhz": 2070.0}}
+    n = 100000
+    r = bench.roofline(api, "mixed_split", n, 4.853, peaks, 2070.0)
+    p = api.plan_info("force", "mixed_split", n)
+    assert p["symmetric"] == 1
+    bi = 32 * p["G"]
+    full, rem = divmod(n, bi)
+    evals = (n * n + full * bi * bi + rem * rem) // 2
+    assert r["evaluations_per_launch"] == evals
+    assert abs(r["achieved"] - 20 * evals / 4.853e-3 / 1e12) < 1e-3
+    assert abs(r["peak"] - 2 * 128 * 152 * 2070e6 / 1e12) < 1e-3
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-4
-    assert r["traffic"] == bench.NCU_TRAFFIC[("mixed_split", 100000)]
-    assert bench.roofline("fp64", 100000, 91.0)["peak"] == round(bench.PEAK_TFLOPS["fp64"], 2)
+    f = bench.roofline(api, "fp64", n, 91.0, peaks, 2070.0)
+    assert abs(f["peak"] - 2 * 2 * 152 * 2070e6 / 1e12) < 1e-3
+    assert f["conv_B"]["frac"] < f["frac"] < 1.2  # 16 executed FP64 flops per evaluation
     for prec in ("fp64", "df64", "mixed", "mixed_split"):
-        for n in (bench.SYM_FROM[prec] - 1, bench.SYM_FROM[prec], 16384, 100000):
+        for n in (400, 1499, 1500, 2000, 16384, 100000):
             sym = api.plan_info("force", prec, n)["symmetric"] == 1
-            assert bench.roofline(prec, n, 1.0)["kernel"].startswith("k_pair_sym" if sym else "k_pair_force"), \
-                (prec, n)
+            r = bench.roofline(api, prec, n, 1.0, peaks, None)
+            assert r["kernel"].startswith("k_pair_sym" if sym else "k_pair_force"), (prec, n)
+            assert r["evaluations_per_launch"] == (n * n if not sym else r["evaluations_per_launch"])
+    # a traffic figure recorded for other kernel sources is not reported
+    assert bench.recorded_traffic("mixed_split", 12345)[0] is None
