@@ -41,9 +41,10 @@ FP64_FLOPS_PER_EVAL_SYM = 2 * 6 + 4
 SM_COUNT = 152
 # The pipe whose rate bounds each path's pair kernel, and the probe kind that
 # measures it (nb_pipe_probe; 2 flops per FMA lane).
-PATH_PIPE = {"fp64": "dfma", "df64": "ffma", "mixed": "ffma", "mixed_split": "ffma"}
-DTYPE = {"fp64": "f64", "df64": "f32x2+f64", "mixed": "f32+f64", "mixed_split": "f32+f64"}
-ACCURACY_GATE = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6}
+PATH_PIPE = {"fp64": "dfma", "df64": "ffma", "mixed": "ffma", "mixed_split": "ffma", "mixed_split_rsq": "ffma"}
+DTYPE = {"fp64": "f64", "df64": "f32x2+f64", "mixed": "f32+f64", "mixed_split": "f32+f64", "mixed_split_rsq": "f32+f64"}
+ACCURACY_GATE = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6, "mixed_split_rsq": 1e-6}
+PATHS = ("fp64", "df64", "mixed", "mixed_split", "mixed_split_rsq")
 PROFILES = os.path.join(ROOT, "profiles")
 # Kernel sources a recorded DRAM-traffic figure is valid for.
 KERNEL_SOURCES = ("nb_sym.cu", "nb_pair.cu", "nb_common.cuh", "nb_pairterm.cuh")
@@ -56,7 +57,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed_split", choices=["fp64", "df64", "mixed", "mixed_split"])
+    ap.add_argument("--precision", default="mixed_split",
+                    choices=["fp64", "df64", "mixed", "mixed_split", "mixed_split_rsq"])
     ap.add_argument("--ions", "--n", dest="n", type=int, default=100000,
                     help="ions (default: the 1e5 workload); spelled --ions under torchrun, whose "
                          "parser takes --n for an abbreviation of its own options")
@@ -74,6 +76,9 @@ def parse():
                     help="profiling case: small-n steps (single-block at n = 16, windows at n = 1000)")
     ap.add_argument("--peaks", action="store_true",
                     help="only the measured pipe rates of this GPU (nb_pipe_probe), one JSON line")
+    ap.add_argument("--step-sweep", default=None, metavar="SIZES",
+                    help="step rate per N (comma-separated sizes, e.g. 10,100,1000,10000,100000) by "
+                         "launch path, one JSON line per N and precision")
     ap.add_argument("--cpu-sweep", action="store_true",
                     help="the oracle's force evaluation per N on one core and on all host cores, "
                          "beside the GPU force evaluation (one JSON line per N)")
@@ -298,7 +303,7 @@ def measure_peaks(nb, kinds=("dfma", "dadd", "ffma", "fadd", "mufu_rsq")):
         nb.pipe_probe(k, iters=16)
         r = nb.pipe_probe(k)
         out[k] = {"lanes_per_clk_per_sm": round(r["lanes_per_clk_per_sm"], 3), "sm_mhz": round(r["sm_mhz"], 1),
-                  "ms": round(r["ms"], 3)}
+                  "shape": r["shape"]}
     return out
 
 
@@ -402,7 +407,7 @@ def main_ours(args):
     sm_mhz = (head["clocks"] or {}).get("sm_mhz")
     paths = {}
     if not args.no_paths:
-        for pth in ("fp64", "df64", "mixed", "mixed_split"):
+        for pth in PATHS:
             r = head if pth == args.precision else run_path(nb, w, pth, max(2, min(args.steps, 5)), 1,
                                                             world, flush)
             paths[pth] = {"value": round(n * n / (r["ms_per_step"] / 1e3) / 1e9, 3), "unit": UNIT,
@@ -413,14 +418,17 @@ def main_ours(args):
         paths["speedup_mixed_split_over_fp64"] = round(
             paths["fp64"]["ms_per_step"] / paths["mixed_split"]["ms_per_step"], 3)
         paths["speedup_df64_over_fp64"] = round(paths["fp64"]["ms_per_step"] / paths["df64"]["ms_per_step"], 3)
+        paths["speedup_mixed_split_rsq_over_fp64"] = round(
+            paths["fp64"]["ms_per_step"] / paths["mixed_split_rsq"]["ms_per_step"], 3)
         paths["note"] = ("mixed is the literal form (FP64 displacement, then cast); mixed_split forms the "
-                         "displacement from FP32 (hi, lo) position pairs (reading C19); accuracy of each "
+                         "displacement from FP32 (hi, lo) position pairs (reading C19); mixed_split_rsq is "
+                         "mixed_split with the bare FP32 seed for r^-3 (no Newton step); accuracy of each "
                          "against the oracle is under cpu_baseline.accuracy_vs_oracle")
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu:
-        precs = ("fp64", "df64", "mixed", "mixed_split") if not args.no_paths else (args.precision,)
+        precs = PATHS if not args.no_paths else (args.precision,)
         cpu = cpu_baseline(w, gpu_acc={pr: gpu_forces(nb, w, pr) for pr in precs})
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -673,9 +681,130 @@ def cpu_sweep(sizes=(10, 100, 1000, 10000, 100000), target_s=2.0):
         print(json.dumps(row), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Step-rate sweep over the paper's 10^1 - 10^5 ion range (Sec. I, Sec. VI):
+# for each N and precision the device time of K velocity-Verlet steps through
+# nb_step, as ms per step, steps per second and G pair-interactions per second
+# (N^2 per step).  At small N a step is a few short kernels, so launch latency
+# dominates and the numbers depend on how the steps are issued:
+#   ms_per_step          one nb_step call of K steps, the library default
+#                        (single-block steps for the smallest N, else the
+#                        multi-kernel steps, with replays of a captured 8-step
+#                        window for N <= 4096)
+#   windows_ms_per_step  the multi-kernel steps with windows (N <= 4096)
+#   plain_ms_per_step    the multi-kernel steps without windows
+#   per_call_ms_per_step K nb_step calls of one step from Python
+#   graph_ms_per_step    K replays of one caller-captured graph of one step
+# Inputs: uniform seeded clouds of about 4 um spacing in a static harmonic trap.
+SWEEP_PRECISIONS = ["fp64", "df64", "mixed", "mixed_split"]
+
+
+def _sweep_steps(n):
+    return 2000 if n <= 1000 else (200 if n <= 10000 else 10)
+
+
+def _timed(fn, k):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / k
+
+
+def time_call(par, sysm, k, precision, small=None, windows=None):
+    """One nb_step call of k steps, after one untimed call of the same length;
+    small / windows = True or False force the single-block steps or the step
+    windows on or off, None keeps the library's default."""
+    from paper_2106_11143_gb300 import api
+    import torch
+    api.set_tuning("force", "fp64", 0, 0, 0)
+    if small is not None:
+        api.set_tuning("small_steps", precision, 0, 1 << 40, 1, R=int(small))
+    if windows is not None:
+        api.set_tuning("step_windows", precision, 0, 1 << 40, 1, R=int(windows))
+    try:
+        api.step(par, sysm, k)
+        torch.cuda.synchronize()
+        return _timed(lambda: api.step(par, sysm, k), k)
+    finally:
+        api.set_tuning("force", "fp64", 0, 0, 0)
+
+
+def time_per_call(par, sysm, k):
+    from paper_2106_11143_gb300 import api
+    import torch
+    api.step(par, sysm, 2)
+    torch.cuda.synchronize()
+
+    def run():
+        for _ in range(k):
+            api.step(par, sysm, 1)
+    return _timed(run, k)
+
+
+def time_graph(par, sysm, k, pos, vel):
+    from paper_2106_11143_gb300 import api
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        api.step(par, api.System(pos, vel), 1, stream=s)  # this stream's scratch
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        api.step(par, sysm, 1)
+    g.replay()
+    torch.cuda.synchronize()
+
+    def run():
+        for _ in range(k):
+            g.replay()
+    return _timed(run, k)
+
+
+def step_sweep(sizes=(10, 100, 1000, 10000, 100000), precisions=SWEEP_PRECISIONS, graphs=True):
+    import math
+    from paper_2106_11143_gb300 import api
+    from paper_2106_11143_gb300 import workloads as W
+    out = []
+    for n in sizes:
+        # about 4 um mean spacing at every N, so the clouds have similar dynamics
+        c = 4e-6 * (n / (4.0 / 3.0 * math.pi * 25.0)) ** (1.0 / 3.0)
+        pos, vel = W.random_cloud(n, seed=21, semi_axes=(c, c, 5 * c))
+        phys = W.phys(omega=(2 * math.pi * 1e6, 2 * math.pi * 1e6, 2 * math.pi * 200e3))
+        k = _sweep_steps(n)
+        for prec in precisions:
+            par = api.Params.from_phys(phys, precision=prec)
+            sysm = api.System(pos, vel)
+            api.forces(par, sysm, total=True)
+            ms = time_call(par, sysm, k, prec)
+            row = {"n": n, "precision": prec, "steps": k, "ms_per_step": round(ms, 5),
+                   "steps_per_s": round(1e3 / ms, 1), "G_pairs_per_s": round(n * n / ms / 1e6, 4)}
+            if n <= 4096:
+                row.update(windows_ms_per_step=round(time_call(par, sysm, k, prec, small=False, windows=True), 5))
+            if n <= 10000:
+                pms = time_call(par, sysm, k, prec, small=False, windows=False)
+                row.update(plain_ms_per_step=round(pms, 5), per_call_ms_per_step=round(time_per_call(par, sysm, k), 5))
+            if graphs and n <= 10000:
+                gms = time_graph(par, sysm, k, pos, vel)
+                row.update(graph_ms_per_step=round(gms, 5), graph_steps_per_s=round(1e3 / gms, 1),
+                           graph_G_pairs_per_s=round(n * n / gms / 1e6, 4))
+            out.append(row)
+    return out
+
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.peaks:
+    if a.step_sweep:
+        import torch
+        torch.cuda.set_device(0)
+        for row in step_sweep(tuple(int(v) for v in a.step_sweep.split(","))):
+            print(json.dumps(row))
+    elif a.peaks:
         main_peaks(a)
     elif a.cpu_sweep:
         cpu_sweep()

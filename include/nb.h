@@ -61,20 +61,28 @@ typedef enum {
  *                   hardware reciprocal square root (MUFU) is refined by a
  *                   Newton residual formed in compensated FP32 (Sec. IV:
  *                   approximate 1/sqrt refined by Newton-Raphson), and one
- *                   FP64 add widens r^-3.  Relative error of r^-3 <= 1.1e-13
- *                   (measured) for any FP64 displacement whose r^-3 is a
- *                   normal double.
+ *                   FP64 add widens r^-3.  This is FP64-class, not IEEE FP64
+ *                   per pair: r^-3 carries a relative error of up to 1.1e-13
+ *                   (about 500 ulp; measured over displacements from 1 nm to
+ *                   1 km and every exponent) where an IEEE FP64 evaluation
+ *                   would be within a few ulp.  Forces meet the 1e-12
+ *                   conditioned-error contract (measured 3.4e-14 at
+ *                   N = 1e5).  NB_FP64_RSQ_NR2 is the plain FP64 Newton form.
  *  NB_MIXED      -- pair displacements in FP64, cast to FP32; r^2, rsqrt,
  *                   r^-3 and the products in FP32; per-tile FP32 partial
  *                   sums added into FP64 accumulators with compensation.
  *  NB_MIXED_SPLIT -- as NB_MIXED, but each position is carried as an FP32
  *                   (hi, lo) pair built from the FP64 value once per call,
  *                   and the displacement is (hi_i - hi_j) + (lo_i - lo_j)
- *                   in FP32.  Same accuracy class as NB_MIXED while the
+ *                   in FP32: the FP64 difference, formed from the 48 bits
+ *                   the pair keeps, then rounded once to FP32 (hi_i - hi_j
+ *                   is exact for close pairs, the lo terms add the low
+ *                   bits).  Same accuracy class as NB_MIXED while the
  *                   coordinates are not much larger than the separations:
- *                   the (hi, lo) pair keeps about 48 bits, so the displacement
- *                   error is about 2^-48 |r| (relative 2^-48 |r| / |r_i - r_j|,
- *                   1e-6 at |r| / |r_i - r_j| ~ 3e8).
+ *                   the displacement error is about 2^-48 |r| beyond the
+ *                   FP32 rounding (relative 2^-48 |r| / |r_i - r_j|, 1e-6 at
+ *                   |r| / |r_i - r_j| ~ 3e8).  No FP64 instruction in the
+ *                   pair loop.
  *  NB_DF64       -- FP64-class accuracy from FP32 arithmetic: FP64
  *                   displacement split into an FP32 (hi, lo) pair; r^2,
  *                   r^-3 and the force products as double-floats (FP32
@@ -89,6 +97,13 @@ typedef enum {
  *                     the GPU counterpart of RSQRT14)
  *  NB_FP64_RSQ_NR1 -- seed + one Newton-Raphson step y (3 - r^2 y^2)/2
  *  NB_FP64_RSQ_NR2 -- seed + two Newton-Raphson steps
+ * and on the FP32 path of NB_MIXED_SPLIT:
+ *  NB_MIXED_SPLIT_RSQ -- NB_MIXED_SPLIT with r^-3 the cube of the bare FP32
+ *                     seed (no correction; the GPU counterpart of RSQRT14
+ *                     alone on the FP32 path): relative error of r^-3 about
+ *                     3.7e-7 from the seed (3 x 2^-22.9) plus FP32 rounding,
+ *                     inside the 1e-6 mixed-precision contract; three fewer
+ *                     FP32 instructions per pair.
  * Positions, velocities, the integrator and energies are FP64 in all modes. */
 typedef enum {
   NB_FP64 = 0,
@@ -98,7 +113,8 @@ typedef enum {
   NB_FP64_SQRTDIV = 4,
   NB_FP64_RSQ = 5,
   NB_FP64_RSQ_NR1 = 6,
-  NB_FP64_RSQ_NR2 = 7
+  NB_FP64_RSQ_NR2 = 7,
+  NB_MIXED_SPLIT_RSQ = 8
 } nb_precision;
 
 /* Confinement (Eq. 1 of the paper).
@@ -422,11 +438,14 @@ nb_status nb_rsqrt_seed_probe(int64_t n, const float *x, float *y, void *stream)
  * speed as a fraction of the FMA peak; this is that peak on the GPU).
  * kind: 0 FP64 FMA, 1 FP64 add, 2 FP64 multiply, 3 FP32 FMA, 4 FP32 add,
  * 5 FP32 reciprocal square root (MUFU).  Two blocks of 512 threads per SM
- * each run eight independent dependence chains for 16 * iters instructions
- * (1 <= iters <= 2^24).  out (HOST, 3 doubles): out[0] lanes retired per
+ * run independent dependence chains of the instruction in three shapes (4
+ * chains with their own operands, 4 and 8 chains sharing operands; the work
+ * of 4 * 8 * iters instructions per thread in each; 2 <= iters <= 2^24) and
+ * the fastest counts: register-bank conflicts make the attainable rate
+ * depend on the shape.  out (HOST, 3 doubles): out[0] lanes retired per
  * clock per SM (median over SMs, from the SM cycle counter), out[1] the SM
- * clock in MHz over the launch (cycles / event time), out[2] the launch's
- * duration in ms.  Allocates a few KB of device memory for the clock
+ * clock in MHz over that launch (cycles / event time), out[2] the shape
+ * (0, 1, 2 as listed).  Allocates a few KB of device memory for the clock
  * records and synchronises the stream.                                    */
 nb_status nb_pipe_probe(int32_t kind, int64_t iters, double out[3], void *stream);
 

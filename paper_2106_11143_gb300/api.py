@@ -15,7 +15,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnb.so")
 
-PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_split": 2, "df64": 3, "sqrtdiv": 4, "rsq": 5,
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_split": 2, "df64": 3, "sqrtdiv": 4, "rsq": 5, "mixed_split_rsq": 8,
               "rsq_nr1": 6, "rsq_nr2": 7}
 TRAPS = {"harmonic": 0, "rf": 1}
 NB_ACC_COULOMB, NB_ACC_TOTAL = 0, 1
@@ -471,17 +471,19 @@ def rsqrt_seed_probe(x, stream=None):
 
 
 PIPE_KINDS = {"dfma": 0, "dadd": 1, "dmul": 2, "ffma": 3, "fadd": 4, "mufu_rsq": 5}
-# default rounds of 16 x 8 instructions per thread: a few ms per kind
-PIPE_ITERS = {"dfma": 256, "dadd": 256, "dmul": 256, "ffma": 4096, "fadd": 4096, "mufu_rsq": 1024}
+# default rounds (each 4 x 8 instructions per thread, per shape): a few ms per kind
+PIPE_ITERS = {"dfma": 1024, "dadd": 1024, "dmul": 1024, "ffma": 16384, "fadd": 16384, "mufu_rsq": 4096}
+PIPE_SHAPES = ("4 chains, own operands", "4 chains, shared operands", "8 chains, shared operands")
 
 
 def pipe_probe(kind, iters=None, stream=None):
-    """nb_pipe_probe: measured throughput of one instruction kind on every SM.
-    Returns {"lanes_per_clk_per_sm", "sm_mhz", "ms"}."""
+    """nb_pipe_probe: measured throughput of one instruction kind on every SM
+    (the fastest of three chain shapes).  Returns {"lanes_per_clk_per_sm",
+    "sm_mhz", "shape"}."""
     out = (C.c_double * 3)()
     it = PIPE_ITERS[kind] if iters is None else int(iters)
     _check(lib().nb_pipe_probe(PIPE_KINDS[kind], it, out, _stream(stream)), "nb_pipe_probe")
-    return {"lanes_per_clk_per_sm": out[0], "sm_mhz": out[1], "ms": out[2]}
+    return {"lanes_per_clk_per_sm": out[0], "sm_mhz": out[1], "shape": PIPE_SHAPES[int(out[2])]}
 
 
 def sym_schedule(nbk):

@@ -134,7 +134,7 @@ nb_status check_params(const nb_params *p) {
   if (!finite(p->k_coulomb) || !finite(p->charge) || !finite(p->soft2) || p->soft2 < 0.0)
     return fail(NB_EINVAL, "k_coulomb, charge and soft2 must be finite (soft2 >= 0)");
   if (p->trap != NB_TRAP_HARMONIC && p->trap != NB_TRAP_RF) return fail(NB_EINVAL, "unknown trap %d", p->trap);
-  if (p->precision < NB_FP64 || p->precision > NB_FP64_RSQ_NR2)
+  if (p->precision < NB_FP64 || p->precision > NB_MIXED_SPLIT_RSQ)
     return fail(NB_EINVAL, "unknown precision %d", p->precision);
   for (int k = 0; k < 3; ++k)
     if (!finite(p->omega[k]) || !finite(p->omega_rate[k])) return fail(NB_EINVAL, "omega must be finite");
@@ -211,7 +211,7 @@ namespace {
 size_t force_bytes(const Plan &pl, int mode, int64_t n, bool extra_pos, bool phi, const Plan &plp) {
   Carver c;
   c.take<double>(part_doubles(pl, n, 3));
-  if (mode == MODE_SPLIT) c.take<float>(6 * (size_t)n);
+  if (split_like(mode)) c.take<float>(6 * (size_t)n);
   if (extra_pos) c.take<double>(3 * (size_t)n);
   if (phi) c.take<double>((size_t)plp.n_jc * n);
   return c.off + 256;
@@ -222,7 +222,7 @@ nb_status pair_forces(const Plan &pl, int mode, int64_t n, const double *x, cons
                       const double *z, const double *q, double soft2, double *part, float *split,
                       unsigned *err, cudaStream_t st) {
   PosF32 pf{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  if (mode == MODE_SPLIT) {
+  if (split_like(mode)) {
     NB_CUDA_TRY(launch_split_positions(n, x, y, z, split, st));
     count_launches(1);
     pf = PosF32{split, split + n, split + 2 * n, split + 3 * n, split + 4 * n, split + 5 * n};
@@ -473,7 +473,7 @@ nb_status nb_forces(const nb_params *params, const nb_system *sys, double *phi, 
   Carver cv;
   cv.base = a->buf;
   double *part = cv.take<double>(part_doubles(pl, n, 3));
-  float *split = mode == MODE_SPLIT ? cv.take<float>(6 * (size_t)n) : nullptr;
+  float *split = split_like(mode) ? cv.take<float>(6 * (size_t)n) : nullptr;
   double *ppart = phi ? cv.take<double>((size_t)plp.n_jc * n) : nullptr;
   const Phys p = to_phys(params);
   const StateView v = to_view(sys);
@@ -523,7 +523,7 @@ nb_status nb_step(const nb_params *params, nb_system *sys, int64_t nsteps, void 
   Carver cv;
   cv.base = a->buf;
   double *part = cv.take<double>(part_doubles(pl, n, 3));
-  float *split = mode == MODE_SPLIT ? cv.take<float>(6 * (size_t)n) : nullptr;
+  float *split = split_like(mode) ? cv.take<float>(6 * (size_t)n) : nullptr;
   double *other = cv.take<double>(3 * (size_t)n);
   double *ubuf[3] = {sys->x, sys->y, sys->z};
   double *obuf[3] = {other, other + n, other + 2 * n};
@@ -638,13 +638,13 @@ nb_status range_pair_sums(const nb_params *params, const nb_system *sys, int64_t
   const Plan pl = make_plan(n, mode, 0, false, ni);
   Carver need;
   need.take<double>((size_t)pl.n_jc * 3 * ni);
-  if (mode == MODE_SPLIT) need.take<float>(6 * (size_t)n);
+  if (split_like(mode)) need.take<float>(6 * (size_t)n);
   NB_TRY(get_arena(st, need.off + 256, arena));
   Carver cv;
   cv.base = (*arena)->buf;
   double *part = cv.take<double>((size_t)pl.n_jc * 3 * ni);
   PosF32 pf{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  if (mode == MODE_SPLIT) {
+  if (split_like(mode)) {
     float *split = cv.take<float>(6 * (size_t)n);
     NB_CUDA_TRY(launch_split_positions(n, sys->x, sys->y, sys->z, split, st));
     count_launches(1);
@@ -811,7 +811,7 @@ nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins
 nb_status nb_plan_info(int32_t kind, int32_t precision, int64_t n, int64_t out[8]) {
   if (!out) return fail(NB_EINVAL, "out is NULL");
   if (kind < 0 || kind > 2) return fail(NB_EINVAL, "kind must be 0 (force), 1 (potential) or 2 (VJP)");
-  if (precision < NB_FP64 || precision > NB_FP64_RSQ_NR2) return fail(NB_EINVAL, "bad precision");
+  if (precision < NB_FP64 || precision > NB_MIXED_SPLIT_RSQ) return fail(NB_EINVAL, "bad precision");
   if (n < 1) return fail(NB_EINVAL, "n must be >= 1");
   const Plan pl = make_plan(n, kind == 0 ? precision : MODE_FP64, kind);
   out[0] = pl.block;
@@ -845,7 +845,7 @@ nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n
     return NB_OK;
   }
   if (kind < 0 || kind > 8) return fail(NB_EINVAL, "kind must be 0..8");
-  if (precision < NB_FP64 || precision > NB_FP64_RSQ_NR2) return fail(NB_EINVAL, "bad precision");
+  if (precision < NB_FP64 || precision > NB_MIXED_SPLIT_RSQ) return fail(NB_EINVAL, "bad precision");
   if (n_lo < 0 || n_hi < n_lo) return fail(NB_EINVAL, "bad n range");
   if (kind == 4) {
     if (block != 32 && block != 64 && block != 128 && block != 256 && block != 512 && block != 1024)

@@ -28,9 +28,15 @@ enum Mode : int {
   MODE_SQRTDIV = 4,  // 1.0 / sqrt(r^2)
   MODE_RSQ = 5,      // hardware seed only (relative error ~2^-22)
   MODE_RSQ_NR1 = 6,  // seed + one FP64 Newton-Raphson step
-  MODE_RSQ_NR2 = 7   // seed + two FP64 Newton-Raphson steps
+  MODE_RSQ_NR2 = 7,  // seed + two FP64 Newton-Raphson steps
+  // the split positions with the bare FP32 seed for r^-3 (no correction)
+  MODE_SPLIT_RSQ = 8
 };
-__host__ __device__ constexpr bool fp64_like(int m) { return m == MODE_FP64 || m >= MODE_SQRTDIV; }
+// the ladder modes: FP64 pair arithmetic with one of the 1/sqrt methods
+__host__ __device__ constexpr bool ladder_mode(int m) { return m >= MODE_SQRTDIV && m <= MODE_RSQ_NR2; }
+__host__ __device__ constexpr bool fp64_like(int m) { return m == MODE_FP64 || ladder_mode(m); }
+// FP32 (hi, lo) position pairs and FP32 pair arithmetic
+__host__ __device__ constexpr bool split_like(int m) { return m == MODE_SPLIT || m == MODE_SPLIT_RSQ; }
 
 // ---------------------------------------------------------------------------
 // Integer-only conversions between FP64 and FP32 bit patterns.  On this GPU
@@ -483,38 +489,34 @@ __device__ __forceinline__ void vjp_term_df(double dx, double dy, double dz, dou
   }
 }
 
-// FP32 bulk shared by the two mixed modes: given the FP32 displacement,
-// acc += w_j d / s^3 with s^-3 = y^3 (1 + 3/2 e), y = MUFU.RSQ(s^2),
-// e = 1 - s^2 y^2 (one first-order correction in FP32).
-template <bool QARR>
-__device__ __forceinline__ void pair_f32_bulk(float fx, float fy, float fz, float qj,
-                                              float soft2f, float &ax, float &ay, float &az) {
-  const float r2 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, soft2f)));
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
-  y = fminf(y, F32_YMAX);
-  const float y2 = y * y;
-  const float e15 = fmaf(-1.5f * r2, y2, 1.5f);
-  const float y3 = y2 * y;
-  float s = fmaf(y3, e15, y3);
-  if (QARR) s *= qj;
-  ax = fmaf(fx, s, ax);
-  ay = fmaf(fy, s, ay);
-  az = fmaf(fz, s, az);
-}
-
 // FP32 r^-3 of an FP32 displacement (the mixed modes' bulk without the
 // accumulation): y = MUFU.RSQ(r^2) clamped against FP32 overflow, corrected
-// once: s = y^3 (1 + 3/2 e), e = 1 - r^2 y^2.
+// once: s = y^3 (1 + 3/2 e), e = 1 - r^2 y^2.  SEED: the bare seed's cube
+// y^3 (Sec. IV's approximate 1/sqrt without a Newton step; the seed's
+// relative error 2^-22.9 gives at most 3.9e-7 on r^-3).
+template <bool SEED = false>
 __device__ __forceinline__ float f32_rinv3(float fx, float fy, float fz, float soft2f) {
   const float r2 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, soft2f)));
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
   y = fminf(y, F32_YMAX);
   const float y2 = y * y;
-  const float e15 = fmaf(-1.5f * r2, y2, 1.5f);
   const float y3 = y2 * y;
+  if (SEED) return y3;
+  const float e15 = fmaf(-1.5f * r2, y2, 1.5f);
   return fmaf(y3, e15, y3);
+}
+
+// FP32 bulk shared by the mixed modes: given the FP32 displacement,
+// acc += w_j d / s^3 with s^-3 from f32_rinv3.
+template <bool QARR, bool SEED = false>
+__device__ __forceinline__ void pair_f32_bulk(float fx, float fy, float fz, float qj,
+                                              float soft2f, float &ax, float &ay, float &az) {
+  float s = f32_rinv3<SEED>(fx, fy, fz, soft2f);
+  if (QARR) s *= qj;
+  ax = fmaf(fx, s, ax);
+  ay = fmaf(fy, s, ay);
+  az = fmaf(fz, s, az);
 }
 
 // Exact FP32 -> FP64 widening by integer ops, for normal or zero inputs
@@ -582,8 +584,9 @@ struct Plan {
   int64_t jchunk = 0;
   int n_it = 0;
   int n_jc = 0;
-  // symmetric (half-pair) kernels: nbk blocks of 32 G ions; they add into
-  // one output slot in a fixed round order (nb_symsched.cuh), so n_jc = 1
+  // symmetric (half-pair) kernels: nbk blocks of 32 G ions.  They either
+  // add into one output slot in a fixed round order (nb_symsched.cuh,
+  // n_jc = 1) or write one partial slot per partner block (n_jc = nbk).
   int sym = 0;
   int G = 0;
   int nbk = 0;
@@ -626,7 +629,7 @@ void timing_end(cudaStream_t st);
 
 // Pair kernels (nb_pair.cu).  Partial outputs are [n_jc][3][n] (force, vjp)
 // or [n_jc][n] (phi), un-scaled sums over j of the pair terms.
-struct PosF32 {  // split FP32 positions for MODE_SPLIT: hi and lo parts
+struct PosF32 {  // split FP32 positions for the split modes: hi and lo parts
   const float *xh, *yh, *zh, *xl, *yl, *zl;
 };
 // part: part_doubles(pl, n, 3) doubles; err: the stream's device error word
@@ -659,11 +662,11 @@ cudaError_t launch_split_positions(int64_t n, const double *x, const double *y,
                                    const double *z, float *out6, cudaStream_t st);
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
                             const double *z, const double *q, const PosF32 &pf, double soft2,
-                            double *part, int *sync, unsigned *err, cudaStream_t st);
+                            double *part, int *sync, unsigned *err, bool inplace, cudaStream_t st);
 cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const double *y,
                            const double *z, const double *q, const double *lx, const double *ly,
                            const double *lz, double soft2, double *part, int *sync, unsigned *err,
-                           cudaStream_t st, bool df, const int *scales);
+                           bool inplace, cudaStream_t st, bool df, const int *scales);
 
 // Epilogue kernels (nb_integrate.cu).
 struct StateView {

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk, i
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t i = min(ibase + (int64_t)r * B, iend - 1);
-    if (MODE == MODE_SPLIT) {
+    if (split_like(MODE)) {
       xh[r] = pf.xh[i]; yh[r] = pf.yh[i]; zh[r] = pf.zh[i];
       xl[r] = pf.xl[i]; yl[r] = pf.yl[i]; zl[r] = pf.zl[i];
     } else {
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk, i
     __syncthreads();
     const int64_t j = j0 + tid;
     if (j < je) {
-      if (MODE == MODE_SPLIT) {
+      if (split_like(MODE)) {
         float4 *s4 = reinterpret_cast<float4 *>(smem_raw);
         const float qf = QARR ? (float)q[j] : 0.0f;
         s4[2 * tid] = make_float4(pf.xh[j], pf.yh[j], pf.zh[j], qf);
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk, i
         for (int r = 0; r < R; ++r)
           pair_f64<QARR>(xi[r], yi[r], zi[r], pj, soft2, ad[r][0], ad[r][1], ad[r][2]);
       }
-    } else if (MODE >= MODE_SQRTDIV) {
+    } else if (ladder_mode(MODE)) {
       const D4 *s4 = reinterpret_cast<const D4 *>(smem_raw);
 #pragma unroll 2
       for (int k = 0; k < cnt; ++k) {
@@ -154,11 +154,11 @@ __global__ void __launch_bounds__(256) k_pair_force(int64_t n, int64_t jchunk, i
           const float fx = (xh[r] - ph.x) + (xl[r] - pl.x);
           const float fy = (yh[r] - ph.y) + (yl[r] - pl.y);
           const float fz = (zh[r] - ph.z) + (zl[r] - pl.z);
-          pair_f32_bulk<QARR>(fx, fy, fz, ph.w, soft2f, af[r][0], af[r][1], af[r][2]);
+          pair_f32_bulk<QARR, MODE == MODE_SPLIT_RSQ>(fx, fy, fz, ph.w, soft2f, af[r][0], af[r][1], af[r][2]);
         }
       }
     }
-    if (MODE == MODE_MIXED || MODE == MODE_SPLIT) {
+    if (MODE == MODE_MIXED || split_like(MODE)) {
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -360,7 +360,7 @@ static cudaError_t launch_force_mr(const Plan &pl, int64_t n, int64_t i0, int64_
                                    const double *y, const double *z, const double *q, const PosF32 &pf,
                                    double soft2, double *part, cudaStream_t st) {
   const dim3 grid(pl.n_it, pl.n_jc);
-  const size_t smem = (MODE == MODE_SPLIT ? 2 * sizeof(float4) : sizeof(D4)) * pl.block;
+  const size_t smem = (split_like(MODE) ? 2 * sizeof(float4) : sizeof(D4)) * pl.block;
   if (q)
     k_pair_force<MODE, R, true><<<grid, pl.block, smem, st>>>(n, pl.jchunk, i0, ni, x, y, z, q, pf, soft2, part);
   else
@@ -393,6 +393,7 @@ cudaError_t launch_pair_force_range(const Plan &pl, int mode, int64_t n, int64_t
     case MODE_RSQ: return launch_force_m<MODE_RSQ>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
     case MODE_RSQ_NR1: return launch_force_m<MODE_RSQ_NR1>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
     case MODE_RSQ_NR2: return launch_force_m<MODE_RSQ_NR2>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
+    case MODE_SPLIT_RSQ: return launch_force_m<MODE_SPLIT_RSQ>(pl, n, i0, ni, x, y, z, q, pf, soft2, part, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -402,7 +403,8 @@ cudaError_t launch_pair_force(const Plan &pl, int mode, int64_t n, const double 
                               const PosF32 &pf, double soft2, double *part, unsigned *err,
                               cudaStream_t st) {
   if (pl.sym)
-    return launch_pair_sym(mode, n, pl.nbk, pl.G, x, y, z, q, pf, soft2, part, part_sync(pl, part, n, 3), err, st);
+    return launch_pair_sym(mode, n, pl.nbk, pl.G, x, y, z, q, pf, soft2, part, part_sync(pl, part, n, 3), err,
+                           pl.n_jc == 1, st);
   return launch_pair_force_range(pl, mode, n, 0, n, x, y, z, q, pf, soft2, part, st);
 }
 
@@ -426,7 +428,7 @@ cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const do
   if (df && !scales) return cudaErrorInvalidValue;
   if (pl.sym)
     return launch_vjp_sym(n, pl.nbk, pl.G, x, y, z, q, lx, ly, lz, soft2, part, part_sync(pl, part, n, 3), err,
-                          st, df, scales);
+                          pl.n_jc == 1, st, df, scales);
   const dim3 grid(pl.n_it, pl.n_jc);
   const size_t smem = 2 * sizeof(D4) * pl.block;
   if (df) {
@@ -519,6 +521,18 @@ bool tuning_lookup(int kind, int mode, int64_t n, int *block, int *R, int *bps) 
 // The symmetric kernels number their work items with an int: at most
 // SYM_MAX_BLOCKS blocks (nbk (nbk + 1) / 2 items).
 constexpr int64_t SYM_MAX_BLOCKS = 60000;
+// Output mode of the symmetric kernels (nb_symsched.cuh): the round-ordered
+// in-place adds from SYM_INPLACE_BLOCKS blocks on (at least about 4600
+// items, ten waves of three items per SM on 152 SMs, so the chain of nbk
+// commits overlaps later rounds' arithmetic), or earlier when the
+// per-partner-block partials (nbk * 3n doubles) would pass SYM_PARTIAL_BYTES.
+constexpr int64_t SYM_INPLACE_BLOCKS = 96;
+constexpr double SYM_PARTIAL_BYTES = 1e9;
+
+static int sym_slots(int64_t n, int64_t nbk) {
+  const bool inplace = nbk >= SYM_INPLACE_BLOCKS || (double)nbk * 3.0 * (double)n * 8.0 > SYM_PARTIAL_BYTES;
+  return inplace ? 1 : (int)nbk;
+}
 
 Plan make_plan(int64_t n, int mode, int kind, bool allow_sym, int64_t ni) {
   Plan pl;
@@ -531,10 +545,10 @@ Plan make_plan(int64_t n, int mode, int kind, bool allow_sym, int64_t ni) {
   // from n = 32768 and 512 from n = 60000; split: 256 from n = 4096 and
   // 512-ion blocks with two P-ions per lane from n = 8000.
   if (allow_sym && kind == 0 &&
-      (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || mode == MODE_SPLIT)) {
+      (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || split_like(mode))) {
     int G;
     bool use;
-    if (mode == MODE_SPLIT) {
+    if (split_like(mode)) {
       use = n >= 500;
       G = n >= 8000 ? 16 : (n >= 4096 ? 8 : (n >= 2500 ? 4 : (n >= 2000 ? 2 : 1)));
     } else {
@@ -554,7 +568,7 @@ Plan make_plan(int64_t n, int mode, int kind, bool allow_sym, int64_t ni) {
       pl.sym = 1;
       pl.G = G;
       pl.nbk = (int)nbk;
-      pl.n_jc = 1;
+      pl.n_jc = sym_slots(n, nbk);
       pl.block = 256;
       return pl;
     }
@@ -575,7 +589,7 @@ Plan make_plan(int64_t n, int mode, int kind, bool allow_sym, int64_t ni) {
       pl.sym = 1;
       pl.G = G;
       pl.nbk = (int)nbk;
-      pl.n_jc = 1;
+      pl.n_jc = sym_slots(n, nbk);
       pl.block = 128;
       return pl;
     }
@@ -586,7 +600,7 @@ Plan make_plan(int64_t n, int mode, int kind, bool allow_sym, int64_t ni) {
     // n = 8192 a target of 8 blocks per SM: more, shorter j-chunks only add
     // partials for the epilogue once the chunks hold about 30 partners.
     pl.block = n >= 24000 ? 256 : (n >= 3000 ? 128 : (n >= 1500 ? 64 : 32));
-    pl.R = (mode == MODE_SPLIT && n >= 24000) ? 4 : 1;
+    pl.R = (split_like(mode) && n >= 24000) ? 4 : 1;
     bps = n < 8192 ? 8 : 32;
   } else {
     pl.block = n >= 8192 ? 128 : (n >= 2048 ? 64 : 32);

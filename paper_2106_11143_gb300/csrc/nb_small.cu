@@ -34,7 +34,7 @@ __device__ __forceinline__ void chunk_partial(const D4 *pos, const float4 *sp, i
   float af[3] = {0.0f, 0.0f, 0.0f};
   double xi = 0.0, yi = 0.0, zi = 0.0;
   float xh = 0.0f, yh = 0.0f, zh = 0.0f, xl = 0.0f, yl = 0.0f, zl = 0.0f;
-  if (MODE == MODE_SPLIT) {
+  if (split_like(MODE)) {
     const float4 h = sp[2 * i], l = sp[2 * i + 1];
     xh = h.x; yh = h.y; zh = h.z;
     xl = l.x; yl = l.y; zl = l.z;
@@ -47,7 +47,7 @@ __device__ __forceinline__ void chunk_partial(const D4 *pos, const float4 *sp, i
     if (MODE == MODE_FP64) {
 #pragma unroll 4
       for (int k = 0; k < cnt; ++k) pair_f64<QARR>(xi, yi, zi, pos[j0 + k], soft2, ad[0], ad[1], ad[2]);
-    } else if (MODE >= MODE_SQRTDIV) {
+    } else if (ladder_mode(MODE)) {
 #pragma unroll 4
       for (int k = 0; k < cnt; ++k)
         pair_ladder<MODE, QARR>(xi, yi, zi, pos[j0 + k], soft2, ad[0], ad[1], ad[2]);
@@ -78,10 +78,10 @@ __device__ __forceinline__ void chunk_partial(const D4 *pos, const float4 *sp, i
         const float fx = (xh - ph.x) + (xl - pl.x);
         const float fy = (yh - ph.y) + (yl - pl.y);
         const float fz = (zh - ph.z) + (zl - pl.z);
-        pair_f32_bulk<QARR>(fx, fy, fz, ph.w, soft2f, af[0], af[1], af[2]);
+        pair_f32_bulk<QARR, MODE == MODE_SPLIT_RSQ>(fx, fy, fz, ph.w, soft2f, af[0], af[1], af[2]);
       }
     }
-    if (MODE == MODE_MIXED || MODE == MODE_SPLIT) {
+    if (MODE == MODE_MIXED || split_like(MODE)) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) flush_tile(af[c], ad[c], cd[c]);
     }
@@ -104,7 +104,7 @@ __device__ __forceinline__ void stage_ion(D4 *pos, float4 *sp, const StateView &
     *reinterpret_cast<float2 *>(&e.w) = make_float2(qh, ql);
   }
   pos[i] = e;
-  if (MODE == MODE_SPLIT) {
+  if (split_like(MODE)) {
     float h[3], l[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1)
   const int tid = threadIdx.x;
   D4 *pos = reinterpret_cast<D4 *>(smem_raw);
   float4 *sp = reinterpret_cast<float4 *>(pos + n);
-  double *part = reinterpret_cast<double *>(sp + (MODE == MODE_SPLIT ? 2 * n : 0));
+  double *part = reinterpret_cast<double *>(sp + (split_like(MODE) ? 2 * n : 0));
   const bool own = tid < n;
   const double dt = p.dt;
   const float soft2f = (float)p.soft2;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1)
 }
 
 size_t small_smem_bytes(const Plan &pl, int mode, int64_t n) {
-  return (size_t)n * sizeof(D4) + (mode == MODE_SPLIT ? (size_t)n * 2 * sizeof(float4) : 0) +
+  return (size_t)n * sizeof(D4) + (split_like(mode) ? (size_t)n * 2 * sizeof(float4) : 0) +
          (size_t)pl.n_jc * 3 * (size_t)n * sizeof(double);
 }
 
@@ -227,6 +227,7 @@ cudaError_t launch_small_steps(const Plan &pl, int mode, const Phys &p, const St
     case MODE_RSQ: return launch_small_m<MODE_RSQ>(pl, p, s, step0, nsteps, err, st);
     case MODE_RSQ_NR1: return launch_small_m<MODE_RSQ_NR1>(pl, p, s, step0, nsteps, err, st);
     case MODE_RSQ_NR2: return launch_small_m<MODE_RSQ_NR2>(pl, p, s, step0, nsteps, err, st);
+    case MODE_SPLIT_RSQ: return launch_small_m<MODE_SPLIT_RSQ>(pl, p, s, step0, nsteps, err, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -176,13 +176,13 @@ __device__ __forceinline__ void sym_step_mixed(const SD4 &pp, SD4 qd, float soft
 // One split-precision pair evaluation: P-ion (ph, pl) against Q-ion (qh, ql),
 // positions as FP32 (hi, lo) pairs with the weight in hi.w; the force goes
 // into a (P side) and, with the opposite sign, into b (Q side).
-template <bool W>
+template <bool W, bool SEED>
 __device__ __forceinline__ void split_eval(const float4 &ph, const float4 &pl, const float4 &qh,
                                            const float4 &ql, float soft2f, float a[3], float b[3]) {
   const float fx = (ph.x - qh.x) + (pl.x - ql.x);
   const float fy = (ph.y - qh.y) + (pl.y - ql.y);
   const float fz = (ph.z - qh.z) + (pl.z - ql.z);
-  const float s = f32_rinv3(fx, fy, fz, soft2f);
+  const float s = f32_rinv3<SEED>(fx, fy, fz, soft2f);
   const float sp = W ? s * qh.w : s, sq = W ? s * ph.w : s;
   a[0] = fmaf(fx, sp, a[0]);
   a[1] = fmaf(fy, sp, a[1]);
@@ -197,13 +197,13 @@ __device__ __forceinline__ void split_eval(const float4 &ph, const float4 &pl, c
 // pair); only the Q accumulators rotate through shuffles.  qhi, qlo point at
 // this lane's entry of the duplicated tile, so entry r of the rotation is
 // qhi[r] (a compile-time offset once the loop is unrolled).
-template <bool W>
+template <bool W, bool SEED>
 __device__ __forceinline__ void sym_step_split(const float4 &ph, const float4 &pl, const float4 *qhi,
                                                const float4 *qlo, float soft2f, int lane, float a[3],
                                                float b[3]) {
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
-    split_eval<W>(ph, pl, qhi[r], qlo[r], soft2f, a, b);
+    split_eval<W, SEED>(ph, pl, qhi[r], qlo[r], soft2f, a, b);
     b[0] = shfl_next(b[0], lane);
     b[1] = shfl_next(b[1], lane);
     b[2] = shfl_next(b[2], lane);
@@ -213,7 +213,7 @@ __device__ __forceinline__ void sym_step_split(const float4 &ph, const float4 &p
 // The same with two P-ions per lane (a 64-ion P-tile): one pair of Q loads
 // and one round of accumulator shuffles serve two pair evaluations, which
 // are independent up to their adds into b.
-template <bool W>
+template <bool W, bool SEED>
 __device__ __forceinline__ void sym_step_split2(const float4 &h1, const float4 &l1, const float4 &h2,
                                                 const float4 &l2, const float4 *qhi, const float4 *qlo,
                                                 float soft2f, int lane, float a1[3], float a2[3],
@@ -221,8 +221,8 @@ __device__ __forceinline__ void sym_step_split2(const float4 &h1, const float4 &
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
     const float4 qh = qhi[r], ql = qlo[r];
-    split_eval<W>(h1, l1, qh, ql, soft2f, a1, b);
-    split_eval<W>(h2, l2, qh, ql, soft2f, a2, b);
+    split_eval<W, SEED>(h1, l1, qh, ql, soft2f, a1, b);
+    split_eval<W, SEED>(h2, l2, qh, ql, soft2f, a2, b);
     b[0] = shfl_next(b[0], lane);
     b[1] = shfl_next(b[1], lane);
     b[2] = shfl_next(b[2], lane);
@@ -254,7 +254,7 @@ __device__ __forceinline__ void df_add(float &h, float &l, float v) {
 // P sums are double-floats in shared memory (accPf: [3][BI] hi, then
 // [3][BI] lo), the Q sums double-floats in registers, stored as FP64 (qsum)
 // once the warp is done with its Q-tile.
-template <bool W, int NW>
+template <bool W, int NW, bool SEED>
 __device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, SD4 *posQ, float *accPf, int G, int BI,
                                                    double soft2) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -269,8 +269,8 @@ __device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, SD4 *posQ, f
       __syncthreads();  // all warps are at step k: their P-tiles are distinct
       const int i1 = pt * 64 + lane, i2 = i1 + 32;
       float a1[3] = {0, 0, 0}, a2[3] = {0, 0, 0}, b[3] = {0, 0, 0};
-      sym_step_split2<W>(fP[i1], fP[BI + i1], fP[i2], fP[BI + i2], qhi, qlo, (float)soft2, lane, a1, a2,
-                         b);
+      sym_step_split2<W, SEED>(fP[i1], fP[BI + i1], fP[i2], fP[BI + i2], qhi, qlo, (float)soft2, lane, a1,
+                               a2, b);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         df_add(accPf[c * BI + i1], accPf[(3 + c) * BI + i1], a1[c]);
@@ -301,7 +301,7 @@ __device__ __forceinline__ void sym_offdiag(const SD4 *posP, SD4 *posQ, double *
       __syncthreads();  // all warps are at step k: their P-tiles are distinct
       const SD4 pp = posP[pt * 32 + lane];
       const int ip = pt * 32 + lane;
-      if (MODE == MODE_MIXED || MODE == MODE_SPLIT) {
+      if (MODE == MODE_MIXED || split_like(MODE)) {
         float a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
         if (MODE == MODE_MIXED) {
           sym_step_mixed<W>(pp, qh, (float)soft2, lane, a, b);
@@ -313,8 +313,8 @@ __device__ __forceinline__ void sym_offdiag(const SD4 *posP, SD4 *posQ, double *
         } else {
           const float4 *fP = reinterpret_cast<const float4 *>(posP);
           const float4 *fQ = reinterpret_cast<const float4 *>(posQ);
-          sym_step_split<W>(fP[ip], fP[BI + ip], fQ + qs * 64 + lane, fQ + 2 * BI + qs * 64 + lane,
-                            (float)soft2, lane, a, b);
+          sym_step_split<W, MODE == MODE_SPLIT_RSQ>(fP[ip], fP[BI + ip], fQ + qs * 64 + lane,
+                                                    fQ + 2 * BI + qs * 64 + lane, (float)soft2, lane, a, b);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             df_add(accPf[c * BI + ip], accPf[(3 + c) * BI + ip], a[c]);
@@ -342,7 +342,7 @@ __device__ __forceinline__ void sym_offdiag(const SD4 *posP, SD4 *posQ, double *
     __syncwarp();  // every lane is done reading the tile
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      qsum(posQ, c, qs * 32 + lane) = (MODE == MODE_SPLIT) ? f32_to_f64(qfh[c]) + f32_to_f64(qfl[c]) : aq[c];
+      qsum(posQ, c, qs * 32 + lane) = split_like(MODE) ? f32_to_f64(qfh[c]) + f32_to_f64(qfl[c]) : aq[c];
   }
 }
 
@@ -355,7 +355,7 @@ __device__ __forceinline__ void sym_stage(SD4 *dst, int i, int BI, int64_t g, in
                                           const PosF32 &pf, bool dup) {
   const bool real = g < n;
   const double w = real ? (QARR ? q[g] : 1.0) : 0.0;
-  if (MODE == MODE_SPLIT) {
+  if (split_like(MODE)) {
     // P side: [BI hi entries][BI lo entries].  Q side (dup): every 32-ion
     // tile stored twice back to back, [2 BI hi][2 BI lo], so that the entry
     // (lane + r) of a rotation is at a fixed offset r from the lane's base.
@@ -385,7 +385,7 @@ __device__ __forceinline__ void sym_stage(SD4 *dst, int i, int BI, int64_t g, in
   dst[i] = e;
 }
 
-template <int MODE, bool QARR, bool P2, int NT>
+template <int MODE, bool QARR, bool P2, int NT, bool INPLACE>
 __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ y,
@@ -393,12 +393,13 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_s
                                                          const double *__restrict__ q, PosF32 pf,
                                                          double soft2, double *__restrict__ acc,
                                                          int *__restrict__ sync, unsigned *err) {
+  constexpr bool inplace = INPLACE;  // the output mode, fixed at compile time
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int BI = 32 * G;
   SD4 *posP = reinterpret_cast<SD4 *>(smem_raw);
   SD4 *posQ = posP + BI;
-  double *accP = reinterpret_cast<double *>(posQ + (MODE == MODE_SPLIT ? 2 * BI : BI));  // [3][BI]
-  const SymItem it = sym_item(sym_draw(sync), nbk);
+  double *accP = reinterpret_cast<double *>(posQ + (split_like(MODE) ? 2 * BI : BI));  // [3][BI]
+  const SymItem it = sym_block_item(inplace, sync, nbk);
   const int P = it.P, Q = it.Q;
   const int64_t p0 = (int64_t)P * BI, q0 = (int64_t)Q * BI;
   const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_s
     for (int i = tid; i < np; i += NT) {
       const SD4 pi = posP[i];
       double a[3] = {0.0, 0.0, 0.0};
-      if (MODE == MODE_MIXED || MODE == MODE_SPLIT) {
+      if (MODE == MODE_MIXED || split_like(MODE)) {
         float af[3] = {0, 0, 0};
         const float4 *f = reinterpret_cast<const float4 *>(posP);
         for (int j = 0; j < np; ++j) {
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_s
             fz = (ih.z - jh.z) + (il.z - jl.z);
             wj = jh.w;
           }
-          float sj = f32_rinv3(fx, fy, fz, (float)soft2);
+          float sj = f32_rinv3<MODE == MODE_SPLIT_RSQ>(fx, fy, fz, (float)soft2);
           if (QARR) sj *= wj;
           af[0] = fmaf(fx, sj, af[0]);
           af[1] = fmaf(fy, sj, af[1]);
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_s
       for (int c = 0; c < 3; ++c) qsum(posQ, c, i) = a[c];
     }
     __syncthreads();
-    sym_commit<NT>(it, n, p0, np, q0, nq, acc, sync, err, [&](int c, int i) { return qsum(posQ, c, i); },
+    sym_output<NT>(inplace, it, n, p0, np, q0, nq, acc, sync, err, [&](int c, int i) { return qsum(posQ, c, i); },
                    [&](int c, int i) { return 0.0; });
     return;
   }
@@ -511,32 +512,32 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_s
   float *accPf = reinterpret_cast<float *>(accP);
   if (P2) {
     if (weighted)
-      sym_offdiag_split2<true, NT / 32>(posP, posQ, accPf, G, BI, soft2);
+      sym_offdiag_split2<true, NT / 32, MODE == MODE_SPLIT_RSQ>(posP, posQ, accPf, G, BI, soft2);
     else
-      sym_offdiag_split2<false, NT / 32>(posP, posQ, accPf, G, BI, soft2);
+      sym_offdiag_split2<false, NT / 32, MODE == MODE_SPLIT_RSQ>(posP, posQ, accPf, G, BI, soft2);
   } else if (weighted) {
     sym_offdiag<MODE, true, NT / 32>(posP, posQ, accP, G, BI, soft2, s2h, s2l);
   } else {
     sym_offdiag<MODE, false, NT / 32>(posP, posQ, accP, G, BI, soft2, s2h, s2l);
   }
   __syncthreads();
-  if (MODE == MODE_SPLIT)
-    sym_commit<NT>(it, n, p0, np, q0, nq, acc, sync, err,
+  if (split_like(MODE))
+    sym_output<NT>(inplace, it, n, p0, np, q0, nq, acc, sync, err,
                    [&](int c, int i) { return f32_to_f64(accPf[c * BI + i]) + f32_to_f64(accPf[(3 + c) * BI + i]); },
                    [&](int c, int i) { return qsum(posQ, c, i); });
   else
-    sym_commit<NT>(it, n, p0, np, q0, nq, acc, sync, err, [&](int c, int i) { return accP[c * BI + i]; },
+    sym_output<NT>(inplace, it, n, p0, np, q0, nq, acc, sync, err, [&](int c, int i) { return accP[c * BI + i]; },
                    [&](int c, int i) { return qsum(posQ, c, i); });
 }
 
 size_t sym_smem_bytes(int G, int mode) {
-  return (size_t)32 * G * ((mode == MODE_SPLIT ? 3 : 2) * sizeof(SD4) + 3 * sizeof(double));
+  return (size_t)32 * G * ((split_like(mode) ? 3 : 2) * sizeof(SD4) + 3 * sizeof(double));
 }
 
 template <int MODE, bool P2, int NT>
 static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, const double *y,
                                 const double *z, const double *q, const PosF32 &pf, double soft2,
-                                double *part, int *sync, unsigned *err, cudaStream_t st) {
+                                double *part, int *sync, unsigned *err, bool inplace, cudaStream_t st) {
   static std::mutex mu;
   static bool done[64] = {false};
   int dev = 0;
@@ -547,64 +548,88 @@ static cudaError_t launch_sym_m(int64_t n, int nbk, int G, const double *x, cons
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!done[dev]) {
       const int lim = (int)sym_smem_bytes(32, MODE);
-      e = cudaFuncSetAttribute(k_pair_sym<MODE, true, P2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      e = cudaFuncSetAttribute(k_pair_sym<MODE, true, P2, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pair_sym<MODE, false, P2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_pair_sym<MODE, false, P2, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 lim);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pair_sym<MODE, true, P2, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 lim);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pair_sym<MODE, false, P2, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  lim);
       if (e != cudaSuccess) return e;
       done[dev] = true;
     }
   }
-  e = cudaMemsetAsync(sync, 0, sizeof(int) * sym_sync_ints(nbk), st);
-  if (e != cudaSuccess) return e;
+  if (inplace) {
+    e = cudaMemsetAsync(sync, 0, sizeof(int) * sym_sync_ints(nbk), st);
+    if (e != cudaSuccess) return e;
+  }
   const int items = nbk * (nbk + 1) / 2;
   const size_t smem = sym_smem_bytes(G, MODE);
-  if (q)
-    k_pair_sym<MODE, true, P2, NT><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err);
+  if (q && inplace)
+    k_pair_sym<MODE, true, P2, NT, true><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err);
+  else if (q)
+    k_pair_sym<MODE, true, P2, NT, false><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err);
+  else if (inplace)
+    k_pair_sym<MODE, false, P2, NT, true><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err);
   else
-    k_pair_sym<MODE, false, P2, NT><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err);
+    k_pair_sym<MODE, false, P2, NT, false><<<items, NT, smem, st>>>(n, nbk, G, x, y, z, q, pf, soft2, part, sync,
+                                                                     err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
                             const double *z, const double *q, const PosF32 &pf, double soft2,
-                            double *part, int *sync, unsigned *err, cudaStream_t st) {
+                            double *part, int *sync, unsigned *err, bool inplace, cudaStream_t st) {
   if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
   constexpr int S = SYM_THREADS_SMALL, L = SYM_THREADS;
   if (G <= 2) {  // 32- and 64-ion blocks at small n: one warp per 32-ion tile
     switch (mode) {
       case MODE_FP64:
-        return G == 1 ? launch_sym_m<MODE_FP64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
-                      : launch_sym_m<MODE_FP64, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
+        return G == 1 ? launch_sym_m<MODE_FP64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
+                      : launch_sym_m<MODE_FP64, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
       case MODE_DF64:
-        return G == 1 ? launch_sym_m<MODE_DF64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
-                      : launch_sym_m<MODE_DF64, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
+        return G == 1 ? launch_sym_m<MODE_DF64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
+                      : launch_sym_m<MODE_DF64, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
       case MODE_MIXED:
-        return G == 1 ? launch_sym_m<MODE_MIXED, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
-                      : launch_sym_m<MODE_MIXED, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
+        return G == 1 ? launch_sym_m<MODE_MIXED, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
+                      : launch_sym_m<MODE_MIXED, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
       case MODE_SPLIT:
-        return G == 1 ? launch_sym_m<MODE_SPLIT, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
-                      : launch_sym_m<MODE_SPLIT, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
+        return G == 1 ? launch_sym_m<MODE_SPLIT, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
+                      : launch_sym_m<MODE_SPLIT, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
+      case MODE_SPLIT_RSQ:
+        return G == 1 ? launch_sym_m<MODE_SPLIT_RSQ, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err,
+                                                                inplace, st)
+                      : launch_sym_m<MODE_SPLIT_RSQ, false, 64>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err,
+                                                                inplace, st);
       default: return cudaErrorInvalidValue;
     }
   }
   const bool small = G == 4;  // 4 warps for 128-ion blocks
   switch (mode) {
     case MODE_FP64:
-      return small ? launch_sym_m<MODE_FP64, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
-                   : launch_sym_m<MODE_FP64, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
+      return small ? launch_sym_m<MODE_FP64, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
+                   : launch_sym_m<MODE_FP64, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
     case MODE_DF64:
-      return small ? launch_sym_m<MODE_DF64, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
-                   : launch_sym_m<MODE_DF64, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
+      return small ? launch_sym_m<MODE_DF64, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
+                   : launch_sym_m<MODE_DF64, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
     case MODE_MIXED:
-      return small ? launch_sym_m<MODE_MIXED, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
-                   : launch_sym_m<MODE_MIXED, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
+      return small ? launch_sym_m<MODE_MIXED, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
+                   : launch_sym_m<MODE_MIXED, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
     case MODE_SPLIT:  // 64-ion P-tiles once the G/2 P-tiles outnumber the 8 warps
-      if (small) return launch_sym_m<MODE_SPLIT, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
+      if (small) return launch_sym_m<MODE_SPLIT, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
       if (G == 32)  // 1024-ion blocks: 16 warps, so that the 16 P-tiles of 64 ions go round
-        return launch_sym_m<MODE_SPLIT, true, 512>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
-      return G >= 16 ? launch_sym_m<MODE_SPLIT, true, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st)
-                     : launch_sym_m<MODE_SPLIT, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, st);
+        return launch_sym_m<MODE_SPLIT, true, 512>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
+      return G >= 16 ? launch_sym_m<MODE_SPLIT, true, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
+                     : launch_sym_m<MODE_SPLIT, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
+    case MODE_SPLIT_RSQ:
+      if (small) return launch_sym_m<MODE_SPLIT_RSQ, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
+      if (G == 32)  // 1024-ion blocks: 16 warps, so that the 16 P-tiles of 64 ions go round
+        return launch_sym_m<MODE_SPLIT_RSQ, true, 512>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
+      return G >= 16 ? launch_sym_m<MODE_SPLIT_RSQ, true, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
+                     : launch_sym_m<MODE_SPLIT_RSQ, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
     default: return cudaErrorInvalidValue;
   }
 }

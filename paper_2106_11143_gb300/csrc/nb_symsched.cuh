@@ -20,6 +20,8 @@
 // every ion's sum is formed in round order, whatever order the items run
 // in, and the result is bitwise reproducible with no partial-sum buffer:
 // the output itself is the only accumulator, 3 n doubles, which L2 holds.
+// (sym_output below also offers the per-partner-block partials for small
+// schedules.)
 //
 // Ordering and progress.  A block of the grid draws its item number from a
 // counter (atomicAdd) when it starts, so item t runs only after every item
@@ -27,7 +29,8 @@
 // only for lower-numbered items (the previous round), so the lowest
 // unfinished item never waits and the grid always progresses.  The wait is a
 // bounded spin on the per-block round counters with acquire loads; the
-// writer publishes with fences and a release store.  A wait that runs out
+// writer's threads meet at a barrier, then its thread 0 fences and
+// publishes with a release store.  A wait that runs out
 // sets ERR_TIMEOUT in the stream's error word and skips its adds (the
 // result is then wrong and flagged; the kernel still ends).
 //
@@ -146,12 +149,43 @@ __device__ __forceinline__ void sym_commit(const SymItem &it, int64_t n, int64_t
         }
     }
   }
-  __threadfence();
-  __syncthreads();
+  __syncthreads();  // every thread's adds happen before thread 0's release
   if (tid == 0) {
+    __threadfence();
     st_release(sync + 1 + it.P, it.round + 1);
     if (it.P != it.Q) st_release(sync + 1 + it.Q, it.round + 1);
   }
+}
+
+// The item's output in either of the two modes of the half-pair kernels:
+//  - inplace: sym_commit, the round-ordered adds into acc ([3][n], no
+//    partial buffer); used when there are many items per resident block, so
+//    the rounds' commits overlap the arithmetic of later rounds;
+//  - partials: one slot per partner block, acc[(X * 3 + c) * n + i] for the
+//    sum over block X, which the epilogue adds in block order; used when the
+//    items fit in a few waves, where the chain of nbk commits would follow
+//    the arithmetic instead of overlapping it.
+template <int NT, class FP, class FQ>
+__device__ __forceinline__ void sym_output(bool inplace, const SymItem &it, int64_t n, int64_t p0, int np,
+                                           int64_t q0, int nq, double *acc, int *sync, unsigned *err, FP sumP,
+                                           FQ sumQ) {
+  if (inplace) {
+    sym_commit<NT>(it, n, p0, np, q0, nq, acc, sync, err, sumP, sumQ);
+    return;
+  }
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    for (int i = tid; i < np; i += NT) acc[((int64_t)it.Q * 3 + c) * n + p0 + i] = sumP(c, i);
+    if (it.P != it.Q)
+      for (int i = tid; i < nq; i += NT) acc[((int64_t)it.P * 3 + c) * n + q0 + i] = sumQ(c, i);
+  }
+}
+
+// The item a block works on: drawn from the counter in the in-place mode
+// (so that waits point only at running items), blockIdx.x otherwise.
+__device__ __forceinline__ SymItem sym_block_item(bool inplace, int *sync, int nbk) {
+  return sym_item(inplace ? sym_draw(sync) : (int)blockIdx.x, nbk);
 }
 
 }  // namespace nb

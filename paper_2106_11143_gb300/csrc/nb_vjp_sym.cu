@@ -135,7 +135,7 @@ __device__ __forceinline__ double &vqsum(VD8 *posQ, int c, int i) {
   return reinterpret_cast<double *>(posQ)[(i >> 5) * 512 + c * 32 + (i & 31)];
 }
 
-template <bool QARR, bool DF>
+template <bool QARR, bool DF, bool INPLACE>
 __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ y,
@@ -147,12 +147,13 @@ __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, 
                                                          const int *__restrict__ scales,
                                                          double *__restrict__ acc,
                                                          int *__restrict__ sync, unsigned *err) {
+  constexpr bool inplace = INPLACE;  // the output mode, fixed at compile time
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int BI = 32 * G;
   VD8 *posP = reinterpret_cast<VD8 *>(smem_raw);
   VD8 *posQ = posP + BI;                                      // 2 BI entries (dup)
   double *accP = reinterpret_cast<double *>(posQ + 2 * BI);  // [3][BI]
-  const SymItem it = sym_item(sym_draw(sync), nbk);
+  const SymItem it = sym_block_item(inplace, sync, nbk);
   const int P = it.P, Q = it.Q;
   const int64_t p0 = (int64_t)P * BI, q0 = (int64_t)Q * BI;
   const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, 
       for (int c = 0; c < 3; ++c) vqsum(posQ, c, i) = a[c];
     }
     __syncthreads();
-    sym_commit<VJP_THREADS>(it, n, p0, np, q0, nq, acc, sync, err,
+    sym_output<VJP_THREADS>(inplace, it, n, p0, np, q0, nq, acc, sync, err,
                             [&](int c, int i) { return vqsum(posQ, c, i); }, [&](int c, int i) { return 0.0; });
     return;
   }
@@ -263,7 +264,8 @@ __global__ void __launch_bounds__(VJP_THREADS, 4) k_vjp_sym(int64_t n, int nbk, 
     for (int c = 0; c < 3; ++c) vqsum(posQ, c, qs * 32 + lane) = aq[c];
   }
   __syncthreads();
-  sym_commit<VJP_THREADS>(it, n, p0, np, q0, nq, acc, sync, err, [&](int c, int i) { return accP[c * BI + i]; },
+  sym_output<VJP_THREADS>(inplace, it, n, p0, np, q0, nq, acc, sync, err,
+                          [&](int c, int i) { return accP[c * BI + i]; },
                           [&](int c, int i) { return vqsum(posQ, c, i); });
 }
 
@@ -272,7 +274,7 @@ static size_t vjp_smem_bytes(int G) { return (size_t)32 * G * (3 * sizeof(VD8) +
 cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const double *y,
                            const double *z, const double *q, const double *lx, const double *ly,
                            const double *lz, double soft2, double *part, int *sync, unsigned *err,
-                           cudaStream_t st, bool df, const int *scales) {
+                           bool inplace, cudaStream_t st, bool df, const int *scales) {
   if (G != 4 && G != 8) return cudaErrorInvalidValue;
   if (df && !scales) return cudaErrorInvalidValue;
   static std::mutex mu;
@@ -285,32 +287,39 @@ cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const dou
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!done[dev]) {
       const int lim = (int)vjp_smem_bytes(8);
-      e = cudaFuncSetAttribute(k_vjp_sym<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_vjp_sym<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_vjp_sym<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_vjp_sym<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      const void *fns[8] = {(const void *)k_vjp_sym<true, false, false>, (const void *)k_vjp_sym<false, false, false>,
+                            (const void *)k_vjp_sym<true, true, false>, (const void *)k_vjp_sym<false, true, false>,
+                            (const void *)k_vjp_sym<true, false, true>, (const void *)k_vjp_sym<false, false, true>,
+                            (const void *)k_vjp_sym<true, true, true>, (const void *)k_vjp_sym<false, true, true>};
+      for (int k = 0; k < 8 && e == cudaSuccess; ++k)
+        e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       if (e != cudaSuccess) return e;
       done[dev] = true;
     }
   }
-  e = cudaMemsetAsync(sync, 0, sizeof(int) * sym_sync_ints(nbk), st);
-  if (e != cudaSuccess) return e;
+  if (inplace) {
+    e = cudaMemsetAsync(sync, 0, sizeof(int) * sym_sync_ints(nbk), st);
+    if (e != cudaSuccess) return e;
+  }
   const int items = nbk * (nbk + 1) / 2;
   const size_t smem = vjp_smem_bytes(G);
-  if (df) {
-    if (q)
-      k_vjp_sym<true, true><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part, sync, err);
-    else
-      k_vjp_sym<false, true><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part, sync, err);
+#define NB_VJP_LAUNCH(QA, DFV, IP)                                                                     \
+  k_vjp_sym<QA, DFV, IP><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part, \
+                                                           sync, err)
+  if (inplace) {
+    if (df) {
+      if (q) NB_VJP_LAUNCH(true, true, true); else NB_VJP_LAUNCH(false, true, true);
+    } else {
+      if (q) NB_VJP_LAUNCH(true, false, true); else NB_VJP_LAUNCH(false, false, true);
+    }
   } else {
-    if (q)
-      k_vjp_sym<true, false><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part, sync, err);
-    else
-      k_vjp_sym<false, false><<<items, VJP_THREADS, smem, st>>>(n, nbk, G, x, y, z, q, lx, ly, lz, soft2, scales, part, sync, err);
+    if (df) {
+      if (q) NB_VJP_LAUNCH(true, true, false); else NB_VJP_LAUNCH(false, true, false);
+    } else {
+      if (q) NB_VJP_LAUNCH(true, false, false); else NB_VJP_LAUNCH(false, false, false);
+    }
   }
+#undef NB_VJP_LAUNCH
   return cudaGetLastError();
 }
 

@@ -62,7 +62,7 @@ def tune_pair(precision, quick=False, log=print):
         reps = 3 if (precision == "fp64" and n >= 100000) else 10
         best = None
         for (b, r, bps) in shapes:
-            if precision != "mixed_split" and r > 1:
+            if not precision.startswith("mixed_split") and r > 1:
                 continue
             api.set_tuning("symmetric", precision, lo, hi, 256, R=0)
             api.set_tuning("force", precision, lo, hi, b, r, bps)

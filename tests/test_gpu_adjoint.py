@@ -66,6 +66,34 @@ def test_loss_and_gradient_match_oracle(nb, orc, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_mid_size_gradient_matches_oracle_symmetric_kernels(nb, orc, precision):
+    """N = 512 over 300 steps with the symmetric force and VJP kernels forced
+    on (by default they start at n = 1500-2000 and 2500): loss and gradients
+    against the oracle's discrete adjoint, as in the small case above."""
+    x0, v0, target, phys = small_problem(n=512, seed=8)
+    nsteps, every = 300, 64
+    try:
+        nb.set_tuning("symmetric", precision, 0, 1 << 40, 128, R=1)
+        nb.set_tuning("symmetric_vjp", "fp64", 0, 1 << 40, 128, R=1)
+        assert nb.plan_info("force", precision, 512)["symmetric"] == 1
+        assert nb.plan_info("vjp", precision, 512)["symmetric"] == 1
+        loss, gx, gv, gw = gpu_grad(nb, x0, v0, target, phys, nsteps, every, precision=precision)
+    finally:
+        nb.set_tuning("force", "fp64", 0, 0, 0)
+    p = orc.make_params(**phys)
+    lr, gxr, gvr, gwr = orc.trajectory_grad(p, x0, v0, nsteps, target)
+    lu, gxu, gvu, gwu = orc.trajectory_grad(p, x0 * (1 + 2.0 ** -52), v0, nsteps, target)
+    print("N=512 loss gpu %.17g oracle %.17g" % (loss, lr))
+    assert abs(loss - lr) <= 1e-12 * abs(lr) + 10 * abs(lu - lr)
+    for g, r, u, name in ((gx, gxr, gxu, "x0"), (gv, gvr, gvu, "v0"), (gw, gwr, gwu, "omega")):
+        d = np.max(np.abs(g - r))
+        self_d = np.max(np.abs(u - r))
+        scale = np.max(np.abs(r))
+        print("%s: |gpu-oracle| %.3g  self %.3g  scale %.3g" % (name, d, self_d, scale))
+        assert d <= 10 * self_d + 1e-11 * scale, name
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
 @pytest.mark.parametrize("n", [100, 3100])
 def test_gradient_independent_of_checkpoint_interval(nb, precision, n):
     """Bitwise the same loss and gradients for every checkpoint interval: the

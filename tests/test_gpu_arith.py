@@ -16,9 +16,11 @@ pytestmark = pytest.mark.gpu
 #   df64: double-float r^2 and residual, about 2^-44 plus the final sum;
 #   sqrtdiv and two Newton steps: FP64 rounding (a few ulp);
 #   one Newton step squares the seed error (1.5 e^2, times 3 for the cube);
-#   the bare seed: 3 x 2^-22; mixed: FP32 rounding of d and the corrected bulk.
+#   the bare seed: 3 x 2^-22; mixed: FP32 rounding of d and the corrected bulk;
+#   mixed_split_rsq: the bare seed cubed in FP32 (3 x 2^-22.9 = 3.7e-7) plus
+#   the FP32 rounding of d, r^2 and the cube.
 BOUND = {"fp64": 4e-13, "df64": 2e-13, "sqrtdiv": 2e-15, "rsq_nr2": 2e-15, "rsq_nr1": 1e-12,
-         "rsq": 1e-6, "mixed": 1e-6, "mixed_split": 1e-6}
+         "rsq": 1e-6, "mixed": 1e-6, "mixed_split": 1e-6, "mixed_split_rsq": 7e-7}
 
 
 @pytest.fixture(scope="module")
@@ -102,7 +104,7 @@ def test_rinv3_softening_and_zero(nb):
     z = np.zeros((3, 4))
     for prec in ("fp64", "sqrtdiv", "rsq", "rsq_nr1", "rsq_nr2"):
         assert np.all(nb.rinv3_probe(prec, z).cpu().numpy() == 0.0), prec
-    for prec in ("df64", "mixed", "mixed_split"):  # clamped seed, finite: the pair term is d * s = 0
+    for prec in ("df64", "mixed", "mixed_split", "mixed_split_rsq"):  # clamped seed, finite: d * s = 0
         assert np.all(np.isfinite(nb.rinv3_probe(prec, z).cpu().numpy())), prec
 
 

@@ -20,7 +20,7 @@ from paper_2106_11143_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-GATE = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6}
+GATE = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6, "mixed_split_rsq": 1e-6}
 ALL = list(GATE)
 
 
@@ -104,14 +104,15 @@ def test_translation_invariance(nb, orc, precision):
     grid multiples, so shifted positions and all their differences are exact
     in FP64: the modes that form the displacement in FP64 (fp64, df64, mixed)
     see bitwise the same displacements and must give bitwise the same forces;
-    the split mode, which works from FP32 (hi, lo) positions, stays within its
-    gate."""
+    the split modes, which work from FP32 (hi, lo) positions, stay within
+    their gate."""
     g = 2.0 ** -40
     for n in (3000, 20000):
         pos, _ = W.random_cloud(n, seed=600 + n)
         pos = np.round(pos / g) * g
         a = coulomb_acc(nb, pos, precision)
-        if precision == "mixed_split":
+        split = precision.startswith("mixed_split")
+        if split:
             idx = np.random.default_rng(n).integers(0, n, 16)
             p = orc.make_params(**W.phys())
             S = np.array([orc.coulomb(p, *pos, i0=int(i), i1=int(i) + 1, want_absf=True)[4][0] for i in idx])
@@ -120,7 +121,7 @@ def test_translation_invariance(nb, orc, precision):
             moved = pos + sh
             assert np.array_equal(moved - sh, pos)  # exact
             b = coulomb_acc(nb, moved, precision)
-            if precision == "mixed_split":
+            if split:
                 d = np.sqrt(np.sum((a[:, idx] - b[:, idx]) ** 2, axis=0))
                 assert np.all(d <= GATE[precision] * S), (n, shift, np.max(d / S))
             else:

@@ -79,8 +79,11 @@ def test_ladder_speed_runs_every_method_one_sided(nb):
 def test_step_rate_sweep_runs(nb):
     """The step-rate sweep (one call with and without step windows, one call
     per step, caller graph replays) on two small sizes."""
-    from paper_2106_11143_gb300 import sweep
-    rows = sweep.sweep(sizes=(10, 1000), precisions=["fp64", "mixed_split"])
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    rows = bench.step_sweep(sizes=(10, 1000), precisions=["fp64", "mixed_split"])
     assert len(rows) == 4
     for r in rows:
         for k in ("ms_per_step", "plain_ms_per_step", "per_call_ms_per_step", "graph_ms_per_step"):

@@ -18,8 +18,8 @@ import floors
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6}
-ALL = ["fp64", "df64", "mixed", "mixed_split"]
+TOL = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6, "mixed_split_rsq": 1e-6}
+ALL = ["fp64", "df64", "mixed", "mixed_split", "mixed_split_rsq"]
 
 
 @pytest.fixture(scope="module")

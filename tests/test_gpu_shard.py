@@ -16,7 +16,7 @@ from paper_2106_11143_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6}
+TOL = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-6, "mixed_split_rsq": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -31,13 +31,13 @@ def nb():
 @pytest.fixture
 def one_sided(nb):
     """The symmetric kernel off (tuning kind 4, R = 0) for the duration."""
-    for prec in ("fp64", "df64", "mixed", "mixed_split"):
+    for prec in ("fp64", "df64", "mixed", "mixed_split", "mixed_split_rsq"):
         nb.set_tuning("symmetric", prec, 0, 1 << 40, 128, R=0)
     yield
     nb.set_tuning("force", "fp64", 0, 0, 0)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "df64", "mixed", "mixed_split"])
+@pytest.mark.parametrize("precision", ["fp64", "df64", "mixed", "mixed_split", "mixed_split_rsq"])
 def test_forces_range_pieces_equal_full_call(nb, orc, one_sided, precision):
     n = 3001
     rng = np.random.default_rng(5)

@@ -15,7 +15,7 @@ from paper_2106_11143_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["fp64", "df64", "mixed", "mixed_split", "sqrtdiv", "rsq", "rsq_nr1", "rsq_nr2"]
+MODES = ["fp64", "df64", "mixed", "mixed_split", "sqrtdiv", "rsq", "rsq_nr1", "rsq_nr2", "mixed_split_rsq"]
 
 
 @pytest.fixture(scope="module")
