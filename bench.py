@@ -47,7 +47,7 @@ ACCURACY_GATE = {"fp64": 1e-12, "df64": 1e-12, "mixed": 1e-6, "mixed_split": 1e-
 PATHS = ("fp64", "df64", "mixed", "mixed_split", "mixed_split_rsq")
 PROFILES = os.path.join(ROOT, "profiles")
 # Kernel sources a recorded DRAM-traffic figure is valid for.
-KERNEL_SOURCES = ("nb_sym.cu", "nb_pair.cu", "nb_common.cuh", "nb_pairterm.cuh")
+KERNEL_SOURCES = ("nb_sym.cu", "nb_symsched.cuh", "nb_pair.cu", "nb_common.cuh", "nb_pairterm.cuh")
 L2_FLUSH_BYTES = 256 << 20
 
 

@@ -79,11 +79,15 @@ __device__ __forceinline__ bool epi_sums(const double *__restrict__ part, int n_
 
 // Eight threads per ion unless tuning kind 8 says one (R = 0) for this n:
 // measured on GB300 the eight-thread form was faster at every n up to 1e5
-// (17-32 % of a step at n = 2500-6000; 148 against 170 us at 1e5).
-static bool epi_eight(int64_t n) {
+// with many partial slots (17-32 % of a step at n = 2500-6000; 148 against
+// 170 us at 1e5 with 196 slots).  With fewer than eight slots (the in-place
+// symmetric kernels leave one) the other seven lanes would have nothing to
+// load, so one thread per ion does it.  Both forms add the slots in the same
+// order, so the choice never changes a result.
+static bool epi_eight(int64_t n, int n_jc) {
   int tb = 0, tr = 0, tbps = 0;
   if (tuning_lookup(8, 0, n, &tb, &tr, &tbps)) return tr == 1;
-  return true;
+  return n_jc >= 8;
 }
 static int epi_blocks(int64_t n, bool eight) { return blocks_for(eight ? 8 * n : n, EPI_THREADS); }
 
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(EPI_THREADS)
 
 cudaError_t launch_epi_forces(const Phys &p, const StateView &s, const double *part, int n_jc,
                               int flags, double t, unsigned *err, cudaStream_t st) {
-  const bool eight = epi_eight(s.n);
+  const bool eight = epi_eight(s.n, n_jc);
   if (eight)
     k_epi_forces8<<<epi_blocks(s.n, true), EPI_THREADS, 0, st>>>(p, s, part, n_jc, flags, t, err);
   else
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(EPI_THREADS)
 cudaError_t launch_epi_vjp(const Phys &p, const StateView &s, const double *part, int n_jc,
                            const double *lx, const double *ly, const double *lz, double *gx,
                            double *gy, double *gz, int flags, double t, cudaStream_t st) {
-  if (epi_eight(s.n))
+  if (epi_eight(s.n, n_jc))
     k_epi_vjp8<<<epi_blocks(s.n, true), EPI_THREADS, 0, st>>>(p, s, part, n_jc, lx, ly, lz, gx, gy, gz, flags, t);
   else
     k_epi_vjp<<<epi_blocks(s.n, false), EPI_THREADS, 0, st>>>(p, s, part, n_jc, lx, ly, lz, gx, gy, gz, flags, t);
@@ -254,7 +258,7 @@ cudaError_t launch_epi_step(const Phys &p, const StateView &s, const double *cx,
                             const double *cz, const double *part, int n_jc, int64_t snew,
                             double *nx, double *ny, double *nz, unsigned *err, cudaStream_t st,
                             const int64_t *cin, int64_t *cout, int64_t cout_off) {
-  if (epi_eight(s.n))
+  if (epi_eight(s.n, n_jc))
     k_epi_step8<<<epi_blocks(s.n, true), EPI_THREADS, 0, st>>>(p, s, cx, cy, cz, part, n_jc, snew, cin, cout,
                                                                 cout_off, nx, ny, nz, err);
   else

@@ -60,11 +60,11 @@ __device__ __forceinline__ float shfl_next(float v, int lane) {
 // One 32x32 tile step for the FP64 pair arithmetic.  pp: this lane's P-ion;
 // qd: the Q-ion currently held (rotating); b: its accumulators
 // (rotating); a: the P-ion's accumulators.
-template <bool W>
+template <bool W, int CNT = 32>
 __device__ __forceinline__ void sym_step_fp64(const SD4 &pp, SD4 qd, double soft2, int lane,
                                               double a[3], double b[3]) {
 #pragma unroll 2
-  for (int r = 0; r < 32; ++r) {
+  for (int r = 0; r < CNT; ++r) {
     const double dx = pp.x - qd.x, dy = pp.y - qd.y, dz = pp.z - qd.z;
     const double s = rinv3_fp64(dx, dy, dz, soft2);
     const double sp = W ? s * qd.w : s;
@@ -88,13 +88,13 @@ __device__ __forceinline__ void sym_step_fp64(const SD4 &pp, SD4 qd, double soft
 // The same step with double-float pair arithmetic (see pair_df64).  The
 // weights w (charge, or 1 / 0 for real / padding ions) are FP64; a, b are
 // double-float (h, l) accumulators for this step.
-template <bool W>
+template <bool W, int CNT = 32>
 __device__ __forceinline__ void sym_step_df64(const SD4 &pp, SD4 qd, float s2h, float s2l, int lane,
                                               float ah[3], float al[3], float bh[3], float bl[3]) {
   float wph = 1.0f, wpl = 0.0f;
   if (W) split_f64(pp.w, wph, wpl);
 #pragma unroll 1
-  for (int r = 0; r < 32; ++r) {
+  for (int r = 0; r < CNT; ++r) {
     float dh[3], dl[3];
     split_f64(pp.x - qd.x, dh[0], dl[0]);
     split_f64(pp.y - qd.y, dh[1], dl[1]);
@@ -145,13 +145,13 @@ __device__ __forceinline__ double wpack(float w) { return __hiloint2double(0, __
 
 // Literal mixed step: FP64 displacement, FP32 bulk, FP32 partials for this
 // step (a: the P-ion, b: the rotating Q-ion).
-template <bool W>
+template <bool W, int CNT = 32>
 __device__ __forceinline__ void sym_step_mixed(const SD4 &pp, SD4 qd, float soft2f, int lane,
                                                float a[3], float b[3]) {
   const float wp = wf32(pp.w);
   float wq = wf32(qd.w);
 #pragma unroll 2
-  for (int r = 0; r < 32; ++r) {
+  for (int r = 0; r < CNT; ++r) {
     const float fx = f64_to_f32_rn(pp.x - qd.x);
     const float fy = f64_to_f32_rn(pp.y - qd.y);
     const float fz = f64_to_f32_rn(pp.z - qd.z);
@@ -197,12 +197,12 @@ __device__ __forceinline__ void split_eval(const float4 &ph, const float4 &pl, c
 // pair); only the Q accumulators rotate through shuffles.  qhi, qlo point at
 // this lane's entry of the duplicated tile, so entry r of the rotation is
 // qhi[r] (a compile-time offset once the loop is unrolled).
-template <bool W, bool SEED>
+template <bool W, bool SEED, int CNT = 32>
 __device__ __forceinline__ void sym_step_split(const float4 &ph, const float4 &pl, const float4 *qhi,
                                                const float4 *qlo, float soft2f, int lane, float a[3],
                                                float b[3]) {
 #pragma unroll
-  for (int r = 0; r < 32; ++r) {
+  for (int r = 0; r < CNT; ++r) {
     split_eval<W, SEED>(ph, pl, qhi[r], qlo[r], soft2f, a, b);
     b[0] = shfl_next(b[0], lane);
     b[1] = shfl_next(b[1], lane);
@@ -530,6 +530,218 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_s
                    [&](int c, int i) { return qsum(posQ, c, i); });
 }
 
+// 32-ion blocks (the mid-range n, where the items are too few to fill the
+// GPU with one warp each): RW warps share an item's 32 rotations, warp w
+// taking rotations [w C, (w + 1) C), C = 32 / RW, starting from the Q-tile
+// turned by w C.  Each warp's P and Q sums go to shared memory (pb, qb:
+// [RW][3][32] doubles each) and are added in warp order, so the result is
+// deterministic.  A diagonal item gives warp w the partners [w C, (w+1) C)
+// of every ion of the block.
+template <int MODE, bool QARR, int RW, bool INPLACE>
+__global__ void __launch_bounds__(32 * RW) k_pair_sym_rot(int64_t n, int nbk, const double *__restrict__ x,
+                                                           const double *__restrict__ y,
+                                                           const double *__restrict__ z,
+                                                           const double *__restrict__ q, PosF32 pf, double soft2,
+                                                           double *__restrict__ acc, int *__restrict__ sync,
+                                                           unsigned *err) {
+  constexpr int BI = 32, C = 32 / RW, NT = 32 * RW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SD4 *posP = reinterpret_cast<SD4 *>(smem_raw);
+  SD4 *posQ = posP + BI;
+  double *pb = reinterpret_cast<double *>(posQ + (split_like(MODE) ? 2 * BI : BI));  // [RW][3][32]
+  double *qb = pb + RW * 3 * 32;                                                      // [RW][3][32]
+  const SymItem it = sym_block_item(INPLACE, sync, nbk);
+  const int P = it.P, Q = it.Q;
+  const int64_t p0 = (int64_t)P * BI, q0 = (int64_t)Q * BI;
+  const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, r0 = w * C;
+  if (tid < BI) {
+    sym_stage<MODE, QARR>(posP, tid, BI, p0 + tid, n, x, y, z, q, pf, false);
+    if (P != Q) sym_stage<MODE, QARR>(posQ, tid, BI, q0 + tid, n, x, y, z, q, pf, true);
+  }
+  float s2h = 0.0f, s2l = 0.0f;
+  if (MODE == MODE_DF64) split_f64(soft2, s2h, s2l);
+  __syncthreads();
+  const float4 *fP = reinterpret_cast<const float4 *>(posP);
+  const float4 *fQ = reinterpret_cast<const float4 *>(posQ);
+  constexpr bool SEED = MODE == MODE_SPLIT_RSQ;
+  double a[3] = {0.0, 0.0, 0.0};
+  if (P == Q) {  // ion `lane` against the partners [r0, r0 + C) of the block
+    const int i = lane;
+    const SD4 pi = posP[i];
+    float af[3] = {0, 0, 0}, al[3] = {0, 0, 0};
+    for (int j = r0; j < min(r0 + C, np); ++j) {
+      if (MODE == MODE_FP64) {
+        const SD4 pj = posP[j];
+        const double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        double sv = rinv3_fp64(dx, dy, dz, soft2);
+        if (QARR) sv *= pj.w;
+        a[0] = fma(dx, sv, a[0]);
+        a[1] = fma(dy, sv, a[1]);
+        a[2] = fma(dz, sv, a[2]);
+      } else if (MODE == MODE_DF64) {
+        const SD4 pj = posP[j];
+        float dh[3], dl[3];
+        split_f64(pi.x - pj.x, dh[0], dl[0]);
+        split_f64(pi.y - pj.y, dh[1], dl[1]);
+        split_f64(pi.z - pj.z, dh[2], dl[2]);
+        float sh, sl;
+        df_rinv3(dh, dl, s2h, s2l, sh, sl);
+        if (QARR) {
+          float wh, wl;
+          split_f64(pj.w, wh, wl);
+          const float ph = sh * wh;
+          sl = fmaf(sh, wl, fmaf(sl, wh, fmaf(sh, wh, -ph)));
+          sh = ph;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float ph = dh[k] * sh;
+          const float pl = fmaf(dh[k], sl, fmaf(dl[k], sh, fmaf(dh[k], sh, -ph)));
+          float sv, tt;
+          two_sum_f(af[k], ph, sv, tt);
+          af[k] = sv;
+          al[k] += tt + pl;
+        }
+      } else {
+        float fx, fy, fz, wj;
+        if (MODE == MODE_MIXED) {
+          const SD4 pj = posP[j];
+          fx = f64_to_f32_rn(pi.x - pj.x);
+          fy = f64_to_f32_rn(pi.y - pj.y);
+          fz = f64_to_f32_rn(pi.z - pj.z);
+          wj = wf32(pj.w);
+        } else {
+          const float4 ih = fP[i], il = fP[BI + i], jh = fP[j], jl = fP[BI + j];
+          fx = (ih.x - jh.x) + (il.x - jl.x);
+          fy = (ih.y - jh.y) + (il.y - jl.y);
+          fz = (ih.z - jh.z) + (il.z - jl.z);
+          wj = jh.w;
+        }
+        float sj = f32_rinv3<SEED>(fx, fy, fz, (float)soft2);
+        if (QARR) sj *= wj;
+        af[0] = fmaf(fx, sj, af[0]);
+        af[1] = fmaf(fy, sj, af[1]);
+        af[2] = fmaf(fz, sj, af[2]);
+      }
+    }
+    if (MODE != MODE_FP64)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) a[k] = f32_to_f64(af[k]) + f32_to_f64(al[k]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pb[(w * 3 + c) * 32 + lane] = a[c];
+    __syncthreads();
+    sym_output<NT>(INPLACE, it, n, p0, np, q0, nq, acc, sync, err,
+                   [&](int c, int i) {
+                     double v = 0.0;
+#pragma unroll
+                     for (int u = 0; u < RW; ++u) v += pb[(u * 3 + c) * 32 + i];
+                     return v;
+                   },
+                   [&](int c, int i) { return 0.0; });
+    return;
+  }
+  const bool weighted = QARR || np < BI || nq < BI;
+  double b[3] = {0.0, 0.0, 0.0};
+  if (MODE == MODE_FP64) {
+    const SD4 pp = posP[lane], qd = posQ[(lane + r0) & 31];
+    if (weighted)
+      sym_step_fp64<true, C>(pp, qd, soft2, lane, a, b);
+    else
+      sym_step_fp64<false, C>(pp, qd, soft2, lane, a, b);
+  } else if (MODE == MODE_DF64) {
+    const SD4 pp = posP[lane], qd = posQ[(lane + r0) & 31];
+    float ah[3] = {0, 0, 0}, al[3] = {0, 0, 0}, bh[3] = {0, 0, 0}, bl[3] = {0, 0, 0};
+    if (weighted)
+      sym_step_df64<true, C>(pp, qd, s2h, s2l, lane, ah, al, bh, bl);
+    else
+      sym_step_df64<false, C>(pp, qd, s2h, s2l, lane, ah, al, bh, bl);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a[c] = f32_to_f64(ah[c]) + f32_to_f64(al[c]);
+      b[c] = f32_to_f64(bh[c]) + f32_to_f64(bl[c]);
+    }
+  } else {
+    float af[3] = {0, 0, 0}, bf[3] = {0, 0, 0};
+    if (MODE == MODE_MIXED) {
+      const SD4 pp = posP[lane], qd = posQ[(lane + r0) & 31];
+      if (weighted)
+        sym_step_mixed<true, C>(pp, qd, (float)soft2, lane, af, bf);
+      else
+        sym_step_mixed<false, C>(pp, qd, (float)soft2, lane, af, bf);
+    } else {
+      // the doubled Q-tile: entry (lane + r0 + r) at a fixed offset for every r < C
+      if (weighted)
+        sym_step_split<true, SEED, C>(fP[lane], fP[BI + lane], fQ + lane + r0, fQ + 2 * BI + lane + r0,
+                                      (float)soft2, lane, af, bf);
+      else
+        sym_step_split<false, SEED, C>(fP[lane], fP[BI + lane], fQ + lane + r0, fQ + 2 * BI + lane + r0,
+                                       (float)soft2, lane, af, bf);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a[c] = f32_to_f64(af[c]);
+      b[c] = f32_to_f64(bf[c]);
+    }
+  }
+  // after C rotations lane l holds the sums of Q-ion (l + r0 + C) mod 32
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    pb[(w * 3 + c) * 32 + lane] = a[c];
+    qb[(w * 3 + c) * 32 + ((lane + r0 + C) & 31)] = b[c];
+  }
+  __syncthreads();
+  sym_output<NT>(INPLACE, it, n, p0, np, q0, nq, acc, sync, err,
+                 [&](int c, int i) {
+                   double v = 0.0;
+#pragma unroll
+                   for (int u = 0; u < RW; ++u) v += pb[(u * 3 + c) * 32 + i];
+                   return v;
+                 },
+                 [&](int c, int i) {
+                   double v = 0.0;
+#pragma unroll
+                   for (int u = 0; u < RW; ++u) v += qb[(u * 3 + c) * 32 + i];
+                   return v;
+                 });
+}
+
+// Warps per 32-ion item (rotation split), the fastest measured on GB300 for
+// n = 1000-2000 step by step: against one warp per item two were 10 % faster
+// for mixed at n = 1000, 4.5 % for fp64 at n = 1500 and 7 % for df64 at
+// n = 2000 (2 % slower for mixed at n = 1500); four were slower than two
+// everywhere.
+constexpr int SYM_ROT_WARPS = 2;
+
+static size_t sym_rot_smem_bytes(int mode) {
+  return (size_t)32 * ((split_like(mode) ? 3 : 2) * sizeof(SD4)) + 2 * (size_t)SYM_ROT_WARPS * 3 * 32 * sizeof(double);
+}
+
+template <int MODE>
+static cudaError_t launch_sym_rot(int64_t n, int nbk, const double *x, const double *y, const double *z,
+                                  const double *q, const PosF32 &pf, double soft2, double *part, int *sync,
+                                  unsigned *err, bool inplace, cudaStream_t st) {
+  constexpr int RW = SYM_ROT_WARPS;
+  if (inplace) {
+    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * sym_sync_ints(nbk), st);
+    if (e != cudaSuccess) return e;
+  }
+  const int items = nbk * (nbk + 1) / 2;
+  const size_t smem = sym_rot_smem_bytes(MODE);
+  if (q && inplace)
+    k_pair_sym_rot<MODE, true, RW, true><<<items, 32 * RW, smem, st>>>(n, nbk, x, y, z, q, pf, soft2, part, sync, err);
+  else if (q)
+    k_pair_sym_rot<MODE, true, RW, false><<<items, 32 * RW, smem, st>>>(n, nbk, x, y, z, q, pf, soft2, part, sync,
+                                                                        err);
+  else if (inplace)
+    k_pair_sym_rot<MODE, false, RW, true><<<items, 32 * RW, smem, st>>>(n, nbk, x, y, z, q, pf, soft2, part, sync,
+                                                                        err);
+  else
+    k_pair_sym_rot<MODE, false, RW, false><<<items, 32 * RW, smem, st>>>(n, nbk, x, y, z, q, pf, soft2, part, sync,
+                                                                         err);
+  return cudaGetLastError();
+}
+
 size_t sym_smem_bytes(int G, int mode) {
   return (size_t)32 * G * ((split_like(mode) ? 3 : 2) * sizeof(SD4) + 3 * sizeof(double));
 }
@@ -585,7 +797,18 @@ cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x
                             double *part, int *sync, unsigned *err, bool inplace, cudaStream_t st) {
   if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
   constexpr int S = SYM_THREADS_SMALL, L = SYM_THREADS;
-  if (G <= 2) {  // 32- and 64-ion blocks at small n: one warp per 32-ion tile
+  if (G == 1) {  // 32-ion blocks: several warps share an item's rotations
+    switch (mode) {
+      case MODE_FP64: return launch_sym_rot<MODE_FP64>(n, nbk, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
+      case MODE_DF64: return launch_sym_rot<MODE_DF64>(n, nbk, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
+      case MODE_MIXED: return launch_sym_rot<MODE_MIXED>(n, nbk, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
+      case MODE_SPLIT: return launch_sym_rot<MODE_SPLIT>(n, nbk, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
+      case MODE_SPLIT_RSQ:
+        return launch_sym_rot<MODE_SPLIT_RSQ>(n, nbk, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (G <= 2) {  // 64-ion blocks at small n: one warp per 32-ion tile
     switch (mode) {
       case MODE_FP64:
         return G == 1 ? launch_sym_m<MODE_FP64, false, 32>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
