@@ -340,6 +340,7 @@ def recorded_traffic(precision, n):
     want = kernel_source_sha()
     for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
         for line in open(path):
+            line = line.strip()
             if not line.startswith("traffic: "):
                 continue
             kv = dict(t.split("=", 1) for t in line.split()[1:])

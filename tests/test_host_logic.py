@@ -299,5 +299,8 @@ def test_bench_roofline_and_kernel_label(api):
             r = bench.roofline(api, prec, n, 1.0, peaks, None)
             assert r["kernel"].startswith("k_pair_sym" if sym else "k_pair_force"), (prec, n)
             assert r["evaluations_per_launch"] == (n * n if not sym else r["evaluations_per_launch"])
-    # a traffic figure recorded for other kernel sources is not reported
+    # a traffic figure recorded for other kernel sources is not reported; the one in
+    # profiles/ for the headline case is, while the kernel sources match its hash
     assert bench.recorded_traffic("mixed_split", 12345)[0] is None
+    t, src = bench.recorded_traffic("mixed_split", 100000)
+    assert t is not None and 1e6 < t < 1e8 and src.endswith(".md"), (t, src)
