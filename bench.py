@@ -64,8 +64,9 @@ def parse():
                          "parser takes --n for an abbreviation of its own options")
     ap.add_argument("--no-paths", action="store_true", help="skip the secondary precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--workload", default="large", choices=["large", "kz"],
-                    help="large: the N=1e5 headline; kz: the 512-instance ensemble (extra line)")
+    ap.add_argument("--workload", default="large", choices=["large", "kz", "kz_sweep"],
+                    help="large: the N=1e5 headline; kz: the 512-instance ensemble (extra line); "
+                         "kz_sweep: the same ensemble with a quench rate per instance")
     ap.add_argument("--profile-forces", action="store_true",
                     help="profiling case: two nb_forces calls per precision at --n, no timing")
     ap.add_argument("--one-sided", action="store_true",
@@ -520,19 +521,26 @@ def kz_roofline(nb, prec, pairs, steps, ms, clk):
 def main_kz(args):
     """Extra line: the Kibble-Zurek ensemble (512 instances, N_k uniform in
     32..4096, FP64) advanced by K steps in ONE persistent launch of
-    nb_step_batched; value = sum_k N_k^2 x K / device time."""
+    nb_step_batched (kz_sweep: nb_step_batched_each, one quench rate per
+    instance); value = sum_k N_k^2 x K / device time."""
     import torch
     torch.cuda.set_device(0)
     import paper_2106_11143_gb300 as nb
     from paper_2106_11143_gb300 import workloads as W
-    w = W.kz_ensemble()
+    each = args.workload == "kz_sweep"
+    w = W.kz_quench_sweep() if each else W.kz_ensemble()
     off = w["offsets"]
     pairs = float(np.sum(np.diff(off).astype(np.float64) ** 2))
     prec = args.precision if args.precision in ("fp64", "df64") else "fp64"
-    par = nb.Params.from_phys(w["phys"], precision=prec)
+    if each:
+        par = [nb.Params.from_phys(ph, precision=prec) for ph in w["phys"]]
+        run = lambda n: nb.step_batched_each(par, sysm, off, n)
+    else:
+        par = nb.Params.from_phys(w["phys"], precision=prec)
+        run = lambda n: nb.step_batched(par, sysm, off, n)
     sysm = nb.System(w["pos"], w["vel"])
     nb.init_batched(par, sysm, off)
-    nb.step_batched(par, sysm, off, args.warmup)
+    run(args.warmup)
     nb.sync_status()
     lib = nb.lib()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -544,7 +552,7 @@ def main_kz(args):
     torch.cuda.synchronize()
     clocks.start()
     a.record(st)
-    nb.step_batched(par, sysm, off, args.steps)
+    run(args.steps)
     b.record(st)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -815,7 +823,7 @@ if __name__ == "__main__":
         profile_vjp(a)
     elif a.profile_forces:
         profile_forces(a)
-    elif a.workload == "kz" and a.impl == "ours":
+    elif a.workload in ("kz", "kz_sweep") and a.impl == "ours":
         main_kz(a)
     elif a.impl == "reference":
         main_reference(a)

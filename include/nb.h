@@ -291,6 +291,27 @@ nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys,
 nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t *offsets,
                           nb_system *packed, int64_t nsteps, void *stream);
 
+/* The ensemble with parameters of its own for every instance (a7; e.g. a
+ * sweep of quench rates, trap ramps or cooling, one realisation per entry):
+ * as nb_step_batched, except that instance k runs with per_inst[k] (HOST
+ * array of n_inst nb_params) and draws its noise with instance word
+ * per_inst[k].instance itself, so it reproduces a standalone nb_step run of
+ * that instance with per_inst[k].  Every entry must pass nb_step's checks
+ * and all entries must have the same precision (NB_FP64 or NB_DF64;
+ * NB_EINVAL otherwise).  The step counter (packed->step) is shared: instance
+ * k's time is per_inst[k].t0 + step * per_inst[k].dt.
+ * The library keeps a device copy of the table per (device, stream) and
+ * copies it again only when the contents differ from the stream's previous
+ * call.  That copy waits for the stream's earlier work (which may still
+ * read the old table), so such a call can block the host; the call returns
+ * once the host array has been read, so the caller may reuse it at once.  A graph capture records the launch, which reads the
+ * stream's table when replayed: capture only after an uncaptured call with
+ * the same per_inst (a capture with other contents fails with NB_EINVAL,
+ * and a later uncaptured call with other contents changes what earlier
+ * captures replay).  Freed by nb_release.                                  */
+nb_status nb_step_batched_each(const nb_params *per_inst, int32_t n_inst, const int64_t *offsets,
+                               nb_system *packed, int64_t nsteps, void *stream);
+
 /* Host-only: the instance-to-block schedule nb_step_batched uses for n_bins
  * blocks.  order[n_inst] lists the instances grouped by block; block b runs
  * order[bin_start[b] .. bin_start[b+1]-1].  max_load / mean_load (nullable)

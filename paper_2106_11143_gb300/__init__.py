@@ -11,8 +11,8 @@ library without the built extension raises.
 from . import workloads  # noqa: F401  (pure numpy, no compute of the method)
 
 _API = ("Params", "System", "forces", "step", "energy", "forces_vjp", "sync_status",
-        "step_batched", "init_batched", "plan_batched", "set_tuning", "trajectory_loss", "TrajectoryLoss",
-        "lib", "NBError", "PRECISIONS", "release", "rinv3_probe", "rsqrt_seed_probe", "save_checkpoint",
+        "step_batched", "step_batched_each", "init_batched", "plan_batched", "set_tuning",
+        "trajectory_loss", "TrajectoryLoss", "lib", "NBError", "PRECISIONS", "release", "rinv3_probe", "rsqrt_seed_probe", "save_checkpoint",
         "load_checkpoint", "plan_info", "pipe_probe", "sym_schedule", "forces_range", "step_range_drift",
         "step_range_kick")
 

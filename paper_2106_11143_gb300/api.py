@@ -77,6 +77,7 @@ def lib():
         I64P = C.POINTER(C.c_int64)
         U16P = C.POINTER(C.c_uint16)
         L.nb_step_batched.argtypes = [P, C.c_int32, I64P, S, C.c_int64, V]
+        L.nb_step_batched_each.argtypes = [P, C.c_int32, I64P, S, C.c_int64, V]
         L.nb_plan_batched.argtypes = [C.c_int32, I64P, C.c_int32, U16P, U16P, _dp, _dp]
         L.nb_set_tuning.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int32,
                                     C.c_int32, C.c_int32]
@@ -98,7 +99,7 @@ def lib():
         I32P = C.POINTER(C.c_int32)
         L.nb_sym_schedule.argtypes = [C.c_int32, I32P, I32P, I32P]
         for f in ("nb_forces", "nb_step", "nb_energy", "nb_forces_vjp", "nb_sync_status",
-                  "nb_release", "nb_timing_enable", "nb_timing_read", "nb_step_batched",
+                  "nb_release", "nb_timing_enable", "nb_timing_read", "nb_step_batched", "nb_step_batched_each",
                   "nb_plan_batched", "nb_set_tuning", "nb_energy_noalloc", "nb_traj_forward",
                   "nb_traj_backward", "nb_rinv3_probe", "nb_rsqrt_seed_probe", "nb_plan_info",
                   "nb_pipe_probe", "nb_sym_schedule", "nb_forces_range", "nb_step_range_drift",
@@ -399,13 +400,30 @@ def step_batched(params, system, offsets, nsteps, stream=None):
     system.step = s.step
 
 
+def step_batched_each(per_inst, system, offsets, nsteps, stream=None):
+    """nb_step_batched_each: as step_batched, with instance k run under
+    per_inst[k] (a sequence of Params, one per instance, same precision)."""
+    off, offp = _offsets(offsets)
+    n_inst = len(off) - 1
+    if len(per_inst) != n_inst:
+        raise ValueError("per_inst has %d entries for %d instances" % (len(per_inst), n_inst))
+    tab = (NbParams * max(n_inst, 1))(*[p.to_c() for p in per_inst])
+    s = system.to_c()
+    _check(lib().nb_step_batched_each(tab, n_inst, offp, C.byref(s), int(nsteps), _stream(stream)),
+           "nb_step_batched_each")
+    system.step = s.step
+
+
 def init_batched(params, system, offsets, stream=None):
     """Set the Verlet-state acceleration of every instance of a packed ensemble
-    (nb_forces with NB_ACC_TOTAL on each instance's own ions)."""
+    (nb_forces with NB_ACC_TOTAL on each instance's own ions); `params` is one
+    Params for all instances or a sequence of one per instance."""
     off = np.asarray(offsets, dtype=np.int64)
+    each = isinstance(params, (list, tuple))
     for k in range(len(off) - 1):
         if off[k + 1] > off[k]:
-            forces(params, system.view(int(off[k]), int(off[k + 1])), total=True, stream=stream)
+            forces(params[k] if each else params, system.view(int(off[k]), int(off[k + 1])), total=True,
+                   stream=stream)
 
 
 def plan_batched(offsets, n_bins):

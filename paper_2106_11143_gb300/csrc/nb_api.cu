@@ -67,6 +67,11 @@ struct Arena {
   cudaStream_t cap_st = nullptr;  // private stream the step windows are captured on
   std::vector<StepGraph> windows;  // at most STEP_WINDOW_CACHE
   uint64_t uses = 0;
+  // nb_step_batched_each: the device table of per-instance parameters
+  // (BATCH_LIMIT_INST entries) and the nb_params it was last filled from
+  Phys *ptab = nullptr;
+  std::vector<nb_params> ptab_src;
+  std::vector<Phys> ptab_stage;
 };
 
 int64_t *step_counters(Arena *a) { return reinterpret_cast<int64_t *>(reinterpret_cast<char *>(a->err) + 64); }
@@ -753,16 +758,18 @@ nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys, const dou
   return NB_OK;
 }
 
-nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t *offsets,
-                          nb_system *packed, int64_t nsteps, void *stream) {
-  NvtxRange range_("nb_step_batched");
-  NB_TRY(check_params(params));
+namespace {
+
+// Checks shared by both ensemble calls: the packed system, the instance
+// offsets and the step count; `p` is one instance's parameters.
+nb_status check_batched(const nb_params *p, int32_t n_inst, const int64_t *offsets,
+                        const nb_system *packed, int64_t nsteps) {
   NB_TRY(check_system(packed, true, true));
-  if (params->precision != NB_FP64 && params->precision != NB_DF64)
+  if (p->precision != NB_FP64 && p->precision != NB_DF64)
     return fail(NB_ENOTSUP, "the ensemble kernel supports NB_FP64 and NB_DF64");
   if (packed->m) return fail(NB_ENOTSUP, "the ensemble kernel has one species (m must be NULL)");
   if (nsteps < 0) return fail(NB_EINVAL, "nsteps must be >= 0");
-  if (!(params->dt > 0.0)) return fail(NB_EINVAL, "dt must be > 0");
+  if (!(p->dt > 0.0)) return fail(NB_EINVAL, "dt must be > 0");
   if (n_inst < 0 || n_inst > BATCH_LIMIT_INST)
     return fail(NB_EINVAL, "n_inst must be in [0, %d]", BATCH_LIMIT_INST);
   if (n_inst > 0 && !offsets) return fail(NB_EINVAL, "offsets is NULL");
@@ -777,6 +784,30 @@ nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t
                     (long long)m, BATCH_LIMIT_N);
     }
   }
+  return NB_OK;
+}
+
+// One persistent launch of the ensemble kernel; ptab = nullptr shares `p`.
+nb_status run_batched(const nb_params *p, const Phys *ptab, int32_t n_inst, const int64_t *offsets,
+                      nb_system *packed, int64_t nsteps, Arena *a, cudaStream_t st) {
+  int threads = 512, R = 1, bps = 1;  // fastest on GB300 with the half-pair phase
+  tuning_lookup(3, p->precision, packed->n, &threads, &R, &bps);
+  const int n_bins = std::min(n_inst, device_sm_count());
+  // a tuning entry with R = 0 keeps the one-sided force phase
+  NB_CUDA_TRY(launch_batched(to_phys(p), ptab, to_view(packed), n_inst, offsets, n_bins, threads, R != 0,
+                             packed->step, nsteps, a->err, st));
+  count_launches(1);
+  packed->step += nsteps;
+  return NB_OK;
+}
+
+}  // namespace
+
+nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t *offsets,
+                          nb_system *packed, int64_t nsteps, void *stream) {
+  NvtxRange range_("nb_step_batched");
+  NB_TRY(check_params(params));
+  NB_TRY(check_batched(params, n_inst, offsets, packed, nsteps));
   if (n_inst == 0 || packed->n == 0 || nsteps == 0) {
     packed->step += nsteps;
     return NB_OK;
@@ -784,15 +815,57 @@ nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t
   cudaStream_t st = (cudaStream_t)stream;
   Arena *a = nullptr;
   NB_TRY(get_arena(st, 256, &a));
-  int threads = 512, R = 1, bps = 1;  // fastest on GB300 with the half-pair phase
-  tuning_lookup(3, params->precision, packed->n, &threads, &R, &bps);
-  const int n_bins = std::min(n_inst, device_sm_count());
-  // a tuning entry with R = 0 keeps the one-sided force phase
-  NB_CUDA_TRY(launch_batched(to_phys(params), to_view(packed), n_inst, offsets, n_bins, threads, R != 0,
-                             packed->step, nsteps, a->err, st));
-  count_launches(1);
-  packed->step += nsteps;
-  return NB_OK;
+  return run_batched(params, nullptr, n_inst, offsets, packed, nsteps, a, st);
+}
+
+nb_status nb_step_batched_each(const nb_params *per_inst, int32_t n_inst, const int64_t *offsets,
+                               nb_system *packed, int64_t nsteps, void *stream) {
+  NvtxRange range_("nb_step_batched_each");
+  if (n_inst < 0 || n_inst > BATCH_LIMIT_INST)
+    return fail(NB_EINVAL, "n_inst must be in [0, %d]", BATCH_LIMIT_INST);
+  if (n_inst > 0 && !per_inst) return fail(NB_EINVAL, "per_inst is NULL");
+  for (int k = 0; k < n_inst; ++k) {
+    const nb_status rc = check_params(&per_inst[k]);
+    if (rc != NB_OK) return fail(rc, "per_inst[%d]: %s", k, g_last_error.c_str());
+    if (per_inst[k].precision != per_inst[0].precision)
+      return fail(NB_EINVAL, "per_inst[%d].precision differs from per_inst[0]'s", k);
+    if (!(per_inst[k].dt > 0.0)) return fail(NB_EINVAL, "per_inst[%d].dt must be > 0", k);
+  }
+  nb_params shape{};  // stands in for the instances' common fields when n_inst == 0
+  shape.precision = n_inst > 0 ? per_inst[0].precision : NB_FP64;
+  shape.dt = 1.0;
+  NB_TRY(check_batched(&shape, n_inst, offsets, packed, nsteps));
+  if (n_inst == 0 || packed->n == 0 || nsteps == 0) {
+    packed->step += nsteps;
+    return NB_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena *a = nullptr;
+  NB_TRY(get_arena(st, 256, &a));
+  const bool same = a->ptab && a->ptab_src.size() == (size_t)n_inst &&
+                    std::memcmp(a->ptab_src.data(), per_inst, n_inst * sizeof(nb_params)) == 0;
+  if (!same) {
+    // a graph capture records the launch, which reads the table at replay
+    // time; a host-to-device copy of new contents is not captured
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    NB_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(NB_EINVAL, "per-instance parameters differ from the stream's last uncaptured call; "
+                             "make one uncaptured call with them before capturing");
+    if (!a->ptab && cudaMalloc(&a->ptab, BATCH_LIMIT_INST * sizeof(Phys)) != cudaSuccess) {
+      cudaGetLastError();
+      a->ptab = nullptr;
+      return fail(NB_ENOMEM, "cudaMalloc(per-instance parameter table) failed");
+    }
+    a->ptab_stage.resize(n_inst);
+    for (int k = 0; k < n_inst; ++k) a->ptab_stage[k] = to_phys(&per_inst[k]);
+    // pageable source: the call returns once the bytes are staged, after the
+    // stream's earlier work (which may read the old table) has finished
+    NB_CUDA_TRY(cudaMemcpyAsync(a->ptab, a->ptab_stage.data(), n_inst * sizeof(Phys),
+                                cudaMemcpyHostToDevice, st));
+    a->ptab_src.assign(per_inst, per_inst + n_inst);
+  }
+  return run_batched(&per_inst[0], a->ptab, n_inst, offsets, packed, nsteps, a, st);
 }
 
 nb_status nb_plan_batched(int32_t n_inst, const int64_t *offsets, int32_t n_bins,
@@ -1097,6 +1170,7 @@ nb_status nb_release(void) {
       if (g.exec && cudaGraphExecDestroy(g.exec) != cudaSuccess) rc = NB_ECUDA;
     if (kv.second.cap_st && cudaStreamDestroy(kv.second.cap_st) != cudaSuccess) rc = NB_ECUDA;
     if (kv.second.buf && cudaFree(kv.second.buf) != cudaSuccess) rc = NB_ECUDA;
+    if (kv.second.ptab && cudaFree(kv.second.ptab) != cudaSuccess) rc = NB_ECUDA;
     if (kv.second.err && cudaFree(kv.second.err) != cudaSuccess) rc = NB_ECUDA;
   }
   g_arenas.clear();

@@ -39,7 +39,8 @@ constexpr int BATCH_MAX_INST = 1024;
 constexpr int BATCH_MAX_BINS = 1024;
 static_assert(BATCH_MAX_INST == BATCH_LIMIT_INST, "schedule arrays sized for the validated instance limit");
 // ions per instance (BATCH_LIMIT_N, checked on the host): 32 B each in shared memory
-static_assert(BATCH_LIMIT_N * sizeof(BD4) <= 227 * 1024, "an instance's positions fit one block's shared memory");
+static_assert(sizeof(Phys) % 16 == 0 && sizeof(Phys) + BATCH_LIMIT_N * sizeof(BD4) <= 227 * 1024,
+              "an instance's parameters and positions fit one block's shared memory");
 
 struct BatchSched {
   int n_inst;
@@ -104,6 +105,8 @@ __device__ __forceinline__ void bpair_df64(double xi, double yi, double zi, cons
 // and rotates tile b's accumulators by shuffle.  The order of every sum is
 // fixed by the schedule, not by the block size.
 constexpr int BATCH_SYM_N = 4096;
+static_assert(sizeof(Phys) + BATCH_SYM_N * (sizeof(BD4) + 3 * sizeof(double)) <= 227 * 1024,
+              "the half-pair phase's accumulators fit beside the positions");
 
 __device__ __forceinline__ double bshfl_next(double v, int lane) {
   return __shfl_sync(0xffffffffu, v, (lane + 1) & 31);
@@ -268,28 +271,32 @@ __device__ void bsym_forces(const BD4 *sp, double *acc, int npad, int n, int np3
 }
 
 template <bool QARR, bool DF, bool SYM>
-__global__ void __launch_bounds__(512, 1) k_batched(Phys p, StateView s,
+__global__ void __launch_bounds__(512, 1) k_batched(Phys pall, const Phys *__restrict__ ptab, StateView s,
                                                   const __grid_constant__ BatchSched sch,
                                                   int64_t step0, int64_t nsteps, int npad, unsigned *err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  BD4 *sp = reinterpret_cast<BD4 *>(smem_raw);
+  Phys &pinst = *reinterpret_cast<Phys *>(smem_raw);  // the running instance's parameters
+  BD4 *sp = reinterpret_cast<BD4 *>(smem_raw + sizeof(Phys));
   double *acc = reinterpret_cast<double *>(sp + npad);  // SYM: [3][npad]
   const int T = blockDim.x;
   const int tid = threadIdx.x;
-  const double dt = p.dt, hdt2 = 0.5 * dt * dt;
-  const double inv = 1.0 / (1.0 + p.gamma * dt / (2.0 * p.mass)), g = p.gamma / p.mass;
-  const double sig = p.noise_T > 0.0 ? sqrt(2.0 * p.gamma * KB * p.noise_T * dt) / p.mass : 0.0;
-  const double pref_u = p.k_coulomb * p.charge * p.charge / p.mass;
-  float s2h = 0.0f, s2l = 0.0f;
-  if (DF) split_f64(p.soft2, s2h, s2l);
   bool bad = false;
 
   for (int kk = sch.bin_start[blockIdx.x]; kk < sch.bin_start[blockIdx.x + 1]; ++kk) {
     const int inst = sch.order[kk];
     const int64_t i0 = sch.off[inst];
     const int n = sch.off[inst + 1] - sch.off[inst];
-    const unsigned inst_id = p.instance + (unsigned)inst;
     __syncthreads();  // the previous instance is done with shared memory
+    if (tid == 0) {
+      // the instance's own table entry, or the shared parameters with the
+      // instance word offset by the instance's index
+      if (ptab) {
+        pinst = ptab[inst];
+      } else {
+        pinst = pall;
+        pinst.instance = pall.instance + (unsigned)inst;
+      }
+    }
     const int np32 = (n + 31) & ~31;
     if (SYM)
       for (int i = n + tid; i < np32; i += T) sp[i] = BD4{1e18, 1e18, 1e18, 0.0};  // weight-0 dummies
@@ -307,6 +314,15 @@ __global__ void __launch_bounds__(512, 1) k_batched(Phys p, StateView s,
       sp[i] = r;
     }
     __syncthreads();
+    const Phys &p = pinst;
+    const unsigned inst_id = p.instance;
+    const double dt = p.dt, hdt2 = 0.5 * dt * dt;
+    const double inv = 1.0 / (1.0 + p.gamma * dt / (2.0 * p.mass)), g = p.gamma / p.mass;
+    const double sig = p.noise_T > 0.0 ? sqrt(2.0 * p.gamma * KB * p.noise_T * dt) / p.mass : 0.0;
+    const double pref_u = p.k_coulomb * p.charge * p.charge / p.mass;
+    const double soft2 = p.soft2;
+    float s2h = 0.0f, s2l = 0.0f;
+    if (DF) split_f64(soft2, s2h, s2l);
     for (int64_t st = 0; st < nsteps; ++st) {
       const int64_t snew = step0 + st + 1;
       const double t = p.t0 + (double)snew * dt;
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(512, 1) k_batched(Phys p, StateView s,
       }
       __syncthreads();
       // forces at r+ and the kick
-      if (SYM) bsym_forces<QARR, DF>(sp, acc, npad, n, np32, p.soft2, s2h, s2l);
+      if (SYM) bsym_forces<QARR, DF>(sp, acc, npad, n, np32, soft2, s2h, s2l);
       for (int ib = 0; ib < n; ib += T) {
         const int i = ib + tid;
         const BD4 ri = sp[min(i, n - 1)];
@@ -343,7 +359,7 @@ __global__ void __launch_bounds__(512, 1) k_batched(Phys p, StateView s,
           }
         } else {
 #pragma unroll 2
-          for (int j = 0; j < n; ++j) bpair<QARR>(ri.x, ri.y, ri.z, sp[j], p.soft2, a0, a1, a2);
+          for (int j = 0; j < n; ++j) bpair<QARR>(ri.x, ri.y, ri.z, sp[j], soft2, a0, a1, a2);
         }
         if (i < n) {
           const int64_t gi = i0 + i;
@@ -411,7 +427,7 @@ int batched_plan(int n_inst, const int64_t *offsets, int n_bins, unsigned short 
   return pos;
 }
 
-cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const int64_t *offsets,
+cudaError_t launch_batched(const Phys &p, const Phys *ptab, const StateView &s, int n_inst, const int64_t *offsets,
                            int n_bins, int threads, bool allow_sym, int64_t step0, int64_t nsteps, unsigned *err,
                            cudaStream_t st) {
   BatchSched sch;
@@ -426,7 +442,8 @@ cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const 
   const bool df = p.precision == MODE_DF64;
   const bool sym = allow_sym && maxn <= BATCH_SYM_N;
   const int npad = (std::max(maxn, 1) + 31) & ~31;
-  const size_t need = sym ? (size_t)npad * (sizeof(BD4) + 3 * sizeof(double)) : (size_t)std::max(maxn, 1) * sizeof(BD4);
+  const size_t need = sizeof(Phys) + (sym ? (size_t)npad * (sizeof(BD4) + 3 * sizeof(double))
+                                          : (size_t)std::max(maxn, 1) * sizeof(BD4));
   // At least 120 KB of shared memory per CTA, so no SM holds two bins: each
   // bin then owns one SM, which is what the LPT packing assumes.
   const size_t smem = std::max(need, (size_t)120 * 1024);
@@ -451,21 +468,21 @@ cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const 
     }
   }
   if (sym && s.q && df)
-    k_batched<true, true, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+    k_batched<true, true, true><<<n_bins, threads, smem, st>>>(p, ptab, s, sch, step0, nsteps, npad, err);
   else if (sym && df)
-    k_batched<false, true, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+    k_batched<false, true, true><<<n_bins, threads, smem, st>>>(p, ptab, s, sch, step0, nsteps, npad, err);
   else if (sym && s.q)
-    k_batched<true, false, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+    k_batched<true, false, true><<<n_bins, threads, smem, st>>>(p, ptab, s, sch, step0, nsteps, npad, err);
   else if (sym)
-    k_batched<false, false, true><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+    k_batched<false, false, true><<<n_bins, threads, smem, st>>>(p, ptab, s, sch, step0, nsteps, npad, err);
   else if (s.q && df)
-    k_batched<true, true, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+    k_batched<true, true, false><<<n_bins, threads, smem, st>>>(p, ptab, s, sch, step0, nsteps, npad, err);
   else if (s.q)
-    k_batched<true, false, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+    k_batched<true, false, false><<<n_bins, threads, smem, st>>>(p, ptab, s, sch, step0, nsteps, npad, err);
   else if (df)
-    k_batched<false, true, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+    k_batched<false, true, false><<<n_bins, threads, smem, st>>>(p, ptab, s, sch, step0, nsteps, npad, err);
   else
-    k_batched<false, false, false><<<n_bins, threads, smem, st>>>(p, s, sch, step0, nsteps, npad, err);
+    k_batched<false, false, false><<<n_bins, threads, smem, st>>>(p, ptab, s, sch, step0, nsteps, npad, err);
   return cudaGetLastError();
 }
 

@@ -708,7 +708,7 @@ cudaError_t launch_epi_step(const Phys &p, const StateView &s, const double *cx,
 // Ensemble kernel (nb_batched.cu).
 int batched_plan(int n_inst, const int64_t *offsets, int n_bins, unsigned short *order,
                  unsigned short *bin_start, double *max_load, double *mean_load);
-cudaError_t launch_batched(const Phys &p, const StateView &s, int n_inst, const int64_t *offsets,
+cudaError_t launch_batched(const Phys &p, const Phys *ptab, const StateView &s, int n_inst, const int64_t *offsets,
                            int n_bins, int threads, bool allow_sym, int64_t step0, int64_t nsteps,
                            unsigned *err, cudaStream_t st);
 constexpr int BATCH_LIMIT_INST = 1024;

@@ -206,6 +206,35 @@ def kz_ensemble(n_inst=512, n_min=32, n_max=4096, seed=4, temperature=0.5e-3, st
                 steps=steps, name="kz-ensemble-%dx[%d..%d]" % (n_inst, n_min, n_max))
 
 
+def kz_quench_sweep(n_inst=512, n_min=32, n_max=4096, seed=6, temperature=0.5e-3, steps=20000, span=10.0):
+    """The Kibble-Zurek ensemble with a quench rate of its own per instance
+    (defect statistics against quench time, Sec. I): instance k ramps the
+    radial frequency linearly at rate r_k, log-spaced from kz_ensemble's rate
+    (k = 0) down to that rate / span, every ramp passing the midpoint
+    frequency (w0 + w1) / 2 at the middle of the run, so the slowest quench
+    changes the trap least; the instance word of the noise is k.  Sizes,
+    chains, velocities, friction, step and temperature as kz_ensemble.
+
+    Returns kz_ensemble's dict with "phys" a list of n_inst dicts."""
+    w = kz_ensemble(n_inst=n_inst, n_min=n_min, n_max=n_max, seed=seed, temperature=temperature, steps=steps)
+    base = w["phys"]
+    w0, w1 = TWO_PI * 1.2e6, TWO_PI * 0.6e6
+    t_mid = 0.5 * steps * base["dt"]
+    rate0 = base["omega_rate"][0]
+    per = []
+    for k in range(n_inst):
+        r = rate0 / span ** (k / max(n_inst - 1, 1))
+        wr = 0.5 * (w0 + w1) - r * t_mid
+        p = dict(base)
+        p["omega"] = (wr, wr, base["omega"][2])
+        p["omega_rate"] = (r, r, 0.0)
+        p["instance"] = k
+        per.append(p)
+    w["phys"] = per
+    w["name"] = "kz-quench-sweep-%dx[%d..%d]-span%g" % (n_inst, n_min, n_max, span)
+    return w
+
+
 def adjoint_cloud(n=4096, seed=5, steps=2000):
     """N = 4096 ions in the harmonic pseudopotential 2pi(1, 1, 0.2) MHz,
     uniform in the cold-fluid spheroid that trap holds, 10 mK velocities,

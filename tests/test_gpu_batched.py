@@ -236,3 +236,142 @@ def test_batched_largest_instance(nb):
         scale = np.max(np.abs(pos[:, i0:i1]))
         d = np.max(np.abs(ens.pos()[:, i0:i1].cpu().numpy() - single.pos().cpu().numpy()))
         assert d <= 1e-12 * scale, (k, d)
+
+
+# ---------------------------------------------------------------------------
+# nb_step_batched_each: a parameter set of its own per instance
+
+
+def each_params(phys, n_inst):
+    """Per-instance parameters that differ in every field the ensemble kernel
+    reads: ramp, friction, temperature, time origin, step, mass, softening,
+    trap kind and noise word (one instance without noise, one RF-driven)."""
+    out = []
+    for k in range(n_inst):
+        ph = dict(phys)
+        ph["omega_rate"] = tuple(r * (0.5 + 0.25 * k) for r in phys["omega_rate"])
+        ph["gamma"] = phys["gamma"] * (1.0 + 0.5 * k)
+        ph["noise_T"] = 0.0 if k % 3 == 1 else phys["noise_T"] * (1.0 + k)
+        ph["dt"] = phys["dt"] * (1.0 + 0.1 * k)
+        ph["t0"] = 1e-7 * k
+        ph["mass"] = phys["mass"] * (1.0 + 0.05 * k)
+        ph["soft2"] = (1e-6 * k) ** 2
+        ph["instance"] = 1000 + 7 * k
+        if k == 2:
+            ph.update(trap="rf", q_mathieu=0.3, omega_rf=2 * math.pi * 10e6, rf_phase=0.4)
+        out.append(ph)
+    return out
+
+
+def oracle_each(orc, ph, x, v, nsteps):
+    p = orc.make_params(**ph)
+    ax, ay, az = orc.accel(p, ph["t0"], *x, *v)
+    st = dict(x=x[0], y=x[1], z=x[2], vx=v[0], vy=v[1], vz=v[2], ax=ax, ay=ay, az=az, step=0)
+    return p, orc.run(p, st, nsteps)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_batched_each_matches_oracle_per_instance(nb, orc, precision):
+    sizes = [3, 33, 100, 257, 600, 31]
+    off, pos, vel, phys = small_ensemble(sizes, seed=21)
+    pos = pos + 1e-7 * np.random.default_rng(6).standard_normal(pos.shape)  # off the axis
+    per = each_params(phys, len(sizes))
+    pars = [nb.Params.from_phys(ph, precision=precision) for ph in per]
+    nsteps = 40
+    sysm = nb.System(pos, vel)
+    nb.init_batched(pars, sysm, off)
+    nb.step_batched_each(pars, sysm, off, nsteps // 2)
+    nb.step_batched_each(pars, sysm, off, nsteps - nsteps // 2)
+    nb.sync_status()
+    assert sysm.step == nsteps
+    gp, gv = sysm.pos().cpu().numpy(), sysm.vel().cpu().numpy()
+    for k, ph in enumerate(per):
+        i0, i1 = off[k], off[k + 1]
+        x, v = pos[:, i0:i1], vel[:, i0:i1]
+        p, ref = oracle_each(orc, ph, x, v, nsteps)
+        _, ulp = oracle_each(orc, ph, x * (1.0 + 2.0 ** -52), v, nsteps)
+        rp = np.stack([ref["x"], ref["y"], ref["z"]])
+        rv = np.stack([ref["vx"], ref["vy"], ref["vz"]])
+        up = np.stack([ulp["x"], ulp["y"], ulp["z"]])
+        uv = np.stack([ulp["vx"], ulp["vy"], ulp["vz"]])
+        ep, ev = floors.per_ion(gp[:, i0:i1] - rp), floors.per_ion(gv[:, i0:i1] - rv)
+        sp, sv = np.max(np.abs(up - rp)), np.max(np.abs(uv - rv))
+        print("instance %d (n=%d): gpu dp=%.3g dv=%.3g | self dp=%.3g dv=%.3g"
+              % (k, sizes[k], np.max(ep), np.max(ev), sp, sv))
+        fp, fv = floors.contract_floor(orc, p, [x, rp], nsteps, ph["dt"], vels=[v, rv])
+        assert np.all(ep <= 10 * sp + fp), k
+        assert np.all(ev <= 10 * sv + fv), k
+        # and not under its neighbour's parameters (with this one's noise word)
+        _, other = oracle_each(orc, dict(per[(k + 1) % len(per)], instance=ph["instance"]), x, v, nsteps)
+        op = np.stack([other["x"], other["y"], other["z"]])
+        assert np.max(np.abs(gp[:, i0:i1] - op)) > 100 * np.max(np.abs(gp[:, i0:i1] - rp)), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_batched_each_with_shared_entries_is_bitwise_the_shared_call(nb, precision):
+    """A table whose entry k is the shared parameters with instance word
+    instance + k gives bitwise the result of nb_step_batched."""
+    sizes = [7, 200, 129, 1000, 33]
+    off, pos, vel, phys = small_ensemble(sizes, seed=22)
+    par = nb.Params.from_phys(phys, precision=precision, instance=40)
+    shared = run_gpu(nb, dict(phys, instance=40), off, pos, vel, 12, precision=precision)
+    pars = [nb.Params.from_phys(phys, precision=precision, instance=40 + k) for k in range(len(sizes))]
+    sysm = nb.System(pos, vel)
+    nb.init_batched(par, sysm, off)
+    nb.step_batched_each(pars, sysm, off, 12)
+    nb.sync_status()
+    for t in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
+        assert torch.equal(getattr(shared, t), getattr(sysm, t)), t
+
+
+def test_batched_each_table_reuse_and_graph_capture(nb):
+    """The stream's table is refilled when the entries change (a table A
+    call then a table B call on one stream equals the same calls with the
+    scratch released in between), a captured launch replays the eager one,
+    and a capture with other entries than the stream's last uncaptured call
+    is refused before anything is enqueued."""
+    sizes = [50, 120, 7]
+    off, pos, vel, phys = small_ensemble(sizes, seed=23)
+    ph = each_params(phys, 3)
+    per_a = [nb.Params.from_phys(p) for p in ph]
+    per_b = [nb.Params.from_phys(dict(ph[2 - k], instance=5 + k)) for k in range(3)]
+
+    def start():
+        sysm = nb.System(pos, vel)
+        nb.init_batched(per_a, sysm, off)
+        return sysm
+
+    both = start()
+    nb.step_batched_each(per_a, both, off, 3)
+    nb.step_batched_each(per_b, both, off, 4)
+    nb.sync_status()
+    ref = start()
+    nb.step_batched_each(per_a, ref, off, 3)
+    nb.sync_status()
+    nb.release()  # drops the stream's table: the next call fills a new one
+    nb.step_batched_each(per_b, ref, off, 4)
+    nb.sync_status()
+    for t in ("x", "vz", "ay"):
+        assert torch.equal(getattr(both, t), getattr(ref, t)), t
+
+    eager = start()
+    nb.step_batched_each(per_a, eager, off, 3)
+    nb.sync_status()
+    sysm = start()
+    scratch = start()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        nb.step_batched_each(per_a, scratch, off, 1, stream=s)  # fills this stream's table
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        nb.step_batched_each(per_a, sysm, off, 3)
+        with pytest.raises(nb.NBError):
+            nb.step_batched_each(per_b, sysm, off, 3)
+    g.replay()
+    torch.cuda.synchronize()
+    for t in ("x", "vz", "ay"):
+        assert torch.equal(getattr(eager, t), getattr(sysm, t)), t

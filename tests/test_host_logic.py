@@ -304,3 +304,41 @@ def test_bench_roofline_and_kernel_label(api):
     assert bench.recorded_traffic("mixed_split", 12345)[0] is None
     t, src = bench.recorded_traffic("mixed_split", 100000)
     assert t is not None and 1e6 < t < 1e8 and src.endswith(".md"), (t, src)
+
+
+def test_batched_each_validation(api):
+    """nb_step_batched_each checks every entry of its host table before it
+    touches the device; an empty ensemble only advances the step."""
+    import ctypes as C
+    L = api.lib()
+    base = W.phys(omega=(1e6, 1e6, 2e5), dt=1e-9)
+
+    def table(*edits):
+        ps = [api.Params.from_phys(base, **e) for e in edits]
+        return (api.NbParams * len(ps))(*[p.to_c() for p in ps]), len(ps)
+
+    sysm = api.NbSystem()
+    sysm.n, sysm.step = 0, 5
+    call = lambda tab, n, off: L.nb_step_batched_each(tab, n, off, C.byref(sysm), 3, None)
+    offs = lambda k: np.zeros(k + 1, dtype=np.int64)
+    tab, n = table({}, {})
+    off = offs(2)
+    offp = off.ctypes.data_as(C.POINTER(C.c_int64))
+    assert call(tab, -1, offp) == 1
+    assert call(None, 2, offp) == 1
+    assert call(tab, 1025, offp) == 1
+    tab, n = table({}, {"mass": 0.0})
+    assert call(tab, n, offp) == 1
+    assert L.nb_last_error().decode().startswith("per_inst[1]: mass")
+    tab, n = table({}, {"precision": "df64"})
+    assert call(tab, n, offp) == 1 and "precision" in L.nb_last_error().decode()
+    tab, n = table({"precision": "mixed"}, {"precision": "mixed"})
+    assert call(tab, n, offp) == 6  # NB_ENOTSUP
+    tab, n = table({"dt": 0.0}, {})
+    assert call(tab, n, offp) == 1
+    bad = np.array([0, 0, 1], dtype=np.int64)
+    tab, n = table({}, {})
+    assert call(tab, n, bad.ctypes.data_as(C.POINTER(C.c_int64))) == 1  # offsets must end at n
+    assert sysm.step == 5
+    assert call(tab, n, offp) == 0 and sysm.step == 8
+    assert L.nb_step_batched_each(None, 0, None, C.byref(sysm), 2, None) == 0 and sysm.step == 10
