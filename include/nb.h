@@ -257,15 +257,12 @@ nb_status nb_energy(const nb_params *params, const nb_system *sys,
  * The Jacobian is symmetric, so this is also the Jacobian-vector product.
  * lam* and g* are device SoA arrays of n doubles.  FP64 differences d and
  * dl.  Each pair's term (with its r^-3, r^-5 and d . dl) is formed in
- * double-float on the FP32 pipe (relative error about 2^-44 of the term):
- *  - params->precision == NB_DF64: in units fixed for the call (positions
- *    and sqrt(soft2) by 2^-sc, cotangents by 2^-se, from the largest
- *    exponents over all ions, found by a pre-pass on the stream), summed in
- *    double-float over tiles of partners and widened to FP64 once per tile.
- *    1/r in those units is capped at 2^25: pairs closer than 2^-25 of the
- *    position unit take the seed terms at that distance.
- *  - otherwise: in units of each pair's own exponents, widened to FP64 per
- *    pair and accumulated in FP64.                                         */
+ * double-float on the FP32 pipe, in units of the pair's own exponents
+ * (relative error about 2^-44 of the term), and an ion's terms are summed in
+ * double-float with one exponent per sum, the largest unit met so far, and
+ * widened into an FP64 sum every 32 partners.  Weights q_j keep 48 bits;
+ * a subnormal weight counts as 0.  One arithmetic for every
+ * params->precision (NB_FP64 and NB_DF64 give the same bits).             */
 nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys,
                         const double *lx, const double *ly, const double *lz,
                         double *gx, double *gy, double *gz, int flags,
@@ -383,9 +380,9 @@ nb_status nb_set_tuning(int32_t kind, int32_t precision, int64_t n_lo, int64_t n
  * numbers), and its exact gradient with respect to x_0, v_0 and the three
  * trap frequencies by the discrete adjoint (reverse sweep) of the Verlet
  * map.  Supported: static harmonic trap, gamma = 0, noise_T = 0, and the
- * NB_FP64 or NB_DF64 arithmetic for the forward, its recompute and the
- * Jacobian products (as nb_forces and nb_forces_vjp in that precision;
- * NB_ENOTSUP otherwise).  The forward stores the state (x, v, a)
+ * NB_FP64 or NB_DF64 arithmetic for the forward and its recompute (as
+ * nb_forces in that precision; NB_ENOTSUP otherwise); the Jacobian products
+ * are those of nb_forces_vjp.  The forward stores the state (x, v, a)
  * at steps 0, every, 2*every, ... in `ckpt`; the backward recomputes each
  * segment from its checkpoint (bitwise identical to the forward) and sweeps
  * it in reverse, so the result does not depend on `every`. */

@@ -18,8 +18,9 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libnb.so")
 SOURCES = ["nb_pair.cu", "nb_sym.cu", "nb_integrate.cu", "nb_batched.cu", "nb_adjoint.cu",
            "nb_api.cu", "nb_noalloc.cu", "nb_probe.cu",
-           "nb_vjp_sym.cu", "nb_small.cu"]
-HEADERS = ["nb_common.cuh", "nb_pairterm.cuh", "nb_verlet.cuh", os.path.join("..", "..", "include", "nb.h")]
+           "nb_vjp.cu", "nb_small.cu"]
+HEADERS = ["nb_common.cuh", "nb_pairterm.cuh", "nb_vjpterm.cuh", "nb_symsched.cuh", "nb_verlet.cuh",
+           os.path.join("..", "..", "include", "nb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -62,8 +62,7 @@ constexpr size_t STEP_WINDOW_CACHE = 4;  // windows kept per stream (least recen
 struct Arena {
   char *buf = nullptr;
   size_t cap = 0;
-  unsigned *err = nullptr;  // 256 B: device error word at 0, step counters at 64 and 72,
-                            // the double-float VJP's two exponents at 128
+  unsigned *err = nullptr;  // 256 B: device error word at 0, step counters at 64 and 72
   cudaStream_t cap_st = nullptr;  // private stream the step windows are captured on
   std::vector<StepGraph> windows;  // at most STEP_WINDOW_CACHE
   uint64_t uses = 0;
@@ -75,7 +74,6 @@ struct Arena {
 };
 
 int64_t *step_counters(Arena *a) { return reinterpret_cast<int64_t *>(reinterpret_cast<char *>(a->err) + 64); }
-int *vjp_scales(Arena *a) { return reinterpret_cast<int *>(reinterpret_cast<char *>(a->err) + 128); }
 
 std::mutex g_mu;
 std::map<std::pair<int, cudaStream_t>, Arena> g_arenas;
@@ -746,13 +744,7 @@ nb_status nb_forces_vjp(const nb_params *params, const nb_system *sys, const dou
   const Phys p = to_phys(params);
   const StateView v = to_view(sys);
   const double t = params->t0 + (double)sys->step * params->dt;
-  const bool df = params->precision == NB_DF64;
-  if (df) {
-    NB_CUDA_TRY(launch_vjp_scales(n, sys->x, sys->y, sys->z, lx, ly, lz, vjp_scales(a), st));
-    count_launches(1);
-  }
-  NB_CUDA_TRY(launch_pair_vjp(pl, n, sys->x, sys->y, sys->z, sys->q, lx, ly, lz, params->soft2, part, a->err, st, df,
-                              vjp_scales(a)));
+  NB_CUDA_TRY(launch_pair_vjp(pl, n, sys->x, sys->y, sys->z, sys->q, lx, ly, lz, params->soft2, part, a->err, st));
   NB_CUDA_TRY(launch_epi_vjp(p, v, part, pl.n_jc, lx, ly, lz, gx, gy, gz, flags, t, st));
   count_launches(2);
   return NB_OK;
@@ -1042,7 +1034,6 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
   if (gscale && !aligned8(gscale)) return fail(NB_EINVAL, "gscale is not 8-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
   const int mode = params->precision;  // the forward's force arithmetic, for the recompute
-  const bool df = mode == NB_DF64;     // and the Jacobian products' arithmetic
   const Plan pl = make_plan(n, mode, 0);
   const Plan plv = make_plan(n, MODE_FP64, 2);
   const int64_t S = n_segments(nsteps, every);
@@ -1110,12 +1101,8 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
     // reverse sweep over the segment
     for (int64_t m = len - 1; m >= 0; --m) {
       const auto X = slot(m + 1);
-      if (df) {
-        NB_CUDA_TRY(launch_vjp_scales(n, X[0], X[1], X[2], ab[0], ab[1], ab[2], vjp_scales(a), st));
-        count_launches(1);
-      }
-      NB_CUDA_TRY(launch_pair_vjp(plv, n, X[0], X[1], X[2], sys->q, ab[0], ab[1], ab[2], params->soft2, vpart, a->err, st,
-                                  df, vjp_scales(a)));
+      NB_CUDA_TRY(launch_pair_vjp(plv, n, X[0], X[1], X[2], sys->q, ab[0], ab[1], ab[2], params->soft2, vpart, a->err,
+                                  st));
       const double *xc[3] = {X[0], X[1], X[2]};
       NB_CUDA_TRY(launch_adj_epi(p, n, sys->q, xc, vpart, plv.n_jc, xb.data(), vb.data(), ab.data(),
                                  wacc.data(), 0, (start + m) >= 1 ? 1 : 0, st));
@@ -1124,12 +1111,8 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
   }
   // x_0 term: J(x_0)^T ab_0 (slot 0 holds x_0 after segment 0's recompute)
   const auto X0 = slot(0);
-  if (df) {
-    NB_CUDA_TRY(launch_vjp_scales(n, X0[0], X0[1], X0[2], ab[0], ab[1], ab[2], vjp_scales(a), st));
-    count_launches(1);
-  }
-  NB_CUDA_TRY(launch_pair_vjp(plv, n, X0[0], X0[1], X0[2], sys->q, ab[0], ab[1], ab[2], params->soft2, vpart, a->err, st,
-                              df, vjp_scales(a)));
+  NB_CUDA_TRY(launch_pair_vjp(plv, n, X0[0], X0[1], X0[2], sys->q, ab[0], ab[1], ab[2], params->soft2, vpart, a->err,
+                              st));
   const double *x0c[3] = {X0[0], X0[1], X0[2]};
   NB_CUDA_TRY(launch_adj_epi(p, n, sys->q, x0c, vpart, plv.n_jc, xb.data(), vb.data(), ab.data(), wacc.data(),
                              1, 0, st));

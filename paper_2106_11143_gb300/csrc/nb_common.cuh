@@ -284,211 +284,6 @@ __device__ __forceinline__ double rinv1_fp64(double dx, double dy, double dz, do
   return em ? a : 0.0;
 }
 
-// Double-float helpers for vjp_term_fp64: exact-product multiply and
-// TwoSum-based add of (hi, lo) pairs (relative error about 2^-44).
-__device__ __forceinline__ void dfmul(float ah, float al, float bh, float bl, float &h, float &l) {
-  h = ah * bh;
-  l = fmaf(ah, bl, fmaf(al, bh, fmaf(ah, bh, -h)));
-}
-__device__ __forceinline__ void dfadd(float ah, float al, float bh, float bl, float &h, float &l) {
-  float e;
-  two_sum_f(ah, bh, h, e);
-  l = e + (al + bl);
-}
-
-// The pair-force VJP term for one pair, T = dl r^-3 - 3 (d . dl) r^-5 d, with
-// d the FP64 displacement and dl the FP64 difference of the cotangents.  All
-// of it runs in double-float on the FP32 pipe: d is split with the scale
-// 2^-sc of rinv3_fp64 (its largest component, or sqrt(soft2), in [1, 2)), dl
-// with its own scale 2^-se; r^-3, 3 r^-5, the dot product and T are formed in
-// those scaled units, and each component of T is widened to FP64 with the
-// scale 2^(se - 3 sc) put back (one FP64 add per component).  Relative error
-// about 2^-44 of the larger of the two terms.  T = 0 when dl = 0 or when d = 0
-// without softening.
-__device__ __forceinline__ void vjp_term_fp64(double dx, double dy, double dz, double lx, double ly,
-                                              double lz, double soft2, double T[3]) {
-  const int ex = (__double2hiint(dx) >> 20) & 0x7ff;
-  const int ey = (__double2hiint(dy) >> 20) & 0x7ff;
-  const int ez = (__double2hiint(dz) >> 20) & 0x7ff;
-  const int e2 = (__double2hiint(soft2) >> 20) & 0x7ff;
-  const int es2 = e2 ? ((e2 - 1023) >> 1) + 1023 : 0;
-  const int em = max(max(ex, ey), max(ez, es2));
-  const int sc = em - 1023;
-  const int fx = (__double2hiint(lx) >> 20) & 0x7ff;
-  const int fy = (__double2hiint(ly) >> 20) & 0x7ff;
-  const int fz = (__double2hiint(lz) >> 20) & 0x7ff;
-  const int fm = max(max(fx, fy), fz);
-  const int se = fm - 1023;
-  float dh[3], dl[3], eh[3], el[3], s2h = 0.0f, s2l = 0.0f;
-  split_f64_scaled(dx, sc, dh[0], dl[0]);
-  split_f64_scaled(dy, sc, dh[1], dl[1]);
-  split_f64_scaled(dz, sc, dh[2], dl[2]);
-  split_f64_scaled(lx, se, eh[0], el[0]);
-  split_f64_scaled(ly, se, eh[1], el[1]);
-  split_f64_scaled(lz, se, eh[2], el[2]);
-  if (e2) split_f64_scaled(soft2, 2 * sc, s2h, s2l);
-  // double-float r^2, seed, compensated residual (as in df_rinv3)
-  const float p0 = dh[0] * dh[0], p1 = dh[1] * dh[1], p2 = dh[2] * dh[2];
-  const float q0 = fmaf(dh[0], dh[0], -p0), q1 = fmaf(dh[1], dh[1], -p1), q2 = fmaf(dh[2], dh[2], -p2);
-  float h, t1, t2;
-  two_sum_f(p0, p1, h, t1);
-  two_sum_f(h, p2, h, t2);
-  float l = (t1 + t2) + (q0 + q1 + q2);
-  l = fmaf(dh[0] + dh[0], dl[0], l);
-  l = fmaf(dh[1] + dh[1], dl[1], l);
-  l = fmaf(dh[2] + dh[2], dl[2], l);
-  if (e2) {
-    float t3;
-    two_sum_f(h, s2h, h, t3);
-    l += t3 + s2l;
-  }
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(h));
-  const float y2 = y * y;
-  const float y2e = fmaf(y, y, -y2);
-  float r = fmaf(-h, y2, 1.0f);
-  r = fmaf(-h, y2e, r);
-  r = fmaf(-l, y2, r);
-  const float c3 = r * fmaf(r, 1.875f, 1.5f);
-  const float c5 = r * fmaf(r, 4.375f, 2.5f);
-  const float y3h = y2 * y;
-  float y3e = fmaf(y2, y, -y3h);
-  y3e = fmaf(y2e, y, y3e);
-  const float y5h = y3h * y2;
-  float y5e = fmaf(y3h, y2, -y5h);
-  y5e = fmaf(y3h, y2e, fmaf(y3e, y2, y5e));
-  const float s3h = y3h, s3l = fmaf(y3h, c3, y3e);
-  const float s5h = y5h, s5l = fmaf(y5h, c5, y5e);
-  // dot = d . dl (scaled units)
-  float dth, dtl, ph, pl;
-  dfmul(dh[0], dl[0], eh[0], el[0], dth, dtl);
-  dfmul(dh[1], dl[1], eh[1], el[1], ph, pl);
-  dfadd(dth, dtl, ph, pl, dth, dtl);
-  dfmul(dh[2], dl[2], eh[2], el[2], ph, pl);
-  dfadd(dth, dtl, ph, pl, dth, dtl);
-  // w = 3 r^-5 dot
-  float wh, wl;
-  dfmul(dth, dtl, s5h, s5l, wh, wl);
-  const float w3h = 3.0f * wh;
-  const float w3l = fmaf(3.0f, wh, -w3h) + 3.0f * wl;
-  const int out = se - 3 * sc;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    float uh, ul, vh, vl, th, tl;
-    dfmul(eh[k], el[k], s3h, s3l, uh, ul);
-    dfmul(dh[k], dl[k], w3h, w3l, vh, vl);
-    dfadd(uh, ul, -vh, -vl, th, tl);
-    const double t = f32_to_f64_scaled(th, out) + f32_to_f64_scaled(tl, out);
-    T[k] = (em && fm) ? t : 0.0;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Double-float VJP (NB_DF64).  vjp_term_fp64 scales each pair by its own
-// exponents, so its double-float T of different pairs have different units
-// and are widened to FP64 one by one.  Here the units are fixed for a whole
-// call: positions (and sqrt(soft2)) scaled by 2^-sc and cotangents by 2^-se,
-// with sc and se from the largest exponents over all ions (k_vjp_scales), so
-// that |d| 2^-sc < 2 and |dl| 2^-se < 2.  Every T' = T 2^(3 sc - se) is then
-// in one unit, and a thread sums them on the FP32 pipe (df_acc) and widens
-// the sum once per tile.
-
-// 1/r in the fixed unit is capped at 2^25, so that y^5 stays below 2^125:
-// pairs closer than 2^-25 of the position unit take the uncorrected seed
-// terms at that distance.
-constexpr float VJP_YMAX = 33554432.0f;  // 2^25
-
-// sc from the largest biased exponent e of the position components (and of
-// sqrt(soft2)), se from that of the cotangent components: |x| < 2^(e - 1022),
-// so differences stay below 2^(e - 1021).
-__device__ __forceinline__ int vjp_pos_scale(int epos, double soft2) {
-  const int e2 = (__double2hiint(soft2) >> 20) & 0x7ff;
-  const int es2 = e2 ? ((e2 - 1023) >> 1) + 1023 : 0;
-  return max(epos, es2) - 1021;
-}
-__device__ __forceinline__ int vjp_lam_scale(int elam) { return elam - 1021; }
-
-// TwoSum accumulation of a double-float term into a double-float sum.
-__device__ __forceinline__ void df_acc(float &ah, float &al, float bh, float bl) {
-  float s, e;
-  two_sum_f(ah, bh, s, e);
-  ah = s;
-  al += e + bl;
-}
-
-// The VJP term T = dl r^-3 - 3 (d . dl) r^-5 d of vjp_term_fp64 in the fixed
-// units (th + tl = T 2^(3 sc - se)); 0 when d = 0 without softening.
-__device__ __forceinline__ void vjp_term_df(double dx, double dy, double dz, double lx, double ly,
-                                            double lz, double soft2, int sc, int se, float th[3],
-                                            float tl[3]) {
-  const int ex = (__double2hiint(dx) >> 20) & 0x7ff;
-  const int ey = (__double2hiint(dy) >> 20) & 0x7ff;
-  const int ez = (__double2hiint(dz) >> 20) & 0x7ff;
-  const bool e2 = soft2 != 0.0;
-  const bool live = (ex | ey | ez) != 0 || e2;
-  float dh[3], dl[3], eh[3], el[3], s2h = 0.0f, s2l = 0.0f;
-  split_f64_scaled(dx, sc, dh[0], dl[0]);
-  split_f64_scaled(dy, sc, dh[1], dl[1]);
-  split_f64_scaled(dz, sc, dh[2], dl[2]);
-  split_f64_scaled(lx, se, eh[0], el[0]);
-  split_f64_scaled(ly, se, eh[1], el[1]);
-  split_f64_scaled(lz, se, eh[2], el[2]);
-  if (e2) split_f64_scaled(soft2, 2 * sc, s2h, s2l);
-  const float p0 = dh[0] * dh[0], p1 = dh[1] * dh[1], p2 = dh[2] * dh[2];
-  const float q0 = fmaf(dh[0], dh[0], -p0), q1 = fmaf(dh[1], dh[1], -p1), q2 = fmaf(dh[2], dh[2], -p2);
-  float h, t1, t2;
-  two_sum_f(p0, p1, h, t1);
-  two_sum_f(h, p2, h, t2);
-  float l = (t1 + t2) + (q0 + q1 + q2);
-  l = fmaf(dh[0] + dh[0], dl[0], l);
-  l = fmaf(dh[1] + dh[1], dl[1], l);
-  l = fmaf(dh[2] + dh[2], dl[2], l);
-  if (e2) {
-    float t3;
-    two_sum_f(h, s2h, h, t3);
-    l += t3 + s2l;
-  }
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(h));
-  const bool capped = !(y <= VJP_YMAX);  // also for h = 0 (y = inf)
-  y = capped ? VJP_YMAX : y;
-  const float y2 = y * y;
-  const float y2e = fmaf(y, y, -y2);
-  float r = fmaf(-h, y2, 1.0f);
-  r = fmaf(-h, y2e, r);
-  r = fmaf(-l, y2, r);
-  r = capped ? 0.0f : r;
-  const float c3 = r * fmaf(r, 1.875f, 1.5f);
-  const float c5 = r * fmaf(r, 4.375f, 2.5f);
-  const float y3h = y2 * y;
-  float y3e = fmaf(y2, y, -y3h);
-  y3e = fmaf(y2e, y, y3e);
-  const float y5h = y3h * y2;
-  float y5e = fmaf(y3h, y2, -y5h);
-  y5e = fmaf(y3h, y2e, fmaf(y3e, y2, y5e));
-  const float s3h = y3h, s3l = fmaf(y3h, c3, y3e);
-  const float s5h = y5h, s5l = fmaf(y5h, c5, y5e);
-  float dth, dtl, ph, pl;
-  dfmul(dh[0], dl[0], eh[0], el[0], dth, dtl);
-  dfmul(dh[1], dl[1], eh[1], el[1], ph, pl);
-  dfadd(dth, dtl, ph, pl, dth, dtl);
-  dfmul(dh[2], dl[2], eh[2], el[2], ph, pl);
-  dfadd(dth, dtl, ph, pl, dth, dtl);
-  float wh, wl;
-  dfmul(dth, dtl, s5h, s5l, wh, wl);
-  const float w3h = 3.0f * wh;
-  const float w3l = fmaf(3.0f, wh, -w3h) + 3.0f * wl;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    float uh, ul, vh, vl;
-    dfmul(eh[k], el[k], s3h, s3l, uh, ul);
-    dfmul(dh[k], dl[k], w3h, w3l, vh, vl);
-    dfadd(uh, ul, -vh, -vl, th[k], tl[k]);
-    th[k] = live ? th[k] : 0.0f;
-    tl[k] = live ? tl[k] : 0.0f;
-  }
-}
-
 // FP32 r^-3 of an FP32 displacement (the mixed modes' bulk without the
 // accumulation): y = MUFU.RSQ(r^2) clamped against FP32 overflow, corrected
 // once: s = y^3 (1 + 3/2 e), e = 1 - r^2 y^2.  SEED: the bare seed's cube
@@ -646,18 +441,12 @@ cudaError_t launch_pair_force_range(const Plan &pl, int mode, int64_t n, int64_t
 cudaError_t launch_pair_phi(const Plan &pl, int64_t n, const double *x, const double *y,
                             const double *z, const double *q, double charge, double soft2,
                             double *part, cudaStream_t st);
-// VJP pair kernels: FP64 (vjp_term_fp64) or, with df, the double-float form
-// in the fixed units of `scales` (two ints written by launch_vjp_scales).
+// VJP pair kernels (nb_vjp.cu): the one-sided kernel into the plan's chunk
+// partials, or the half-pair kernel when pl.sym.
 cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const double *y,
                             const double *z, const double *q, const double *lx,
                             const double *ly, const double *lz, double soft2, double *part,
-                            unsigned *err, cudaStream_t st, bool df = false,
-                            const int *scales = nullptr);
-// The largest biased exponents of the position and cotangent components
-// (scales[0], scales[1]); zeroes them first, on `st`.
-cudaError_t launch_vjp_scales(int64_t n, const double *x, const double *y, const double *z,
-                              const double *lx, const double *ly, const double *lz, int *scales,
-                              cudaStream_t st);
+                            unsigned *err, cudaStream_t st);
 cudaError_t launch_split_positions(int64_t n, const double *x, const double *y,
                                    const double *z, float *out6, cudaStream_t st);
 cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x, const double *y,
@@ -666,7 +455,7 @@ cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x
 cudaError_t launch_vjp_sym(int64_t n, int nbk, int G, const double *x, const double *y,
                            const double *z, const double *q, const double *lx, const double *ly,
                            const double *lz, double soft2, double *part, int *sync, unsigned *err,
-                           bool inplace, cudaStream_t st, bool df, const int *scales);
+                           bool inplace, cudaStream_t st);
 
 // Epilogue kernels (nb_integrate.cu).
 struct StateView {

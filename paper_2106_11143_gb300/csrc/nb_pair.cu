@@ -216,124 +216,6 @@ __global__ void __launch_bounds__(256) k_pair_phi(int64_t n, int64_t jchunk,
 }
 
 // ---------------------------------------------------------------------------
-// VJP kernel (FP64): part[(jc*3+c)*n + i] =
-//   sum_{j in chunk} w_j [ dl^c / s^3 - 3 d^c (d . dl) / s^5 ],  dl = lam_i - lam_j.
-// FP64 for the differences and the accumulation; the term itself is formed
-// in double-float on the FP32 pipe and widened (vjp_term_fp64).
-template <bool QARR, bool DF>
-__global__ void __launch_bounds__(256) k_pair_vjp(int64_t n, int64_t jchunk,
-                                                  const double *__restrict__ x,
-                                                  const double *__restrict__ y,
-                                                  const double *__restrict__ z,
-                                                  const double *__restrict__ q,
-                                                  const double *__restrict__ lx,
-                                                  const double *__restrict__ ly,
-                                                  const double *__restrict__ lz, double soft2,
-                                                  const int *__restrict__ scales,
-                                                  double *__restrict__ part) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  D4 *s4 = reinterpret_cast<D4 *>(smem_raw);
-  const int B = blockDim.x;
-  const int tid = threadIdx.x;
-  const int64_t i = (int64_t)blockIdx.x * B + tid;
-  const int64_t ic = min(i, n - 1);
-  const int64_t jb = (int64_t)blockIdx.y * jchunk;
-  const int64_t je = min(jb + jchunk, n);
-  const double xi = x[ic], yi = y[ic], zi = z[ic];
-  const double mi = lx[ic], ni = ly[ic], oi = lz[ic];
-  int sc = 0, se = 0, out = 0;
-  if (DF) {
-    sc = vjp_pos_scale(scales[0], soft2);
-    se = vjp_lam_scale(scales[1]);
-    out = se - 3 * sc;
-  }
-  double gx = 0.0, gy = 0.0, gz = 0.0;
-  for (int64_t j0 = jb; j0 < je; j0 += B) {
-    __syncthreads();
-    const int64_t j = j0 + tid;
-    if (j < je) {
-      D4 e = make_d4(x[j], y[j], z[j], QARR ? q[j] : 1.0);
-      if (DF && QARR) {  // q as an FP32 (hi, lo) pair for the double-float product
-        float qh, ql;
-        split_f64(q[j], qh, ql);
-        *reinterpret_cast<float2 *>(&e.w) = make_float2(qh, ql);
-      }
-      s4[2 * tid] = e;
-      s4[2 * tid + 1] = make_d4(lx[j], ly[j], lz[j], 0.0);
-    }
-    __syncthreads();
-    const int cnt = (int)min((int64_t)B, je - j0);
-    if (DF) {
-      float ah[3] = {0.0f, 0.0f, 0.0f}, al[3] = {0.0f, 0.0f, 0.0f};
-      for (int k = 0; k < cnt; ++k) {
-        const D4 pj = s4[2 * k];
-        const D4 lj = s4[2 * k + 1];
-        float th[3], tl[3];
-        vjp_term_df(xi - pj.x, yi - pj.y, zi - pj.z, mi - lj.x, ni - lj.y, oi - lj.z, soft2, sc, se, th, tl);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (QARR) {
-            const float2 w = *reinterpret_cast<const float2 *>(&pj.w);
-            float uh, ul;
-            dfmul(th[c], tl[c], w.x, w.y, uh, ul);
-            df_acc(ah[c], al[c], uh, ul);
-          } else {
-            df_acc(ah[c], al[c], th[c], tl[c]);
-          }
-        }
-      }
-      gx += f32_to_f64_scaled(ah[0], out) + f32_to_f64_scaled(al[0], out);
-      gy += f32_to_f64_scaled(ah[1], out) + f32_to_f64_scaled(al[1], out);
-      gz += f32_to_f64_scaled(ah[2], out) + f32_to_f64_scaled(al[2], out);
-    } else {
-      for (int k = 0; k < cnt; ++k) {
-        const D4 pj = s4[2 * k];
-        const D4 lj = s4[2 * k + 1];
-        double T[3];
-        vjp_term_fp64(xi - pj.x, yi - pj.y, zi - pj.z, mi - lj.x, ni - lj.y, oi - lj.z, soft2, T);
-        if (QARR) {
-          gx = fma(pj.w, T[0], gx);
-          gy = fma(pj.w, T[1], gy);
-          gz = fma(pj.w, T[2], gz);
-        } else {
-          gx += T[0];
-          gy += T[1];
-          gz += T[2];
-        }
-      }
-    }
-  }
-  if (i < n) {
-    part[((int64_t)blockIdx.y * 3 + 0) * n + i] = gx;
-    part[((int64_t)blockIdx.y * 3 + 1) * n + i] = gy;
-    part[((int64_t)blockIdx.y * 3 + 2) * n + i] = gz;
-  }
-}
-
-// Largest biased exponents of the position components (out[0]) and of the
-// cotangent components (out[1]) over all ions: grid-stride maxima, a warp
-// reduction and one atomicMax per warp (a maximum, so the result does not
-// depend on the order).
-__global__ void k_vjp_scales(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
-                             const double *__restrict__ z, const double *__restrict__ lx,
-                             const double *__restrict__ ly, const double *__restrict__ lz,
-                             int *out) {
-  auto ex = [](double v) { return (unsigned)((__double2hiint(v) >> 20) & 0x7ff); };
-  unsigned ep = 0, el = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    ep = max(ep, max(ex(x[i]), max(ex(y[i]), ex(z[i]))));
-    el = max(el, max(ex(lx[i]), max(ex(ly[i]), ex(lz[i]))));
-  }
-  ep = __reduce_max_sync(0xffffffffu, ep);
-  el = __reduce_max_sync(0xffffffffu, el);
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(out, (int)ep);
-    atomicMax(out + 1, (int)el);
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Split FP64 positions into FP32 (hi, lo): hi = fl32(x), lo = fl32(x - hi).
 // out6 = [xh | yh | zh | xl | yl | zl], n floats each.
 __global__ void k_split_positions(int64_t n, const double *__restrict__ x,
@@ -418,41 +300,6 @@ cudaError_t launch_pair_phi(const Plan &pl, int64_t n, const double *x, const do
     k_pair_phi<true><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, soft2, part);
   else
     k_pair_phi<false><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, soft2, part);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pair_vjp(const Plan &pl, int64_t n, const double *x, const double *y,
-                            const double *z, const double *q, const double *lx,
-                            const double *ly, const double *lz, double soft2, double *part,
-                            unsigned *err, cudaStream_t st, bool df, const int *scales) {
-  if (df && !scales) return cudaErrorInvalidValue;
-  if (pl.sym)
-    return launch_vjp_sym(n, pl.nbk, pl.G, x, y, z, q, lx, ly, lz, soft2, part, part_sync(pl, part, n, 3), err,
-                          pl.n_jc == 1, st, df, scales);
-  const dim3 grid(pl.n_it, pl.n_jc);
-  const size_t smem = 2 * sizeof(D4) * pl.block;
-  if (df) {
-    if (q)
-      k_pair_vjp<true, true><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, lx, ly, lz, soft2, scales, part);
-    else
-      k_pair_vjp<false, true><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, lx, ly, lz, soft2, scales, part);
-  } else {
-    if (q)
-      k_pair_vjp<true, false><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, lx, ly, lz, soft2, scales, part);
-    else
-      k_pair_vjp<false, false><<<grid, pl.block, smem, st>>>(n, pl.jchunk, x, y, z, q, lx, ly, lz, soft2, scales, part);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_vjp_scales(int64_t n, const double *x, const double *y, const double *z,
-                              const double *lx, const double *ly, const double *lz, int *scales,
-                              cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(scales, 0, 2 * sizeof(int), st);
-  if (e != cudaSuccess) return e;
-  const int T = 256;
-  const int blocks = (int)std::min<int64_t>(round_up(n, T), 2 * (int64_t)device_sm_count());
-  k_vjp_scales<<<std::max(blocks, 1), T, 0, st>>>(n, x, y, z, lx, ly, lz, scales);
   return cudaGetLastError();
 }
 

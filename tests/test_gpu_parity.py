@@ -141,8 +141,7 @@ def test_vjp(nb, orc, precision):
 def test_vjp_symmetric_kernel(nb, orc, precision):
     """The half-pair VJP kernel (on from n = 2500), forced on at small and
     ragged sizes with both block sizes, with charges and softening, against the
-    oracle; and against the one-sided VJP kernel at n = 4100.  df64: the
-    double-float terms summed per tile on the FP32 pipe."""
+    oracle; and against the one-sided VJP kernel at n = 4100."""
     rng = np.random.default_rng(6)
     Pm = lambda phys: nb.Params.from_phys(phys, precision=precision)
     try:
@@ -182,14 +181,14 @@ def _vjp_term_bound(pos, lam, q, k_c, mass):
 
 
 @pytest.mark.parametrize("n", [1500, 6000])
-def test_vjp_df64_fixed_units(nb, orc, n):
-    """The double-float VJP works in units fixed for the whole call (the
-    largest position and cotangent exponents).  Stress them: a cloud 1 cm off
-    the origin (a position unit far above the spacing), cotangents spread over
-    20 decades, a pair 10 nm apart, charges; the one-sided (n = 1500) and the
-    half-pair (n = 6000) kernels.  Gate per ion: the error against the oracle
-    within 1e-12 of a bound on the sum of the ion's term magnitudes, for
-    fp64 and df64 alike."""
+def test_vjp_extreme_units(nb, orc, n):
+    """The VJP forms each pair's term in that pair's own units and sums the
+    terms in block-floating double-float.  Stress the units: a cloud 1 cm off
+    the origin (a position scale far above the spacing), cotangents spread
+    over 20 decades, a pair 10 nm apart, charges; the one-sided (n = 1500) and
+    the half-pair (n = 6000) kernels.  Gate per ion: the error against the
+    oracle within 1e-12 of a bound on the sum of the ion's term magnitudes.
+    NB_FP64 and NB_DF64 share the VJP arithmetic, so they agree bit for bit."""
     rng = np.random.default_rng(n)
     pos, _ = W.random_cloud(n, seed=n)
     pos = pos + np.array([[1e-2], [0.0], [-3e-3]])
@@ -206,7 +205,53 @@ def test_vjp_df64_fixed_units(nb, orc, n):
         err = np.max(np.sqrt(np.sum((out[prec] - ref) ** 2, axis=0)) / bound)
         print("%s n=%d: max conditioned error %.3g" % (prec, n, err))
         assert err <= 1e-12, prec
-    assert not np.array_equal(out["fp64"], out["df64"])
+    assert np.array_equal(out["fp64"], out["df64"])
+
+
+@pytest.mark.parametrize("n", [1500, 3000])
+def test_vjp_no_unit_cap(nb, orc, n):
+    """A pair far closer than the cloud's extent is exact, since every pair
+    is scaled by its own exponents: a pair 0.1 nm apart in a cloud 1 cm off
+    the origin (2^-27 of the position scale), one-sided and half-pair
+    kernels."""
+    rng = np.random.default_rng(n + 3)
+    pos, _ = W.random_cloud(n, seed=n + 3)
+    pos = pos + np.array([[1e-2], [0.0], [-3e-3]])
+    pos[:, 1] = pos[:, 0] + np.array([0.0, 1e-10, 0.0])
+    lam = rng.standard_normal((3, n))
+    phys = W.phys(omega=(6e6, 5e6, 1.2e6))
+    q = np.full(n, W.E_CHARGE)
+    ref = np.stack(orc.forces_vjp(oparams(orc, phys), 0.0, *pos, *lam))
+    bound = _vjp_term_bound(pos, lam, q, W.K_COULOMB, W.MASS_40U)
+    g = nb.forces_vjp(nb.Params.from_phys(phys), nb.System(pos), lam).cpu().numpy()
+    err = np.max(np.sqrt(np.sum((g - ref) ** 2, axis=0)) / bound)
+    print("n=%d: conditioned error %.3g" % (n, err))
+    assert err <= 1e-12
+
+
+@pytest.mark.parametrize("n", [1500, 3000])
+def test_vjp_block_floating_sums(nb, orc, n):
+    """The VJP sums each 32-partner tile in double-float with one
+    exponent per accumulator, rescaled when a term of a larger unit arrives.
+    Stress the rescaling: weights (charges) spread over 80 decades with both
+    signs, cotangents over 20 decades, a pair 10 nm apart and two ions with
+    equal cotangents (a vanishing term besides the self pairs); the one-sided
+    (n = 1500) and the half-pair (n = 3000) kernels.  Gate per ion: 1e-12 of
+    the bound on the sum of the ion's term magnitudes."""
+    rng = np.random.default_rng(n + 7)
+    pos, _ = W.random_cloud(n, seed=n + 7)
+    pos[:, 1] = pos[:, 0] + np.array([1e-8, 0.0, 0.0])
+    q = W.E_CHARGE * rng.choice([-1.0, 1.0], size=n) * 10.0 ** rng.uniform(-40, 40, size=n)
+    lam = rng.standard_normal((3, n)) * 10.0 ** rng.uniform(-10, 10, size=n)
+    lam[:, 5] = lam[:, 4]
+    phys = W.phys(omega=(6e6, 5e6, 1.2e6))
+    ref = np.stack(orc.forces_vjp(oparams(orc, phys), 0.0, *pos, *lam, q=q))
+    bound = _vjp_term_bound(pos, lam, q, W.K_COULOMB, W.MASS_40U)
+    g = nb.forces_vjp(nb.Params.from_phys(phys), nb.System(pos, q=q), lam).cpu().numpy()
+    assert np.all(np.isfinite(g))
+    err = np.max(np.sqrt(np.sum((g - ref) ** 2, axis=0)) / bound)
+    print("fp64 n=%d: max conditioned error %.3g" % (n, err))
+    assert err <= 1e-12
 
 
 def _oracle_traj(orc, phys, pos, vel, nsteps, reverse=False, q=None, eps=0.0):
