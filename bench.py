@@ -331,12 +331,13 @@ def kernel_source_sha():
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(precision, n):
-    """DRAM bytes (read + write) per launch of the pair kernel, from the ncu
-    summaries under profiles/: a line `traffic: precision=P n=N bytes=B
-    source=S` records one capture of this bench's command, S the kernel
-    sources' hash when it was taken.  None when there is no capture for this
-    case or the kernel has changed since."""
+def recorded_counters(precision, n):
+    """ncu counters of the pair kernel per launch, from the summaries under
+    profiles/: a line `traffic: precision=P n=N bytes=B [inst=I] source=S`
+    records one capture of this bench's command: B the DRAM bytes (read +
+    write), I the warp instructions executed (smsp__inst_executed.sum), S
+    the kernel sources' hash when it was taken.  ({}, None) when there is no
+    capture for this case or the kernel has changed since."""
     import glob
     want = kernel_source_sha()
     for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
@@ -346,8 +347,18 @@ def recorded_traffic(precision, n):
                 continue
             kv = dict(t.split("=", 1) for t in line.split()[1:])
             if kv.get("precision") == precision and int(kv.get("n", -1)) == n and kv.get("source") == want:
-                return int(kv["bytes"]), os.path.basename(path)
-    return None, None
+                out = {"bytes": int(kv["bytes"])}
+                if "inst" in kv:
+                    out["inst"] = int(kv["inst"])
+                return out, os.path.basename(path)
+    return {}, None
+
+
+def recorded_traffic(precision, n):
+    """DRAM bytes (read + write) per launch of the pair kernel and the
+    summary they come from (recorded_counters); (None, None) if unrecorded."""
+    c, src = recorded_counters(precision, n)
+    return c.get("bytes"), src
 
 
 def roofline(nb, path, n, kernel_ms, peaks, sm_mhz):
@@ -361,7 +372,8 @@ def roofline(nb, path, n, kernel_ms, peaks, sm_mhz):
     mhz = sm_mhz or peaks[pipe]["sm_mhz"]
     peak = 2 * lanes * SM_COUNT * mhz * 1e6 / 1e12
     achieved = FLOPS_PER_PAIR * evals / (kernel_ms / 1e3) / 1e12
-    traffic, src = recorded_traffic(path, n)
+    counters, src = recorded_counters(path, n)
+    traffic = counters.get("bytes")
     r = {"bound": "alu", "pipe": "FP64 FMA" if pipe == "dfma" else "FP32 FMA",
          "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
          "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kname,
@@ -375,6 +387,17 @@ def roofline(nb, path, n, kernel_ms, peaks, sm_mhz):
                                    "interactions, so this is not a pipe fraction"}}
     if traffic is not None:
         r["traffic_source"] = "profiles/" + src
+    if "inst" in counters:
+        # instruction issue: 4 warp instructions per clock per SM (one per
+        # scheduler), the unit that binds a kernel whose evaluation needs more
+        # issue slots than its convention-A flops suggest
+        ipeak = 4 * SM_COUNT * mhz * 1e6 / 1e9
+        iach = counters["inst"] / (kernel_ms / 1e3) / 1e9
+        r["issue"] = {"achieved": round(iach, 2), "peak": round(ipeak, 2), "unit": "G warp-instructions/s",
+                      "frac": round(iach / ipeak, 4),
+                      "warp_instructions_per_32_evaluations": round(counters["inst"] / (evals / 32.0), 2),
+                      "source": "smsp__inst_executed.sum per launch from profiles/%s over the live kernel time; "
+                                "peak 4 per clock per SM x %d SMs x %.0f MHz" % (src, SM_COUNT, mhz)}
     if path == "fp64" and kname.startswith("k_pair_sym"):
         b = FP64_FLOPS_PER_EVAL_SYM * evals / (kernel_ms / 1e3) / 1e12
         r["conv_B"] = {"achieved": round(b, 3), "frac": round(b / peak, 4),

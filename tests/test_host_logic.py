@@ -304,6 +304,16 @@ def test_bench_roofline_and_kernel_label(api):
     assert bench.recorded_traffic("mixed_split", 12345)[0] is None
     t, src = bench.recorded_traffic("mixed_split", 100000)
     assert t is not None and 1e6 < t < 1e8 and src.endswith(".md"), (t, src)
+    # the issue roofline: recorded warp instructions per launch over the kernel
+    # time, against 4 per clock per SM x 152 SMs x the clock
+    c, _ = bench.recorded_counters("mixed_split", 100000)
+    r = bench.roofline(api, "mixed_split", 100000, 4.715, peaks, 2070.0)
+    iss = r["issue"]
+    assert abs(iss["peak"] - 4 * 152 * 2070e6 / 1e9) < 1e-2
+    assert abs(iss["achieved"] - c["inst"] / 4.715e-3 / 1e9) < 1e-2
+    assert abs(iss["frac"] - iss["achieved"] / iss["peak"]) < 1e-4 and 0.5 < iss["frac"] <= 1.0
+    assert 20 < iss["warp_instructions_per_32_evaluations"] < 40
+    assert "issue" not in bench.roofline(api, "fp64", 100000, 91.0, peaks, 2070.0)
 
 
 def test_batched_each_validation(api):
