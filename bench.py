@@ -64,6 +64,8 @@ def parse():
                          "parser takes --n for an abbreviation of its own options")
     ap.add_argument("--no-paths", action="store_true", help="skip the secondary precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--kz-instances", type=int, default=512,
+                    help="instances of the kz / kz_sweep ensemble (512 as configured; fewer for a profile)")
     ap.add_argument("--workload", default="large", choices=["large", "kz", "kz_sweep"],
                     help="large: the N=1e5 headline; kz: the 512-instance ensemble (extra line); "
                          "kz_sweep: the same ensemble with a quench rate per instance")
@@ -551,7 +553,8 @@ def main_kz(args):
     import paper_2106_11143_gb300 as nb
     from paper_2106_11143_gb300 import workloads as W
     each = args.workload == "kz_sweep"
-    w = W.kz_quench_sweep() if each else W.kz_ensemble()
+    k = args.kz_instances
+    w = W.kz_quench_sweep(n_inst=k) if each else W.kz_ensemble(n_inst=k)
     off = w["offsets"]
     pairs = float(np.sum(np.diff(off).astype(np.float64) ** 2))
     prec = args.precision if args.precision in ("fp64", "df64") else "fp64"
