@@ -64,6 +64,8 @@ def parse():
                          "parser takes --n for an abbreviation of its own options")
     ap.add_argument("--no-paths", action="store_true", help="skip the secondary precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--precisions", default="fp64,df64,mixed,mixed_split",
+                    help="--profile-forces: the precisions, in launch order")
     ap.add_argument("--kz-instances", type=int, default=512,
                     help="instances of the kz / kz_sweep ensemble (512 as configured; fewer for a profile)")
     ap.add_argument("--workload", default="large", choices=["large", "kz", "kz_sweep"],
@@ -267,15 +269,15 @@ def _timing_read(lib):
 
 def run_e2e(nb, w, precision, steps, world, flush):
     """Same metric through the public API with host buffers: every step copies
-    the state (x, v, a) from pinned host memory to the device, runs nb_step,
-    and reads the state back into pinned host memory."""
+    the Verlet state (x, v, a: System.state, one packed device tensor) from
+    pinned host memory to the device in one copy, runs nb_step, and reads the
+    state back into pinned host memory in one copy."""
     import torch
     n = w["n"]
     par = nb.Params.from_phys(w["phys"], precision=precision)
     sysm = nb.System(w["pos"], w["vel"])
     nb.forces(par, sysm, total=True)
-    names = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")
-    host = {k: getattr(sysm, k).cpu().pin_memory() for k in names}
+    host = sysm.state.cpu().pin_memory()
     st = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     barrier(world)
@@ -283,19 +285,18 @@ def run_e2e(nb, w, precision, steps, world, flush):
     for k in range(steps):
         flush.zero_()
         ev[k][0].record(st)
-        for nm in names:
-            getattr(sysm, nm).copy_(host[nm], non_blocking=True)
+        sysm.state.copy_(host, non_blocking=True)
         nb.step(par, sysm, 1)
-        for nm in names:
-            host[nm].copy_(getattr(sysm, nm), non_blocking=True)
+        host.copy_(sysm.state, non_blocking=True)
         ev[k][1].record(st)
     torch.cuda.synchronize()
     barrier(world)
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ms = allreduce_max(ms, world)
-    nbytes = len(names) * n * 8
+    nbytes = host.numel() * host.element_size()
     return {"value": pair_rate(world, n * n, steps, ms), "unit": UNIT,
-            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "copies_per_step": {"h2d": 1, "d2h": 1}}
 
 
 def measure_peaks(nb, kinds=("dfma", "dadd", "ffma", "fadd", "mufu_rsq")):
@@ -342,6 +343,7 @@ def recorded_counters(precision, n):
     capture for this case or the kernel has changed since."""
     import glob
     want = kernel_source_sha()
+    out, src = {}, None
     for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
         for line in open(path):
             line = line.strip()
@@ -349,11 +351,11 @@ def recorded_counters(precision, n):
                 continue
             kv = dict(t.split("=", 1) for t in line.split()[1:])
             if kv.get("precision") == precision and int(kv.get("n", -1)) == n and kv.get("source") == want:
-                out = {"bytes": int(kv["bytes"])}
-                if "inst" in kv:
-                    out["inst"] = int(kv["inst"])
-                return out, os.path.basename(path)
-    return {}, None
+                for k in ("bytes", "inst", "fp64_inst"):  # the first summary naming a counter wins
+                    if k in kv and k not in out:
+                        out[k] = int(kv[k])
+                        src = src or os.path.basename(path)
+    return out, src
 
 
 def recorded_traffic(precision, n):
@@ -398,8 +400,27 @@ def roofline(nb, path, n, kernel_ms, peaks, sm_mhz):
         r["issue"] = {"achieved": round(iach, 2), "peak": round(ipeak, 2), "unit": "G warp-instructions/s",
                       "frac": round(iach / ipeak, 4),
                       "warp_instructions_per_32_evaluations": round(counters["inst"] / (evals / 32.0), 2),
-                      "source": "smsp__inst_executed.sum per launch from profiles/%s over the live kernel time; "
-                                "peak 4 per clock per SM x %d SMs x %.0f MHz" % (src, SM_COUNT, mhz)}
+                      "source": "smsp__inst_executed.sum per launch from profiles/ over the live kernel time; "
+                                "peak 4 per clock per SM x %d SMs x %.0f MHz" % (SM_COUNT, mhz)}
+    if "fp64_inst" in counters and "dfma" in peaks:
+        # the FP64 pipe, for the paths whose FP64 adds bind them (2 lanes per
+        # clock per SM: a warp instruction occupies it for 16 clocks)
+        lanes64 = peaks["dfma"]["lanes_per_clk_per_sm"]
+        fpeak = lanes64 * SM_COUNT * mhz * 1e6 / 1e12
+        fach = counters["fp64_inst"] * 32 / (kernel_ms / 1e3) / 1e12
+        r["fp64_pipe"] = {"achieved": round(fach, 4), "peak": round(fpeak, 4), "unit": "T lane-instructions/s",
+                          "frac": round(fach / fpeak, 4),
+                          "fp64_instructions_per_evaluation": round(counters["fp64_inst"] * 32 / evals, 3),
+                          "source": "smsp__inst_executed_pipe_fp64.sum per launch from profiles/ over the live "
+                                    "kernel time; peak the measured FP64 FMA rate %.3f lanes/clk/SM x %d SMs x "
+                                    "%.0f MHz" % (lanes64, SM_COUNT, mhz)}
+    units = [("FP64 FMA" if pipe == "dfma" else "FP32 FMA", r["frac"])]
+    if "issue" in r:
+        units.append(("issue", r["issue"]["frac"]))
+    if "fp64_pipe" in r:
+        units.append(("FP64 pipe", r["fp64_pipe"]["frac"]))
+    if len(units) > 1:
+        r["binding"] = max(units, key=lambda u: u[1])[0]
     if path == "fp64" and kname.startswith("k_pair_sym"):
         b = FP64_FLOPS_PER_EVAL_SYM * evals / (kernel_ms / 1e3) / 1e12
         r["conv_B"] = {"achieved": round(b, 3), "frac": round(b / peak, 4),
@@ -599,9 +620,9 @@ def main_kz(args):
 
 
 def profile_forces(args):
-    """Small case for ncu: a warm-up pass then a measured pass of nb_forces in
-    each precision (pair-kernel launches 1-4 warm up, 5-8 are the ones to capture:
-    fp64, df64, mixed, mixed_split)."""
+    """Case for ncu: a warm-up pass then a measured pass of nb_forces in each
+    precision of --precisions (default fp64, df64, mixed, mixed_split: pair-kernel
+    launches 1-4 warm up, 5-8 are the ones to capture)."""
     import torch
     torch.cuda.set_device(0)
     import paper_2106_11143_gb300 as nb
@@ -612,7 +633,7 @@ def profile_forces(args):
         for prec in ("fp64", "df64", "mixed", "mixed_split"):
             nb.set_tuning("symmetric", prec, 0, 1 << 40, 128, R=0)
     for _ in range(2):
-        for prec in ("fp64", "df64", "mixed", "mixed_split"):
+        for prec in args.precisions.split(","):
             nb.forces(nb.Params.from_phys(w["phys"], precision=prec), sysm)
     nb.sync_status()
     print("profile case done: n=%d" % w["n"])

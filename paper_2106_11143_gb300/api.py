@@ -179,30 +179,45 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+STATE_NAMES = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")
+
+
+def _packed_state(n, device):
+    """One (9, n_pad) float64 device tensor for the Verlet state, rows padded
+    to 32 doubles (256 B) so that every array starts aligned."""
+    return torch.zeros(len(STATE_NAMES), max(32, -(-n // 32) * 32), dtype=torch.float64, device=device)
+
+
 class System:
     """Ion state in device memory: SoA float64 tensors x, y, z, vx, vy, vz,
     ax, ay, az (length n), optional per-ion charges q and masses m (several
-    species), and the step counter.  The constructor copies pos/vel/q/m: the
-    library updates its own arrays in place, never the caller's."""
+    species), and the step counter.  The nine state arrays are rows of one
+    device tensor, `state` (9 x n_pad, rows padded to 256 B; the first n
+    columns are the ions), so the whole state moves to or from the host in one
+    copy.  The constructor copies pos/vel/q/m: the library updates its own
+    arrays in place, never the caller's."""
 
     def __init__(self, pos, vel=None, q=None, device="cuda", step=0, m=None):
         pos = _dev(pos, device).reshape(3, -1)
         n = pos.shape[1]
-        vel = torch.zeros(3, n, dtype=torch.float64, device=device) if vel is None else \
-            _dev(vel, device).reshape(3, n)
         self.n = n
-        self.x, self.y, self.z = (pos[k].clone() for k in range(3))
-        self.vx, self.vy, self.vz = (vel[k].clone() for k in range(3))
-        self.ax, self.ay, self.az = (torch.zeros(n, dtype=torch.float64, device=device)
-                                     for _ in range(3))
+        self._bind(_packed_state(n, device))
+        self.state[0:3, :n].copy_(pos)
+        if vel is not None:
+            self.state[3:6, :n].copy_(_dev(vel, device).reshape(3, n))
         self.q = None if q is None else _dev(q, device).reshape(n).clone()
         self.m = None if m is None else _dev(m, device).reshape(n).clone()
         self.step = int(step)
 
+    def _bind(self, state):
+        self.state = state
+        for k, name in enumerate(STATE_NAMES):
+            setattr(self, name, state[k, :self.n])
+
     def to_c(self):
         s = NbSystem()
         s.n = self.n
-        for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
+        for k in STATE_NAMES:
             setattr(s, k, _ptr(getattr(self, k)))
         s.q = _ptr(self.q)
         s.m = _ptr(self.m)
@@ -210,10 +225,12 @@ class System:
         return s
 
     def view(self, i0, i1):
-        """A System sharing memory with ions [i0, i1) of this one."""
+        """A System sharing memory with ions [i0, i1) of this one (its
+        `state` is the (9, i1 - i0) column slice)."""
         v = System.__new__(System)
         v.n = int(i1 - i0)
-        for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
+        v.state = self.state[:, i0:i1]
+        for k in STATE_NAMES:
             setattr(v, k, getattr(self, k)[i0:i1])
         v.q = None if self.q is None else self.q[i0:i1]
         v.m = None if self.m is None else self.m[i0:i1]
@@ -226,7 +243,7 @@ class System:
         system rebuilt from it continues bitwise as the original would: the
         acceleration is part of the state, and the step counter sets the time
         and the Langevin noise stream."""
-        d = {k: getattr(self, k).detach().cpu().clone() for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")}
+        d = {k: getattr(self, k).detach().cpu().clone() for k in STATE_NAMES}
         d["q"] = None if self.q is None else self.q.detach().cpu().clone()
         d["m"] = None if self.m is None else self.m.detach().cpu().clone()
         d["step"] = int(self.step)
@@ -237,11 +254,12 @@ class System:
         """A System holding the state saved by state_dict (copied to `device`)."""
         s = cls.__new__(cls)
         s.n = int(d["x"].numel())
-        for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az"):
+        s._bind(_packed_state(s.n, device))
+        for k in STATE_NAMES:
             t = d[k]
             if t.dtype != torch.float64 or t.numel() != s.n:
                 raise ValueError("state entry %s must be float64 of length %d" % (k, s.n))
-            setattr(s, k, t.to(device).clone())
+            getattr(s, k).copy_(t.reshape(s.n))
         s.q = None if d.get("q") is None else d["q"].to(device, torch.float64).clone()
         s.m = None if d.get("m") is None else d["m"].to(device, torch.float64).clone()
         s.step = int(d["step"])
@@ -258,7 +276,6 @@ class System:
 
 
 CKPT_MAGIC = b"NBCKPT1\n"
-_STATE = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")
 
 
 def save_checkpoint(path, system, params=None):
@@ -272,7 +289,7 @@ def save_checkpoint(path, system, params=None):
     import dataclasses
     import json
     import struct
-    names = list(_STATE) + [k for k in ("q", "m") if getattr(system, k) is not None]
+    names = list(STATE_NAMES) + [k for k in ("q", "m") if getattr(system, k) is not None]
     header = {"format": "nb-checkpoint", "version": 1, "n": int(system.n), "step": int(system.step),
               "arrays": names, "params": None if params is None else dataclasses.asdict(params)}
     if header["params"] is not None:
@@ -302,7 +319,7 @@ def load_checkpoint(path, device="cuda"):
             raise ValueError("unknown checkpoint format or version")
         n = int(header["n"])
         names = header["arrays"]
-        if not set(_STATE) <= set(names) or not set(names) <= set(_STATE) | {"q", "m"}:
+        if not set(STATE_NAMES) <= set(names) or not set(names) <= set(STATE_NAMES) | {"q", "m"}:
             raise ValueError("checkpoint arrays %s" % names)
         arrays = {}
         for k in names:
@@ -312,7 +329,7 @@ def load_checkpoint(path, device="cuda"):
             arrays[k] = torch.from_numpy(np.frombuffer(b, dtype="<f8").astype(np.float64))
         if f.read(1):
             raise ValueError("trailing bytes after the checkpoint arrays")
-    d = {k: arrays[k] for k in _STATE}
+    d = {k: arrays[k] for k in STATE_NAMES}
     d["q"], d["m"], d["step"] = arrays.get("q"), arrays.get("m"), header["step"]
     system = System.from_state(d, device=device)
     par = header["params"]

@@ -98,6 +98,33 @@ def test_system_state_round_trip(api, tmp_path):
         assert torch.equal(getattr(r, k), getattr(s, k)), k
 
 
+def test_system_packed_state(api):
+    """The nine state arrays are rows of System.state (rows padded to 32
+    doubles, 256 B): writes through either name are seen through the other,
+    rows start 256-byte aligned, and a view's state is the column slice."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(5)
+    for n in (1, 31, 32, 33, 100):
+        pos, vel = rng.standard_normal((3, n)), rng.standard_normal((3, n))
+        s = api.System(pos, vel, device="cpu")
+        assert s.state.shape == (9, max(32, -(-n // 32) * 32)) and s.state.is_contiguous()
+        for k, name in enumerate(api.STATE_NAMES):
+            row = getattr(s, name)
+            assert row.shape == (n,) and row.data_ptr() == s.state[k].data_ptr()
+            assert row.data_ptr() % 256 == (s.state.data_ptr() % 256)
+        assert np.array_equal(s.pos().numpy(), pos) and np.array_equal(s.vel().numpy(), vel)
+        assert torch.count_nonzero(s.acc()) == 0
+        s.state[7, :n] = 3.0
+        assert torch.all(s.ay == 3.0)
+        s.vz.fill_(-1.0)
+        assert torch.all(s.state[5, :n] == -1.0)
+        if n > 3:
+            v = s.view(1, 3)
+            assert v.state.shape == (9, 2) and torch.equal(v.state[0], s.x[1:3])
+            assert v.vz.data_ptr() == s.vz[1:].data_ptr()
+
+
 def test_checkpoint_file_round_trip(api, tmp_path):
     """save_checkpoint / load_checkpoint: the framework-free file keeps every
     array, the step counter and the parameters bit for bit, with and without
@@ -313,7 +340,19 @@ def test_bench_roofline_and_kernel_label(api):
     assert abs(iss["achieved"] - c["inst"] / 4.715e-3 / 1e9) < 1e-2
     assert abs(iss["frac"] - iss["achieved"] / iss["peak"]) < 1e-4 and 0.5 < iss["frac"] <= 1.0
     assert 20 < iss["warp_instructions_per_32_evaluations"] < 40
-    assert "issue" not in bench.roofline(api, "fp64", 100000, 91.0, peaks, 2070.0)
+    # every path at N = 1e5 has recorded counters, and the unit named as binding
+    # is the one with the largest fraction (FP64 pipe for the paths with FP64
+    # adds in the pair loop, issue for the split forms)
+    times = {"fp64": 90.98, "df64": 33.97, "mixed": 31.93, "mixed_split": 4.713, "mixed_split_rsq": 4.39}
+    want = {"fp64": "FP64 pipe", "df64": "FP64 pipe", "mixed": "FP64 pipe", "mixed_split": "issue",
+            "mixed_split_rsq": "issue"}
+    for prec, ms in times.items():
+        r = bench.roofline(api, prec, 100000, ms, peaks, 2070.0)
+        assert r["binding"] == want[prec], (prec, r.get("binding"))
+        fr = {"issue": r["issue"]["frac"], "FP64 pipe": r["fp64_pipe"]["frac"]}[r["binding"]]
+        assert 0.5 < fr <= 1.0, (prec, fr)
+    assert abs(bench.roofline(api, "fp64", 100000, 90.98, peaks, 2070.0)["fp64_pipe"]
+               ["fp64_instructions_per_evaluation"] - 10.26) < 0.05
 
 
 def test_batched_each_validation(api):
