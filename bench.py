@@ -183,8 +183,9 @@ def cpu_baseline(w, target_s=12.0, gpu_acc=None):
     same sample's oracle forces are the reference for each path's accuracy:
     gpu_acc maps a precision to the Coulomb accelerations (3, N) that nb_forces
     gave for the same positions; per path the largest conditioned error (the
-    gate's measure, |da_i| / sum_j |a_ij|) and the largest and 99th-percentile
-    plain relative error |da_i| / |a_i| over the sample."""
+    gate's measure, |da_i| / sum_j |a_ij|), the largest, 99th-percentile and
+    median plain relative error |da_i| / |a_i| and the global ||da|| / ||a||
+    over the sample."""
     import oracle
     p = oracle.make_params(**w["phys"])
     n = w["n"]
@@ -209,6 +210,8 @@ def cpu_baseline(w, target_s=12.0, gpu_acc=None):
             acc[prec] = {"max_conditioned": float("%.3g" % np.max(d / absf)), "gate": ACCURACY_GATE[prec],
                          "max_rel": float("%.3g" % np.max(rel)),
                          "p99_rel": float("%.3g" % np.percentile(rel, 99)),
+                         "median_rel": float("%.3g" % np.median(rel)),
+                         "global_rel": float("%.3g" % (np.sqrt(np.sum(d * d)) / np.sqrt(np.sum(mag * mag)))),
                          "ions_rel_above_gate": int(np.sum(rel > ACCURACY_GATE[prec]))}
         out["accuracy_vs_oracle"] = {"ions": s, "paths": acc}
     return out
