@@ -361,6 +361,26 @@ def recorded_counters(precision, n):
     return out, src
 
 
+def recorded_opmix(precision):
+    """FP64 lane-instructions per pair evaluation of the pair kernel in this
+    precision, by kind ({"dadd", "dfma", "dmul"}), from an `opmix:` line of
+    the summaries under profiles/ (SASS op counters of one ncu capture, which
+    take three passes, so they come from a case smaller than the bench's with
+    the same kernel configuration); {} when unrecorded or the kernel sources
+    have changed since."""
+    import glob
+    want = kernel_source_sha()
+    for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
+        for line in open(path):
+            line = line.strip()
+            if not line.startswith("opmix: "):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:])
+            if kv.get("precision") == precision and kv.get("source") == want:
+                return {k: float(kv[k]) for k in ("dadd", "dfma", "dmul") if k in kv}
+    return {}
+
+
 def recorded_traffic(precision, n):
     """DRAM bytes (read + write) per launch of the pair kernel and the
     summary they come from (recorded_counters); (None, None) if unrecorded."""
@@ -417,6 +437,21 @@ def roofline(nb, path, n, kernel_ms, peaks, sm_mhz):
                           "source": "smsp__inst_executed_pipe_fp64.sum per launch from profiles/ over the live "
                                     "kernel time; peak the measured FP64 FMA rate %.3f lanes/clk/SM x %d SMs x "
                                     "%.0f MHz" % (lanes64, SM_COUNT, mhz)}
+        # the pipe's attainable rate for this kernel's own mix of FP64 adds,
+        # FMAs and multiplies, each at its measured rate (an add retires at
+        # about 0.84 of an FMA's rate on this GPU)
+        mix = recorded_opmix(path)
+        kinds = [k for k in ("dadd", "dfma", "dmul") if mix.get(k, 0.0) > 0.0]
+        if kinds and all(k in peaks for k in kinds):
+            tot = sum(mix[k] for k in kinds)
+            lanes_mix = tot / sum(mix[k] / peaks[k]["lanes_per_clk_per_sm"] for k in kinds)
+            mpeak = lanes_mix * SM_COUNT * mhz * 1e6 / 1e12
+            r["fp64_pipe"]["mix"] = {k: mix[k] for k in kinds}
+            r["fp64_pipe"]["mix_ceiling"] = round(mpeak, 4)
+            r["fp64_pipe"]["frac_of_mix_ceiling"] = round(fach / mpeak, 4)
+            r["fp64_pipe"]["mix_note"] = ("ceiling = the kernel's FP64 lane-instructions per evaluation by kind "
+                                          "(opmix, profiles/) at the measured rate of each kind: %.3f lanes/clk/SM"
+                                          % lanes_mix)
     units = [("FP64 FMA" if pipe == "dfma" else "FP32 FMA", r["frac"])]
     if "issue" in r:
         units.append(("issue", r["issue"]["frac"]))
@@ -449,7 +484,7 @@ def main_ours(args):
     w = W.cloud_large(n=args.n)
     n = w["n"]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    peaks = measure_peaks(nb, ("dfma", "ffma"))
+    peaks = measure_peaks(nb, ("dfma", "dadd", "ffma"))
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     head = run_path(nb, w, args.precision, args.steps, args.warmup, world, flush, clocks)
     ms = allreduce_max(head["ms"], world)

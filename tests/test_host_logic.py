@@ -353,6 +353,16 @@ def test_bench_roofline_and_kernel_label(api):
         assert 0.5 < fr <= 1.0, (prec, fr)
     assert abs(bench.roofline(api, "fp64", 100000, 90.98, peaks, 2070.0)["fp64_pipe"]
                ["fp64_instructions_per_evaluation"] - 10.26) < 0.05
+    # with a measured add rate, each FP64-bound path's fraction of the ceiling
+    # its own mix of adds and FMAs allows
+    peaks3 = dict(peaks, dadd={"lanes_per_clk_per_sm": 1.684, "sm_mhz": 2070.0})
+    for prec in ("fp64", "df64", "mixed"):
+        fp = bench.roofline(api, prec, 100000, times[prec], peaks3, 2070.0)["fp64_pipe"]
+        mix = bench.recorded_opmix(prec)
+        lanes = sum(mix.values()) / sum(v / {"dadd": 1.684, "dfma": 2.0}[k] for k, v in mix.items() if v)
+        assert abs(fp["mix_ceiling"] - lanes * 152 * 2070e6 / 1e12) < 1e-3, prec
+        assert 0.85 < fp["frac_of_mix_ceiling"] <= 1.05, (prec, fp["frac_of_mix_ceiling"])
+    assert "mix_ceiling" not in bench.roofline(api, "fp64", 100000, 90.98, peaks, 2070.0)["fp64_pipe"]
 
 
 def test_batched_each_validation(api):
