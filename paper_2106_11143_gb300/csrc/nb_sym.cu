@@ -385,8 +385,12 @@ __device__ __forceinline__ void sym_stage(SD4 *dst, int i, int BI, int64_t g, in
   dst[i] = e;
 }
 
+// Register budgets: fp64 two 256-thread blocks per SM; the split path with
+// two P-ions per lane three blocks, the count its shared memory allows (up
+// to 80 registers; left to itself the compiler stays at 64, 0.3 % slower at
+// N = 1e5 and 2 % at N = 16384).
 template <int MODE, bool QARR, bool P2, int NT, bool INPLACE>
-__global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_sym(int64_t n, int nbk, int G,
+__global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : (P2 ? 768 / NT : 0)) k_pair_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ y,
                                                          const double *__restrict__ z,
