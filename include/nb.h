@@ -299,9 +299,9 @@ nb_status nb_step_batched(const nb_params *params, int32_t n_inst, const int64_t
  * k's time is per_inst[k].t0 + step * per_inst[k].dt.
  * The library keeps a device copy of the table per (device, stream) and
  * copies it again only when the contents differ from the stream's previous
- * call.  That copy waits for the stream's earlier work (which may still
- * read the old table), so such a call can block the host; the call returns
- * once the host array has been read, so the caller may reuse it at once.  A graph capture records the launch, which reads the
+ * call.  That copy is ordered on the stream after its earlier work (which
+ * may still read the old table), and the call returns once the host array
+ * has been read, so the caller may reuse it at once.  A graph capture records the launch, which reads the
  * stream's table when replayed: capture only after an uncaptured call with
  * the same per_inst (a capture with other contents fails with NB_EINVAL,
  * and a later uncaptured call with other contents changes what earlier

@@ -851,8 +851,9 @@ nb_status nb_step_batched_each(const nb_params *per_inst, int32_t n_inst, const 
     }
     a->ptab_stage.resize(n_inst);
     for (int k = 0; k < n_inst; ++k) a->ptab_stage[k] = to_phys(&per_inst[k]);
-    // pageable source: the call returns once the bytes are staged, after the
-    // stream's earlier work (which may read the old table) has finished
+    // pageable source: the call returns once the bytes are staged; the copy
+    // to the device is ordered after the stream's earlier work, which may
+    // still read the old table
     NB_CUDA_TRY(cudaMemcpyAsync(a->ptab, a->ptab_stage.data(), n_inst * sizeof(Phys),
                                 cudaMemcpyHostToDevice, st));
     a->ptab_src.assign(per_inst, per_inst + n_inst);
