@@ -401,3 +401,20 @@ def test_batched_each_validation(api):
     assert sysm.step == 5
     assert call(tab, n, offp) == 0 and sysm.step == 8
     assert L.nb_step_batched_each(None, 0, None, C.byref(sysm), 2, None) == 0 and sysm.step == 10
+
+
+def test_workloads_have_no_coincident_ions():
+    """Reading C1: the oracle skips the self pair by index, the kernels give a
+    pair at r = 0 (without softening) no force; the two agree as long as no
+    two distinct ions coincide, so every configured workload (each ensemble
+    instance on its own) is checked for that."""
+    import time
+    t0 = time.time()
+    singles = [W.cloud_harmonic_1024(), W.cloud_rf_16384(), W.cloud_large(), W.adjoint_cloud()]
+    for w in singles:
+        assert W.min_pair_distance(w["pos"]) > 0.0, w["name"]
+    for w in (W.kz_ensemble(), W.kz_quench_sweep()):
+        off = w["offsets"]
+        for k in range(len(off) - 1):
+            assert W.min_pair_distance(w["pos"][:, off[k]:off[k + 1]]) > 0.0, (w["name"], k)
+    assert time.time() - t0 < 120
