@@ -471,6 +471,19 @@ nb_status nb_pipe_probe(int32_t kind, int64_t iters, double out[3], void *stream
  * NB_OK, NB_ENONFINITE or NB_ETIMEOUT (or NB_ECUDA if the stream failed). */
 nb_status nb_sync_status(void *stream);
 
+/* Probe of the bounded wait behind the half-pair kernels' round-ordered
+ * output (one item waits until the items of the previous round that touched
+ * its blocks have committed): one device thread publishes `committed` rounds
+ * for a block, with a release store, then waits with acquire loads until the
+ * block has committed `round`, as an item does.  *ok (host) receives 1 if
+ * the wait succeeded.  A wait for a round nobody commits (round > committed)
+ * spins until its limit (one to a few seconds), sets the stream's device
+ * error word, so that nb_sync_status returns NB_ETIMEOUT, and ends normally:
+ * the failure path of every bounded wait, without a GPU fault.  Uses the
+ * stream's scratch; synchronises the stream.  NB_EINVAL for a NULL ok or a
+ * negative argument.                                                        */
+nb_status nb_sym_wait_probe(int32_t committed, int32_t round, int32_t *ok, void *stream);
+
 /* Frees all library scratch on every device (after synchronising them). */
 nb_status nb_release(void);
 

@@ -14,7 +14,7 @@ _API = ("Params", "System", "forces", "step", "energy", "forces_vjp", "sync_stat
         "step_batched", "step_batched_each", "init_batched", "plan_batched", "set_tuning",
         "trajectory_loss", "TrajectoryLoss", "lib", "NBError", "PRECISIONS", "release", "rinv3_probe", "rsqrt_seed_probe", "save_checkpoint",
         "load_checkpoint", "plan_info", "pipe_probe", "sym_schedule", "forces_range", "step_range_drift",
-        "step_range_kick")
+        "step_range_kick", "sym_wait_probe")
 
 
 def __getattr__(name):

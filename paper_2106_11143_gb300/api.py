@@ -98,12 +98,13 @@ def lib():
         L.nb_step_range_kick.argtypes = [P, S, C.c_int64, C.c_int64, V]
         I32P = C.POINTER(C.c_int32)
         L.nb_sym_schedule.argtypes = [C.c_int32, I32P, I32P, I32P]
+        L.nb_sym_wait_probe.argtypes = [C.c_int32, C.c_int32, I32P, V]
         for f in ("nb_forces", "nb_step", "nb_energy", "nb_forces_vjp", "nb_sync_status",
                   "nb_release", "nb_timing_enable", "nb_timing_read", "nb_step_batched", "nb_step_batched_each",
                   "nb_plan_batched", "nb_set_tuning", "nb_energy_noalloc", "nb_traj_forward",
                   "nb_traj_backward", "nb_rinv3_probe", "nb_rsqrt_seed_probe", "nb_plan_info",
                   "nb_pipe_probe", "nb_sym_schedule", "nb_forces_range", "nb_step_range_drift",
-                  "nb_step_range_kick"):
+                  "nb_step_range_kick", "nb_sym_wait_probe"):
             getattr(L, f).restype = C.c_int
         _LIB = L
     return _LIB
@@ -459,6 +460,16 @@ def plan_batched(offsets, n_bins):
 
 PLAN_KINDS = {"force": 0, "potential": 1, "vjp": 2}
 PLAN_FIELDS = ("block", "R", "jchunk", "n_it", "n_jc", "symmetric", "G", "single_block")
+
+
+def sym_wait_probe(committed, round_, stream=None):
+    """nb_sym_wait_probe: one bounded wait of the half-pair kernels' output
+    order; True if block 0, with `committed` rounds published, reached
+    `round_` (a wait that runs out leaves NB_ETIMEOUT for sync_status)."""
+    ok = C.c_int32()
+    _check(lib().nb_sym_wait_probe(int(committed), int(round_), C.byref(ok), _stream(stream)),
+           "nb_sym_wait_probe")
+    return bool(ok.value)
 
 
 def plan_info(kind, precision, n):

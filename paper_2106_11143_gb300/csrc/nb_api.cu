@@ -22,6 +22,8 @@ namespace nb {
 
 cudaError_t launch_chunk_sum1(int64_t n, const double *part, int n_jc, double scale, double *out,
                               cudaStream_t st);
+// Bounded-wait probe (nb_probe.cu): sync holds 2 ints, ok 1 int, device.
+cudaError_t launch_sym_wait_probe(int *sync, int committed, int round, unsigned *err, int *ok, cudaStream_t st);
 
 namespace {
 thread_local std::string g_last_error;
@@ -1119,6 +1121,23 @@ extern "C" nb_status nb_traj_backward(const nb_params *params, const nb_system *
                              1, 0, st));
   NB_CUDA_TRY(launch_adj_out(n, xb.data(), vb.data(), wacc.data(), gscale, gx0, gv0, gomega, bpart, st));
   count_launches(4);
+  return NB_OK;
+}
+
+nb_status nb_sym_wait_probe(int32_t committed, int32_t round, int32_t *ok, void *stream) {
+  if (!ok) return fail(NB_EINVAL, "ok is NULL");
+  if (committed < 0 || round < 0) return fail(NB_EINVAL, "committed and round must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena *a = nullptr;
+  NB_TRY(get_arena(st, 256, &a));
+  int *sync = reinterpret_cast<int *>(a->buf);
+  int *dev_ok = sync + 2;
+  NB_CUDA_TRY(launch_sym_wait_probe(sync, committed, round, a->err, dev_ok, st));
+  count_launches(1);
+  int h = 0;
+  NB_CUDA_TRY(cudaMemcpyAsync(&h, dev_ok, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NB_CUDA_TRY(cudaStreamSynchronize(st));
+  *ok = h;
   return NB_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "nb_common.cuh"
+#include "nb_symsched.cuh"
 
 namespace nb {
 
@@ -228,6 +229,26 @@ static cudaError_t pipe_best(int sms, int64_t iters, unsigned long long *clk, do
   out[1] = m[k];
   out[2] = k;
   return cudaSuccess;
+}
+
+// Probe of the half-pair kernels' bounded wait: one thread publishes
+// `committed` rounds for block 0 (a release store, as sym_commit does) and
+// then waits, as sym_commit does, until block 0 has committed `round`.  A
+// wait for a round nobody commits runs out its spin limit, sets
+// ERR_TIMEOUT in the error word and ends normally.
+__global__ void k_sym_wait_probe(int *sync, int committed, int round, unsigned *err, int *ok) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st_release(sync + 1, committed);
+  const bool done = sym_wait(sync, 0, round, err);
+  if (!done) atomicOr(err, ERR_TIMEOUT);
+  ok[0] = done ? 1 : 0;
+}
+
+cudaError_t launch_sym_wait_probe(int *sync, int committed, int round, unsigned *err, int *ok, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(sync, 0, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_sym_wait_probe<<<1, 32, 0, st>>>(sync, committed, round, err, ok);
+  return cudaGetLastError();
 }
 
 }  // namespace nb
