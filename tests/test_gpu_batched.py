@@ -375,3 +375,31 @@ def test_batched_each_table_reuse_and_graph_capture(nb):
     torch.cuda.synchronize()
     for t in ("x", "vz", "ay"):
         assert torch.equal(getattr(eager, t), getattr(sysm, t)), t
+
+
+def test_batched_each_at_the_instance_limit(nb):
+    """1024 instances (the limit; the device table's size) of 1-4 ions: a
+    table of the shared parameters with instance words instance + k gives
+    bitwise the shared call, and 1025 instances are refused."""
+    rng = np.random.default_rng(24)
+    sizes = rng.integers(1, 5, size=1024)
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    w = W.kz_ensemble(n_inst=2, n_min=1, n_max=2, seed=24)
+    phys = dict(w["phys"], instance=7)
+    pos = np.zeros((3, off[-1]))
+    for k, m in enumerate(sizes):
+        pos[2, off[k]:off[k + 1]] = W.chain_positions(int(m), 2 * math.pi * 100e3)
+    vel = W.thermal_velocities(int(off[-1]), 0.5e-3, W.MASS_40U, rng)
+    shared = run_gpu(nb, phys, off, pos, vel, 6)
+    pars = [nb.Params.from_phys(phys, instance=7 + k) for k in range(len(sizes))]
+    sysm = nb.System(pos, vel)
+    nb.init_batched(pars[0], sysm, off)
+    nb.step_batched_each(pars, sysm, off, 6)
+    nb.sync_status()
+    for t in ("x", "vz", "az"):
+        assert torch.equal(getattr(shared, t), getattr(sysm, t)), t
+    off2 = np.concatenate([off, [off[-1] + 1]])
+    big = nb.System(np.zeros((3, int(off2[-1]))), np.zeros((3, int(off2[-1]))))
+    with pytest.raises(nb.NBError):
+        nb.step_batched_each(pars + pars[:1], big, off2, 1)
