@@ -587,3 +587,57 @@ def test_concurrent_host_threads_own_streams(nb):
         nb.sync_status(streams[k])
         for t in ("x", "vy", "az"):
             assert torch.equal(getattr(serial[k], t), getattr(conc[k], t)), (k, t)
+
+
+@pytest.mark.parametrize("n", [300, 3000])
+@pytest.mark.parametrize("precision", ["fp64", "df64", "mixed", "mixed_split"])
+def test_coincident_ions_contribute_nothing(nb, orc, precision, n):
+    """Reading C1: two distinct ions A and B at the same position (no
+    softening) exert no force on each other; every other pair is as usual.
+    That equals the system with B merged into A (charge q_A + q_B), which the
+    oracle can evaluate: each other ion's acceleration is the merged system's,
+    and A's and B's are the merged ion's scaled by q_A / (q_A + q_B) and
+    q_B / (q_A + q_B).  The VJP likewise, with lam_B = lam_A.  One-sided
+    (n = 300) and half-pair (n = 3000) kernels; A and B at ragged places."""
+    rng = np.random.default_rng(n + 11)
+    pos, _ = W.random_cloud(n, seed=n + 11)
+    q = W.E_CHARGE * rng.choice([1.0, 2.0], size=n)
+    a, b = 5, n - 7
+    pos[:, b] = pos[:, a]
+    lam = rng.standard_normal((3, n))
+    lam[:, b] = lam[:, a]
+    keep = np.array([i for i in range(n) if i != b])
+    qm = q[keep].copy()
+    ia = int(np.where(keep == a)[0][0])
+    qm[ia] = q[a] + q[b]
+    phys = W.phys(omega=(6e6, 5e6, 1.2e6))
+    p = oparams(orc, phys)
+    ax, ay, az, _, absf = orc.coulomb(p, *pos[:, keep], q=qm, want_absf=True)
+    merged = np.stack([ax, ay, az])
+    ref = np.empty((3, n))
+    ref[:, keep] = merged
+    ref[:, a] = merged[:, ia] * (q[a] / qm[ia])
+    ref[:, b] = merged[:, ia] * (q[b] / qm[ia])
+    cond = np.empty(n)
+    cond[keep] = absf
+    cond[a] = absf[ia] * q[a] / qm[ia]
+    cond[b] = absf[ia] * q[b] / qm[ia]
+    par = nb.Params.from_phys(phys, precision=precision)
+    s = nb.System(pos, q=q)
+    nb.forces(par, s)
+    nb.sync_status()
+    got = s.acc().cpu().numpy()
+    assert np.all(np.isfinite(got))
+    err = np.max(np.sqrt(np.sum((got - ref) ** 2, axis=0)) / cond)
+    gate = 1e-12 if precision in ("fp64", "df64") else 1e-6
+    print("%s n=%d: conditioned error %.3g" % (precision, n, err))
+    assert err <= gate
+    if precision == "fp64":
+        gv = nb.forces_vjp(par, nb.System(pos, q=q), lam).cpu().numpy()
+        vm = np.stack(orc.forces_vjp(p, 0.0, *pos[:, keep], *lam[:, keep], q=qm))
+        vref = np.empty((3, n))
+        vref[:, keep] = vm
+        vref[:, a] = vm[:, ia] * (q[a] / qm[ia])
+        vref[:, b] = vm[:, ia] * (q[b] / qm[ia])
+        assert np.all(np.isfinite(gv))
+        assert np.max(np.abs(gv - vref)) <= 1e-11 * np.max(np.abs(vref))
