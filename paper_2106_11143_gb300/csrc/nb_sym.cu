@@ -5,7 +5,9 @@
 //
 // The split and literal mixed precisions use it too (FP32 pair arithmetic
 // with per-step FP32 partials added into FP64, or into double-float sums on
-// the FP32 pipe for split).
+// the FP32 pipe for split).  In the split path's large blocks (G >= 16) a
+// lane holds four P-ions, whose arithmetic runs as two packed pairs of FP32
+// (.f32x2) instructions: sym_offdiag_split4.
 //
 // Ions are grouped in blocks of BI = 32 G ions (G tiles of one warp).  One
 // CTA handles one work item, a block pair (P, Q) with P <= Q, drawn from the
@@ -210,25 +212,6 @@ __device__ __forceinline__ void sym_step_split(const float4 &ph, const float4 &p
   }
 }
 
-// The same with two P-ions per lane (a 64-ion P-tile): one pair of Q loads
-// and one round of accumulator shuffles serve two pair evaluations, which
-// are independent up to their adds into b.
-template <bool W, bool SEED>
-__device__ __forceinline__ void sym_step_split2(const float4 &h1, const float4 &l1, const float4 &h2,
-                                                const float4 &l2, const float4 *qhi, const float4 *qlo,
-                                                float soft2f, int lane, float a1[3], float a2[3],
-                                                float b[3]) {
-#pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    const float4 qh = qhi[r], ql = qlo[r];
-    split_eval<W, SEED>(h1, l1, qh, ql, soft2f, a1, b);
-    split_eval<W, SEED>(h2, l2, qh, ql, soft2f, a2, b);
-    b[0] = shfl_next(b[0], lane);
-    b[1] = shfl_next(b[1], lane);
-    b[2] = shfl_next(b[2], lane);
-  }
-}
-
 // Where an item keeps the finished sums of its Q block (and a diagonal item
 // its block's sums): in the Q-tile's own 1 KB of staged positions, which only
 // the warp that owns that Q-tile reads, so it is free once that warp is done
@@ -247,18 +230,124 @@ __device__ __forceinline__ void df_add(float &h, float &l, float v) {
   l += e;
 }
 
-// Off-diagonal item, split precision with 64-ion P-tiles (G >= 16, so that
-// the G/2 P-tiles outnumber the warps): warp w takes the Q-tiles qs = w,
-// w + 8, ...; at step k it holds P-tile (qs + k) mod G/2, distinct across
-// warps because all warps advance in lockstep through the barriers.  The
-// P sums are double-floats in shared memory (accPf: [3][BI] hi, then
-// [3][BI] lo), the Q sums double-floats in registers, stored as FP64 (qsum)
-// once the warp is done with its Q-tile.
+// Packed FP32 pairs (.f32x2): one instruction applies the same IEEE
+// operation, rounded to nearest, to both halves.  It takes one issue slot and
+// two cycles of the FMA pipe, so an issue-bound loop gains where its FMA pipe
+// has room; a pair {x, x} built from one register feeds it without an
+// instruction of its own.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_split(f2 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// sym_step_split4 with the four P-ions' arithmetic in two packed pairs
+// (ions 0-1 and 2-3): two independent chains per lane; per ion the same
+// operations in the same order as split_eval, and the Q sum takes the ions'
+// terms in the order 0, 1, 2, 3.
+template <bool W, bool SEED>
+__device__ __forceinline__ void sym_step_split4_packed(const float4 *h, const float4 *l, const float4 *qhi,
+                                                       const float4 *qlo, float soft2f, int lane, float a[4][3],
+                                                       float b[3]) {
+  f2 phx[2], phy[2], phz[2], plx[2], ply[2], plz[2], pw[2], ax[2], ay[2], az[2];
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    phx[v] = f2_pack(h[2 * v].x, h[2 * v + 1].x);
+    phy[v] = f2_pack(h[2 * v].y, h[2 * v + 1].y);
+    phz[v] = f2_pack(h[2 * v].z, h[2 * v + 1].z);
+    plx[v] = f2_pack(l[2 * v].x, l[2 * v + 1].x);
+    ply[v] = f2_pack(l[2 * v].y, l[2 * v + 1].y);
+    plz[v] = f2_pack(l[2 * v].z, l[2 * v + 1].z);
+    pw[v] = f2_pack(h[2 * v].w, h[2 * v + 1].w);
+    ax[v] = f2_pack(a[2 * v][0], a[2 * v + 1][0]);
+    ay[v] = f2_pack(a[2 * v][1], a[2 * v + 1][1]);
+    az[v] = f2_pack(a[2 * v][2], a[2 * v + 1][2]);
+  }
+  const f2 s2 = f2_pack(soft2f, soft2f), m15 = f2_pack(-1.5f, -1.5f), p15 = f2_pack(1.5f, 1.5f);
+#pragma unroll(SEED ? 32 : 16)
+  for (int r = 0; r < 32; ++r) {
+    const float4 qh = qhi[r], ql = qlo[r];
+    const f2 qhx = f2_pack(qh.x, qh.x), qhy = f2_pack(qh.y, qh.y), qhz = f2_pack(qh.z, qh.z);
+    const f2 qlx = f2_pack(ql.x, ql.x), qly = f2_pack(ql.y, ql.y), qlz = f2_pack(ql.z, ql.z);
+    float dxs[4], dys[4], dzs[4], sqs[4];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const f2 dx = f2_add(f2_sub(phx[v], qhx), f2_sub(plx[v], qlx));
+      const f2 dy = f2_add(f2_sub(phy[v], qhy), f2_sub(ply[v], qly));
+      const f2 dz = f2_add(f2_sub(phz[v], qhz), f2_sub(plz[v], qlz));
+      const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, s2)));
+      float r2a, r2b, ya, yb;
+      f2_split(r2, r2a, r2b);
+      asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ya) : "f"(r2a));
+      asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yb) : "f"(r2b));
+      const f2 y = f2_pack(fminf(ya, F32_YMAX), fminf(yb, F32_YMAX));
+      const f2 y2 = f2_mul(y, y);
+      const f2 y3 = f2_mul(y2, y);
+      const f2 sv = SEED ? y3 : f2_fma(y3, f2_fma(f2_mul(m15, r2), y2, p15), y3);
+      const f2 sp = W ? f2_mul(sv, f2_pack(qh.w, qh.w)) : sv;
+      const f2 sq = W ? f2_mul(sv, pw[v]) : sv;
+      ax[v] = f2_fma(dx, sp, ax[v]);
+      ay[v] = f2_fma(dy, sp, ay[v]);
+      az[v] = f2_fma(dz, sp, az[v]);
+      f2_split(dx, dxs[2 * v], dxs[2 * v + 1]);
+      f2_split(dy, dys[2 * v], dys[2 * v + 1]);
+      f2_split(dz, dzs[2 * v], dzs[2 * v + 1]);
+      f2_split(sq, sqs[2 * v], sqs[2 * v + 1]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      b[0] = fmaf(-dxs[u], sqs[u], b[0]);
+      b[1] = fmaf(-dys[u], sqs[u], b[1]);
+      b[2] = fmaf(-dzs[u], sqs[u], b[2]);
+    }
+    b[0] = shfl_next(b[0], lane);
+    b[1] = shfl_next(b[1], lane);
+    b[2] = shfl_next(b[2], lane);
+  }
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    f2_split(ax[v], a[2 * v][0], a[2 * v + 1][0]);
+    f2_split(ay[v], a[2 * v][1], a[2 * v + 1][1]);
+    f2_split(az[v], a[2 * v][2], a[2 * v + 1][2]);
+  }
+}
+
+// Off-diagonal item, split precision with 128-ion P-tiles: GP = G/4 P-tiles
+// and NW = 2 GP warps (8 warps for 512-ion blocks, 16 for 1024).  At step k
+// warp w holds P-tile (qs + k) mod GP, which it shares with warp w +- GP; the
+// two keep their P sums in separate double-float copies (accPf: [2][2][3][BI]
+// floats, copy w / GP), added in copy order at the end, so no two warps ever
+// update one word.
 template <bool W, int NW, bool SEED>
-__device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, SD4 *posQ, float *accPf, int G, int BI,
+__device__ __forceinline__ void sym_offdiag_split4(const SD4 *posP, SD4 *posQ, float *accPf, int G, int BI,
                                                    double soft2) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int GP = G >> 1;
+  const int GP = G >> 2;
+  float *acc = accPf + (warp / GP) * 6 * BI;
   const float4 *fP = reinterpret_cast<const float4 *>(posP);
   const float4 *fQ = reinterpret_cast<const float4 *>(posQ);
   for (int qs = warp; qs < G; qs += NW) {
@@ -266,17 +355,25 @@ __device__ __forceinline__ void sym_offdiag_split2(const SD4 *posP, SD4 *posQ, f
     const float4 *qhi = fQ + qs * 64 + lane, *qlo = fQ + 2 * BI + qs * 64 + lane;
     for (int k = 0; k < GP; ++k) {
       const int pt = (qs + k) % GP;
-      __syncthreads();  // all warps are at step k: their P-tiles are distinct
-      const int i1 = pt * 64 + lane, i2 = i1 + 32;
-      float a1[3] = {0, 0, 0}, a2[3] = {0, 0, 0}, b[3] = {0, 0, 0};
-      sym_step_split2<W, SEED>(fP[i1], fP[BI + i1], fP[i2], fP[BI + i2], qhi, qlo, (float)soft2, lane, a1,
-                               a2, b);
+      __syncthreads();  // all warps are at step k
+      float4 h[4], l[4];
+      float a[4][3], b[3] = {0, 0, 0};
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        df_add(accPf[c * BI + i1], accPf[(3 + c) * BI + i1], a1[c]);
-        df_add(accPf[c * BI + i2], accPf[(3 + c) * BI + i2], a2[c]);
-        df_add(qh[c], ql[c], b[c]);
+      for (int u = 0; u < 4; ++u) {
+        const int i = pt * 128 + 32 * u + lane;
+        h[u] = fP[i];
+        l[u] = fP[BI + i];
+        a[u][0] = a[u][1] = a[u][2] = 0.0f;
       }
+      sym_step_split4_packed<W, SEED>(h, l, qhi, qlo, (float)soft2, lane, a, b);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = pt * 128 + 32 * u + lane;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) df_add(acc[c * BI + i], acc[(3 + c) * BI + i], a[u][c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) df_add(qh[c], ql[c], b[c]);
     }
     __syncwarp();  // every lane is done reading the tile
 #pragma unroll
@@ -385,12 +482,11 @@ __device__ __forceinline__ void sym_stage(SD4 *dst, int i, int BI, int64_t g, in
   dst[i] = e;
 }
 
-// Register budgets: fp64 two 256-thread blocks per SM; the split path with
-// two P-ions per lane three blocks, the count its shared memory allows (up
-// to 80 registers; left to itself the compiler stays at 64, 0.3 % slower at
-// N = 1e5 and 2 % at N = 16384).
+// Register budgets: fp64 two 256-thread blocks per SM; the split path's
+// packed four-ion step is left to the compiler (about 100 registers, two
+// blocks per SM: capped at three blocks it spills and runs slower).
 template <int MODE, bool QARR, bool P2, int NT, bool INPLACE>
-__global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : (P2 ? 768 / NT : 0)) k_pair_sym(int64_t n, int nbk, int G,
+__global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ y,
                                                          const double *__restrict__ z,
@@ -414,6 +510,11 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : (P2 ? 768 /
     accP[i] = 0.0;
     accP[BI + i] = 0.0;
     accP[2 * BI + i] = 0.0;
+    if (P2) {  // the second copy of the P sums
+      accP[3 * BI + i] = 0.0;
+      accP[4 * BI + i] = 0.0;
+      accP[5 * BI + i] = 0.0;
+    }
   }
   float s2h = 0.0f, s2l = 0.0f;
   if (MODE == MODE_DF64) split_f64(soft2, s2h, s2l);
@@ -516,16 +617,24 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : (P2 ? 768 /
   float *accPf = reinterpret_cast<float *>(accP);
   if (P2) {
     if (weighted)
-      sym_offdiag_split2<true, NT / 32, MODE == MODE_SPLIT_RSQ>(posP, posQ, accPf, G, BI, soft2);
+      sym_offdiag_split4<true, NT / 32, MODE == MODE_SPLIT_RSQ>(posP, posQ, accPf, G, BI, soft2);
     else
-      sym_offdiag_split2<false, NT / 32, MODE == MODE_SPLIT_RSQ>(posP, posQ, accPf, G, BI, soft2);
+      sym_offdiag_split4<false, NT / 32, MODE == MODE_SPLIT_RSQ>(posP, posQ, accPf, G, BI, soft2);
   } else if (weighted) {
     sym_offdiag<MODE, true, NT / 32>(posP, posQ, accP, G, BI, soft2, s2h, s2l);
   } else {
     sym_offdiag<MODE, false, NT / 32>(posP, posQ, accP, G, BI, soft2, s2h, s2l);
   }
   __syncthreads();
-  if (split_like(MODE))
+  if (P2)  // two copies of the P sums, added in copy order
+    sym_output<NT>(inplace, it, n, p0, np, q0, nq, acc, sync, err,
+                   [&](int c, int i) {
+                     return ((f32_to_f64(accPf[c * BI + i]) + f32_to_f64(accPf[(3 + c) * BI + i])) +
+                             f32_to_f64(accPf[(6 + c) * BI + i])) +
+                            f32_to_f64(accPf[(9 + c) * BI + i]);
+                   },
+                   [&](int c, int i) { return qsum(posQ, c, i); });
+  else if (split_like(MODE))
     sym_output<NT>(inplace, it, n, p0, np, q0, nq, acc, sync, err,
                    [&](int c, int i) { return f32_to_f64(accPf[c * BI + i]) + f32_to_f64(accPf[(3 + c) * BI + i]); },
                    [&](int c, int i) { return qsum(posQ, c, i); });
@@ -747,7 +856,9 @@ static cudaError_t launch_sym_rot(int64_t n, int nbk, const double *x, const dou
 }
 
 size_t sym_smem_bytes(int G, int mode) {
-  return (size_t)32 * G * ((split_like(mode) ? 3 : 2) * sizeof(SD4) + 3 * sizeof(double));
+  // the split path with four P-ions per lane (G >= 16) keeps two copies of the P sums
+  const int acc = (split_like(mode) && G >= 16) ? 6 : 3;
+  return (size_t)32 * G * ((split_like(mode) ? 3 : 2) * sizeof(SD4) + acc * sizeof(double));
 }
 
 template <int MODE, bool P2, int NT>
