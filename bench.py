@@ -361,13 +361,17 @@ def recorded_counters(precision, n):
     return out, src
 
 
+OPMIX_KINDS = ("dadd", "dfma", "dmul", "fadd", "ffma", "fmul", "fadd2", "ffma2", "fmul2")
+
+
 def recorded_opmix(precision):
-    """FP64 lane-instructions per pair evaluation of the pair kernel in this
-    precision, by kind ({"dadd", "dfma", "dmul"}), from an `opmix:` line of
-    the summaries under profiles/ (SASS op counters of one ncu capture, which
-    take three passes, so they come from a case smaller than the bench's with
-    the same kernel configuration); {} when unrecorded or the kernel sources
-    have changed since."""
+    """Lane-instructions per pair evaluation of the pair kernel in this
+    precision, by kind (FP64 "dadd", "dfma", "dmul"; FP32 "fadd", "ffma",
+    "fmul" and the packed "fadd2", "ffma2", "fmul2"), from an `opmix:` line
+    of the summaries under profiles/ (SASS op counters of one ncu capture,
+    which take three passes, so they come from a case smaller than the
+    bench's with the same kernel configuration); {} when unrecorded or the
+    kernel sources have changed since."""
     import glob
     want = kernel_source_sha()
     for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
@@ -377,7 +381,7 @@ def recorded_opmix(precision):
                 continue
             kv = dict(t.split("=", 1) for t in line.split()[1:])
             if kv.get("precision") == precision and kv.get("source") == want:
-                return {k: float(kv[k]) for k in ("dadd", "dfma", "dmul") if k in kv}
+                return {k: float(kv[k]) for k in OPMIX_KINDS if k in kv}
     return {}
 
 
@@ -452,11 +456,27 @@ def roofline(nb, path, n, kernel_ms, peaks, sm_mhz):
             r["fp64_pipe"]["mix_note"] = ("ceiling = the kernel's FP64 lane-instructions per evaluation by kind "
                                           "(opmix, profiles/) at the measured rate of each kind: %.3f lanes/clk/SM"
                                           % lanes_mix)
+    mix = recorded_opmix(path)
+    if pipe == "ffma" and all(k in mix for k in ("fadd", "ffma", "fmul", "fadd2", "ffma2", "fmul2")):
+        # the FMA pipe by the work it does: each FP32 add, multiply or FMA
+        # one lane-cycle, each packed .f32x2 one two lane-cycles (it holds
+        # the pipe for two cycles), against the measured FFMA rate
+        lane_ops = mix["fadd"] + mix["ffma"] + mix["fmul"] + 2 * (mix["fadd2"] + mix["ffma2"] + mix["fmul2"])
+        cpeak = lanes * SM_COUNT * mhz * 1e6 / 1e12
+        cach = lane_ops * evals / (kernel_ms / 1e3) / 1e12
+        r["fma_pipe"] = {"achieved": round(cach, 3), "peak": round(cpeak, 3), "unit": "T lane-cycles/s",
+                         "frac": round(cach / cpeak, 4),
+                         "lane_cycles_per_evaluation": round(lane_ops, 3),
+                         "source": "FP32 op mix per evaluation (opmix, profiles/) x evaluations over the live "
+                                   "kernel time; peak the measured FFMA rate %.3f lanes/clk/SM x %d SMs x "
+                                   "%.0f MHz" % (lanes, SM_COUNT, mhz)}
     units = [("FP64 FMA" if pipe == "dfma" else "FP32 FMA", r["frac"])]
     if "issue" in r:
         units.append(("issue", r["issue"]["frac"]))
     if "fp64_pipe" in r:
         units.append(("FP64 pipe", r["fp64_pipe"]["frac"]))
+    if "fma_pipe" in r:
+        units.append(("FMA pipe", r["fma_pipe"]["frac"]))
     if len(units) > 1:
         r["binding"] = max(units, key=lambda u: u[1])[0]
     if path == "fp64" and kname.startswith("k_pair_sym"):

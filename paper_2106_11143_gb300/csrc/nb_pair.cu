@@ -390,7 +390,7 @@ Plan make_plan(int64_t n, int mode, int kind, bool allow_sym, int64_t ni) {
   // (split), 1000 (mixed), 1500 (fp64) or 2000 (df64); 32-ion blocks (one
   // warp) first, then 64 from n = 2000-2500, 128 from n = 2500-4096, 256
   // from n = 32768 and 512 from n = 60000; split: 256 from n = 4096 and
-  // 512-ion blocks with two P-ions per lane from n = 8000.
+  // 512-ion blocks with four P-ions per lane from n = 8000.
   if (allow_sym && kind == 0 &&
       (mode == MODE_FP64 || mode == MODE_DF64 || mode == MODE_MIXED || split_like(mode))) {
     int G;

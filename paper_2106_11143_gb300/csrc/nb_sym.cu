@@ -265,24 +265,48 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
   return r;
 }
 
+// The four P-ions of a lane as two packed pairs (ions 0-1 and 2-3), staged
+// in shared memory already paired: for P-tile t, pair v and lane, four
+// float4 at ((t 2 + v) 4 + k) 32 + lane, k = 0..3, holding (hx, hy), (hz, lx),
+// (ly, lz) and (w, 0) with each coordinate as the pair (ion 2v, ion 2v+1).
+// Loading a pair from one 128-bit entry gives it an aligned register pair;
+// pairs assembled from separate loads were re-assembled inside the pair loop
+// by the compiler (about 20 register moves per 128 evaluations).
+__device__ __forceinline__ void sym_stage_p4(float4 *f, int t, int BI, int64_t p0, int64_t n, const double *q,
+                                             const PosF32 &pf, bool qarr) {
+  const int pt = t >> 6, v = (t >> 5) & 1, lane = t & 31;
+  const int64_t ga = p0 + pt * 128 + 64 * v + lane, gb = ga + 32;  // ions 2v and 2v + 1 of the lane
+  const bool ra = ga < n, rb = gb < n;
+  const float far = (float)SYM_FAR;
+  float4 *e = f + (pt * 2 + v) * 128 + lane;
+  e[0] = make_float4(ra ? pf.xh[ga] : far, rb ? pf.xh[gb] : far, ra ? pf.yh[ga] : far, rb ? pf.yh[gb] : far);
+  e[32] = make_float4(ra ? pf.zh[ga] : far, rb ? pf.zh[gb] : far, ra ? pf.xl[ga] : 0.0f, rb ? pf.xl[gb] : 0.0f);
+  e[64] = make_float4(ra ? pf.yl[ga] : 0.0f, rb ? pf.yl[gb] : 0.0f, ra ? pf.zl[ga] : 0.0f, rb ? pf.zl[gb] : 0.0f);
+  e[96] = make_float4(ra ? (qarr ? (float)q[ga] : 1.0f) : 0.0f, rb ? (qarr ? (float)q[gb] : 1.0f) : 0.0f, 0.0f, 0.0f);
+}
+
 // sym_step_split4 with the four P-ions' arithmetic in two packed pairs
 // (ions 0-1 and 2-3): two independent chains per lane; per ion the same
 // operations in the same order as split_eval, and the Q sum takes the ions'
-// terms in the order 0, 1, 2, 3.
+// terms in the order 0, 1, 2, 3.  pe: this lane's first staged entry of the
+// P-tile (sym_stage_p4's layout).
 template <bool W, bool SEED>
-__device__ __forceinline__ void sym_step_split4_packed(const float4 *h, const float4 *l, const float4 *qhi,
-                                                       const float4 *qlo, float soft2f, int lane, float a[4][3],
-                                                       float b[3]) {
+__device__ __forceinline__ void sym_step_split4_packed(const float4 *pe, const float4 *qhi, const float4 *qlo,
+                                                       float soft2f, int lane, float a[4][3], float b[3]) {
   f2 phx[2], phy[2], phz[2], plx[2], ply[2], plz[2], pw[2], ax[2], ay[2], az[2];
 #pragma unroll
   for (int v = 0; v < 2; ++v) {
-    phx[v] = f2_pack(h[2 * v].x, h[2 * v + 1].x);
-    phy[v] = f2_pack(h[2 * v].y, h[2 * v + 1].y);
-    phz[v] = f2_pack(h[2 * v].z, h[2 * v + 1].z);
-    plx[v] = f2_pack(l[2 * v].x, l[2 * v + 1].x);
-    ply[v] = f2_pack(l[2 * v].y, l[2 * v + 1].y);
-    plz[v] = f2_pack(l[2 * v].z, l[2 * v + 1].z);
-    pw[v] = f2_pack(h[2 * v].w, h[2 * v + 1].w);
+    const float4 e0 = pe[v * 128], e1 = pe[v * 128 + 32], e2 = pe[v * 128 + 64];
+    phx[v] = f2_pack(e0.x, e0.y);
+    phy[v] = f2_pack(e0.z, e0.w);
+    phz[v] = f2_pack(e1.x, e1.y);
+    plx[v] = f2_pack(e1.z, e1.w);
+    ply[v] = f2_pack(e2.x, e2.y);
+    plz[v] = f2_pack(e2.z, e2.w);
+    if (W) {
+      const float4 e3 = pe[v * 128 + 96];
+      pw[v] = f2_pack(e3.x, e3.y);
+    }
     ax[v] = f2_pack(a[2 * v][0], a[2 * v + 1][0]);
     ay[v] = f2_pack(a[2 * v][1], a[2 * v + 1][1]);
     az[v] = f2_pack(a[2 * v][2], a[2 * v + 1][2]);
@@ -337,7 +361,8 @@ __device__ __forceinline__ void sym_step_split4_packed(const float4 *h, const fl
 }
 
 // Off-diagonal item, split precision with 128-ion P-tiles: GP = G/4 P-tiles
-// and NW = 2 GP warps (8 warps for 512-ion blocks, 16 for 1024).  At step k
+// and NW = 2 GP warps (8 warps for 512-ion blocks, 16 for 1024); posP holds
+// the P block in sym_stage_p4's paired layout.  At step k
 // warp w holds P-tile (qs + k) mod GP, which it shares with warp w +- GP; the
 // two keep their P sums in separate double-float copies (accPf: [2][2][3][BI]
 // floats, copy w / GP), added in copy order at the end, so no two warps ever
@@ -356,16 +381,10 @@ __device__ __forceinline__ void sym_offdiag_split4(const SD4 *posP, SD4 *posQ, f
     for (int k = 0; k < GP; ++k) {
       const int pt = (qs + k) % GP;
       __syncthreads();  // all warps are at step k
-      float4 h[4], l[4];
       float a[4][3], b[3] = {0, 0, 0};
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = pt * 128 + 32 * u + lane;
-        h[u] = fP[i];
-        l[u] = fP[BI + i];
-        a[u][0] = a[u][1] = a[u][2] = 0.0f;
-      }
-      sym_step_split4_packed<W, SEED>(h, l, qhi, qlo, (float)soft2, lane, a, b);
+      for (int u = 0; u < 4; ++u) a[u][0] = a[u][1] = a[u][2] = 0.0f;
+      sym_step_split4_packed<W, SEED>(fP + pt * 256 + lane, qhi, qlo, (float)soft2, lane, a, b);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = pt * 128 + 32 * u + lane;
@@ -483,10 +502,12 @@ __device__ __forceinline__ void sym_stage(SD4 *dst, int i, int BI, int64_t g, in
 }
 
 // Register budgets: fp64 two 256-thread blocks per SM; the split path's
-// packed four-ion step is left to the compiler (about 100 registers, two
-// blocks per SM: capped at three blocks it spills and runs slower).
+// packed four-ion step with 256 threads three blocks per SM, the number its
+// 72 KB of shared memory allows (80 registers, a few bytes of spills outside
+// the pair loop: 2.6 % faster at n = 1e5 than two blocks of 102 registers,
+// 0.5-1 % slower at n = 16384-40000).
 template <int MODE, bool QARR, bool P2, int NT, bool INPLACE>
-__global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_sym(int64_t n, int nbk, int G,
+__global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : (P2 && NT == 256) ? 3 : 0) k_pair_sym(int64_t n, int nbk, int G,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ y,
                                                          const double *__restrict__ z,
@@ -504,8 +525,11 @@ __global__ void __launch_bounds__(NT, MODE == MODE_FP64 ? 512 / NT : 0) k_pair_s
   const int64_t p0 = (int64_t)P * BI, q0 = (int64_t)Q * BI;
   const int np = (int)min((int64_t)BI, n - p0), nq = (int)min((int64_t)BI, n - q0);
   const int tid = threadIdx.x;
+  const bool paired = P2 && P != Q;  // off-diagonal four-ion items: P block staged in pairs
+  if (paired)
+    for (int t = tid; t < BI / 2; t += NT) sym_stage_p4(reinterpret_cast<float4 *>(posP), t, BI, p0, n, q, pf, QARR);
   for (int i = tid; i < BI; i += NT) {
-    sym_stage<MODE, QARR>(posP, i, BI, p0 + i, n, x, y, z, q, pf, false);
+    if (!paired) sym_stage<MODE, QARR>(posP, i, BI, p0 + i, n, x, y, z, q, pf, false);
     if (P != Q) sym_stage<MODE, QARR>(posQ, i, BI, q0 + i, n, x, y, z, q, pf, true);
     accP[i] = 0.0;
     accP[BI + i] = 0.0;
@@ -956,15 +980,15 @@ cudaError_t launch_pair_sym(int mode, int64_t n, int nbk, int G, const double *x
     case MODE_MIXED:
       return small ? launch_sym_m<MODE_MIXED, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
                    : launch_sym_m<MODE_MIXED, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
-    case MODE_SPLIT:  // 64-ion P-tiles once the G/2 P-tiles outnumber the 8 warps
+    case MODE_SPLIT:  // four P-ions per lane (128-ion P-tiles) from 512-ion blocks
       if (small) return launch_sym_m<MODE_SPLIT, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
-      if (G == 32)  // 1024-ion blocks: 16 warps, so that the 16 P-tiles of 64 ions go round
+      if (G == 32)  // 1024-ion blocks: 16 warps, two on each of the 8 P-tiles of 128 ions
         return launch_sym_m<MODE_SPLIT, true, 512>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
       return G >= 16 ? launch_sym_m<MODE_SPLIT, true, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
                      : launch_sym_m<MODE_SPLIT, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
     case MODE_SPLIT_RSQ:
       if (small) return launch_sym_m<MODE_SPLIT_RSQ, false, S>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
-      if (G == 32)  // 1024-ion blocks: 16 warps, so that the 16 P-tiles of 64 ions go round
+      if (G == 32)  // 1024-ion blocks: 16 warps, two on each of the 8 P-tiles of 128 ions
         return launch_sym_m<MODE_SPLIT_RSQ, true, 512>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
       return G >= 16 ? launch_sym_m<MODE_SPLIT_RSQ, true, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st)
                      : launch_sym_m<MODE_SPLIT_RSQ, false, L>(n, nbk, G, x, y, z, q, pf, soft2, part, sync, err, inplace, st);
