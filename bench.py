@@ -470,6 +470,16 @@ def roofline(nb, path, n, kernel_ms, peaks, sm_mhz):
                          "source": "FP32 op mix per evaluation (opmix, profiles/) x evaluations over the live "
                                    "kernel time; peak the measured FFMA rate %.3f lanes/clk/SM x %d SMs x "
                                    "%.0f MHz" % (lanes, SM_COUNT, mhz)}
+        # convention B on the FP32 pipe: the flops it executes (an FMA two, an
+        # add or multiply one, a packed instruction twice that) over the FP32
+        # FMA peak
+        flops = (2 * mix["ffma"] + mix["fadd"] + mix["fmul"]
+                 + 2 * (2 * mix["ffma2"] + mix["fadd2"] + mix["fmul2"]))
+        bach = flops * evals / (kernel_ms / 1e3) / 1e12
+        r["conv_B"] = {"achieved": round(bach, 3), "frac": round(bach / peak, 4),
+                       "flops_per_evaluation": round(flops, 3),
+                       "note": "executed FP32 flops from the recorded op mix (2 per FFMA, 1 per FADD/FMUL, "
+                               "twice that per packed .f32x2 instruction) over the FP32 FMA peak"}
     units = [("FP64 FMA" if pipe == "dfma" else "FP32 FMA", r["frac"])]
     if "issue" in r:
         units.append(("issue", r["issue"]["frac"]))

@@ -350,6 +350,13 @@ def test_bench_roofline_and_kernel_label(api):
     assert abs(fm["achieved"] - cyc * r["evaluations_per_launch"] / 4.12e-3 / 1e12) < 1e-3
     assert abs(fm["peak"] - 128 * 152 * 2070e6 / 1e12) < 1e-3
     assert abs(fm["frac"] - fm["achieved"] / fm["peak"]) < 1e-4 and fm["frac"] > iss["frac"]
+    # convention B on the FP32 pipe: executed flops (FMA 2, add or multiply 1,
+    # packed twice that) over 2 flops x the FFMA rate
+    flops = 2 * mix["ffma"] + mix["fadd"] + mix["fmul"] + 2 * (2 * mix["ffma2"] + mix["fadd2"] + mix["fmul2"])
+    cb = r["conv_B"]
+    assert abs(cb["flops_per_evaluation"] - flops) < 1e-3 and 30 < flops < 40
+    assert abs(cb["achieved"] - flops * r["evaluations_per_launch"] / 4.12e-3 / 1e12) < 1e-3
+    assert abs(cb["frac"] - cb["achieved"] / r["peak"]) < 1e-4 and r["frac"] < cb["frac"] < fm["frac"]
     assert "fma_pipe" not in bench.roofline(api, "fp64", 100000, 91.09, peaks, 2070.0)
     # every path at N = 1e5 has recorded counters, and the unit named as binding
     # is the one with the largest fraction (FP64 pipe for the paths with FP64
